@@ -1,0 +1,235 @@
+/*
+ * tcdtw.h -- C ABI of libtcdtw.so: exact 1-nearest-neighbour search under
+ * Sakoe-Chiba-windowed dependent multivariate DTW on one GB300 (sm_103a), after
+ * TC-DTW (Shen & Chi): query envelopes, the lower-bound cascade LB_MV -> LB_PC /
+ * LB_TI with selective deployment, survivor compaction, banded DTW with early
+ * abandoning against a device-resident best-so-far; plus a differentiable DTW
+ * distance (forward and adjoint) and a batched persistent launch.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Series are float32, C-contiguous, layout [count][L][D] (D innermost).  Unless a
+ *    comment says "host", every array pointer is a DEVICE pointer on the current
+ *    CUDA device.  The caller owns all inputs and outputs.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls enqueue work on it and return without synchronising, except where a
+ *    host output (stats) is requested.
+ *  - W is the half-width of the Sakoe-Chiba band (Section 2, "Window DTW": cells
+ *    with j-W <= i <= j+W); W >= L-1 means unconstrained and is clamped to L-1.
+ *  - The DTW point cost is the SQUARED Euclidean distance of two D-vectors, summed
+ *    along the warping path (Eq. 1 with the dependent multivariate cost of
+ *    Section 2); distances are returned without a square root.
+ *  - Return value: TCDTW_OK (0) or one of the error codes below; the message is
+ *    tcdtw_strerror(code).  On an error no output is guaranteed to be written.
+ */
+#ifndef TCDTW_H
+#define TCDTW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TCDTW_OK 0
+#define TCDTW_ERR_INVALID 1   /* bad argument: L<1, D<1, W<0, K<1, N<1, null pointer, ... */
+#define TCDTW_ERR_NOMEM 2     /* a device allocation failed */
+#define TCDTW_ERR_CUDA 3      /* a CUDA runtime call or kernel launch failed */
+#define TCDTW_ERR_TIMEOUT 4   /* a device-side wait hit its iteration limit */
+#define TCDTW_ERR_NONFINITE 5 /* NaN or Inf found in an input series */
+#define TCDTW_ERR_UNSUPPORTED 6 /* shape outside the compiled kernels (e.g. D too large) */
+
+/* Largest number of dimensions the kernels are compiled for. */
+#define TCDTW_MAX_D 64
+
+/* Which lower bound tcdtw_lower_bounds computes. */
+#define TCDTW_LB_MV 0 /* LB_MV (Section 3), over candidate points, no sqrt            */
+#define TCDTW_LB_PC 1 /* LB_PC (Section 5) with uniform window grouping              */
+#define TCDTW_LB_TI 2 /* LB_TI in its TIP_TOP form (Section 4.2 (3))                  */
+
+typedef struct tcdtw_index tcdtw_index; /* opaque; created by tcdtw_build */
+
+/*
+ * Search options (Sections 6 and 7.1 give the paper's values).
+ *  P       LB_TI period: query rows i with i mod P == 0 use exact distances (5).
+ *  Lq      LB_PC quantisation levels per dimension (2).
+ *  w       LB_PC window expansion factor: boxes per group of w windows (6).
+ *  e_pc, e_ti  selective-deployment thresholds: LB_PC / LB_TI run on a pair only if
+ *          e * best-so-far < LB_MV < best-so-far (0.1, 0.1).
+ *  use_pc, use_ti  enable the two tight bounds (1, 1).
+ *  seed_s  per query, the DTW of the seed_s candidates with the smallest LB_MV is
+ *          computed first to start the best-so-far low (4).
+ *  qblock  queries per pipeline block (0 = chosen from free memory).
+ *  tile    DTW band-tile id (-1 = autotuned; see tcdtw_tile_count()).
+ *  check_finite  1 = scan inputs and fail with TCDTW_ERR_NONFINITE on NaN/Inf (1).
+ */
+typedef struct {
+    int32_t P;
+    int32_t Lq;
+    int32_t w;
+    float e_pc;
+    float e_ti;
+    int32_t use_pc;
+    int32_t use_ti;
+    int32_t seed_s;
+    int32_t qblock;
+    int32_t tile;
+    int32_t check_finite;
+} tcdtw_opts;
+
+/* Counters of one tcdtw_nn call, summed over its queries. */
+typedef struct {
+    uint64_t pairs;         /* query-candidate pairs considered (M*N)               */
+    uint64_t pruned_mv;     /* pairs whose LB_MV exceeded the best-so-far threshold  */
+    uint64_t pruned_pc;     /* ... pruned by LB_PC after passing LB_MV               */
+    uint64_t pruned_ti;     /* ... pruned by LB_TI                                   */
+    uint64_t dtw_started;   /* DTWs started (seeds included)                         */
+    uint64_t dtw_abandoned; /* DTWs stopped early against the best-so-far            */
+    uint64_t cells;         /* DTW cells computed in FP32                            */
+    uint64_t refined;       /* candidates recomputed in FP64 to settle near-ties     */
+} tcdtw_stats;
+
+/* Fill *opts with the defaults listed above. */
+void tcdtw_default_opts(tcdtw_opts *opts);
+
+/*
+ * tcdtw_build -- prepare a searchable candidate set C (Def. 1: the set C of
+ * candidate series; the search is for each query's nearest member of C).
+ *   cand  device [N][L][D] float32.  BORROWED: it must stay alive and unchanged
+ *         until tcdtw_free (large sets are not copied).
+ *   N, L, D, W  set size, series length, dimensions, band half-width.
+ *   K     maximum number of LB_PC clusters per expanded window (Section 5).
+ *   opts  NULL = defaults.
+ *   out   host: receives the new index; it owns its device workspaces.
+ * Validates the shapes, scans the candidates for non-finite values (if
+ * opts->check_finite), allocates the per-block workspaces and chooses the DTW tile.
+ * Errors: INVALID, NOMEM, CUDA, NONFINITE, UNSUPPORTED.
+ */
+int tcdtw_build(const float *cand, int64_t N, int32_t L, int32_t D, int32_t W, int32_t K,
+                const tcdtw_opts *opts, void *stream, tcdtw_index **out);
+
+/*
+ * tcdtw_nn -- exact DTW nearest neighbour of each query (Def. 1; Section 2
+ * "DTW-NN"; the search loop of Sections 6-7 re-laid out for the GPU).
+ *   q     device [M][L][D] float32 queries (same L and D as the index).
+ *   idx   device [M] int64: index in C of the nearest candidate; exact ties go to
+ *         the smallest index.
+ *   dist  device [M] float64: its DTW distance, recomputed in FP64.
+ *   stats host, may be NULL; when given, the call synchronises `stream` and fills it.
+ * Every bound is a rigorous lower bound in FP32 (directed rounding), pruning uses a
+ * margin that covers the FP32 DTW rounding error, and candidates whose FP32 DTW
+ * cannot be told apart from the best are recomputed in FP64 -- so idx equals the
+ * FP64 brute-force argmin.  Errors: INVALID, NOMEM, CUDA, NONFINITE, TIMEOUT.
+ */
+int tcdtw_nn(tcdtw_index *index, const float *q, int64_t M, int64_t *idx, double *dist,
+             tcdtw_stats *stats, void *stream);
+
+/* Release an index and its workspaces (NULL is accepted). */
+void tcdtw_free(tcdtw_index *index);
+
+/*
+ * tcdtw_dtw_pairs -- DTW distance of P independent pairs (A[p], B[p]) (Eq. 1 in the
+ * Sakoe-Chiba band), no abandoning.
+ *   A, B  device [P][L][D] float32.   dist  device [P] float32.
+ *   ckpt  device buffer of ckpt_bytes (from tcdtw_dtw_pairs_ckpt_bytes) that
+ *         receives band rows every few rows for tcdtw_dtw_pairs_backward, or NULL.
+ * Errors: INVALID (also ckpt_bytes too small), CUDA, UNSUPPORTED.
+ */
+int tcdtw_dtw_pairs(const float *A, const float *B, int64_t P, int32_t L, int32_t D, int32_t W,
+                    float *dist, void *ckpt, int64_t ckpt_bytes, void *stream);
+
+/* Bytes of checkpoint storage tcdtw_dtw_pairs needs for P pairs (host *bytes). */
+int tcdtw_dtw_pairs_ckpt_bytes(int64_t P, int32_t L, int32_t D, int32_t W, int64_t *bytes);
+
+/*
+ * tcdtw_dtw_pairs_backward -- adjoint of tcdtw_dtw_pairs (not in the paper, which
+ * only names DTW as a loss, Section 1).  For each pair the optimal warping path is
+ * recomputed segment by segment from the checkpointed band rows and backtracked from
+ * (L-1, L-1) (exact ties: diagonal, then (i-1, j), then (i, j-1)); then
+ *   gA[p][i] = grad_dist[p] * sum_{(i,j) on path} 2 (A[p][i] - B[p][j]),
+ *   gB[p][j] = grad_dist[p] * sum_{(i,j) on path} 2 (B[p][j] - A[p][i]).
+ *   ckpt  the buffer filled by tcdtw_dtw_pairs on the same A, B, L, D, W.
+ *   grad_dist device [P] float32;  gA, gB device [P][L][D] float32 (overwritten).
+ * Errors: INVALID, CUDA, UNSUPPORTED.
+ */
+int tcdtw_dtw_pairs_backward(const float *A, const float *B, const void *ckpt, int64_t ckpt_bytes,
+                             const float *grad_dist, int64_t P, int32_t L, int32_t D, int32_t W,
+                             float *gA, float *gB, void *stream);
+
+/*
+ * Stage entry points (each is one step of the tcdtw_nn pipeline, exposed for
+ * checking and for callers who build their own pruning).
+ */
+
+/* Query envelopes (Section 3, "Algorithm LB_MV"): U[m][i][p] = max of q[m][k][p] over
+ * k in [i-W, i+W] clipped to [0, L-1], Lo likewise with min.  q, U, Lo device
+ * [M][L][D] float32.  Exact (min/max).  Errors: INVALID, CUDA. */
+int tcdtw_envelope(const float *q, int64_t M, int32_t L, int32_t D, int32_t W, float *U, float *Lo,
+                   void *stream);
+
+/* Query neighbour distances d(q_{i-1}, q_i) (Section 4.1) as an interval:
+ * dq_lo[m][i] <= exact <= dq_hi[m][i] (FP32 rounded down / up); entry 0 is 0.
+ * dq_lo, dq_hi device [M][L] float32.  Errors: INVALID, CUDA. */
+int tcdtw_query_dq(const float *q, int64_t M, int32_t L, int32_t D, float *dq_lo, float *dq_hi,
+                   void *stream);
+
+/* LB_PC boxes of each query (Section 5): boxes device [M][G][K][2][D] float32
+ * (lower corner, upper corner), counts device [M][G] int32, G = ceil(L/w).  Cell ids
+ * are taken with FP32 round-to-nearest subtraction and division,
+ * id = min(Lq-1, floor((x - min_p) / max((max_p - min_p)/Lq, 1e-5))); cells are
+ * ordered lexicographically (dimension 0 most significant); beyond K cells the
+ * first K-1 are kept and the rest merged; boxes are tight member bounding boxes.
+ * Errors: INVALID (Lq^D must fit in 63 bits), CUDA. */
+int tcdtw_pc_boxes(const float *q, int64_t M, int32_t L, int32_t D, int32_t W, int32_t K, int32_t Lq,
+                   int32_t w, float *boxes, int32_t *counts, void *stream);
+
+/* All M*N values of one lower bound (which = TCDTW_LB_*), no abandoning, rounded
+ * down so that out[m][n] <= the exact bound <= DTW(q[m], c[n]).
+ * q device [M][L][D], c device [N][L][D], out device [M][N] float32.
+ * opts supplies P, Lq and w (NULL = defaults); K is the LB_PC cluster cap.
+ * Errors: INVALID, NOMEM, CUDA. */
+int tcdtw_lower_bounds(const float *q, int64_t M, const float *c, int64_t N, int32_t L, int32_t D,
+                       int32_t W, int32_t K, const tcdtw_opts *opts, int32_t which, float *out,
+                       void *stream);
+
+/* Survivor compaction: for each row m of lb [M][N], the column indices n with
+ * lb[m][n] <= thresh[m], in increasing n, written to out_idx[m][0 .. count[m]-1]
+ * (out_idx device [M][N] int32, count device [M] int32).  Errors: INVALID, CUDA. */
+int tcdtw_compact(const float *lb, int64_t M, int64_t N, const float *thresh, int32_t *out_idx,
+                  int32_t *count, void *stream);
+
+/*
+ * Batched search: many independent (candidate set, query set) problems of uneven
+ * L, D, N, W in one persistent launch off a device work queue (not in the paper).
+ * Each entry is searched exactly as tcdtw_nn would (same bounds, same exactness).
+ */
+typedef struct {
+    const float *cand; /* device [N][L][D] */
+    int64_t N;
+    int32_t L, D, W, K;
+    const float *q;    /* device [M][L][D] */
+    int64_t M;
+    int64_t *idx;      /* device [M] */
+    double *dist;      /* device [M] */
+} tcdtw_dataset;
+
+/* sets: HOST array of nsets descriptors.  opts: NULL = defaults.  stats: host, may
+ * be NULL (summed over all sets; synchronises when given).
+ * Errors: INVALID, NOMEM, CUDA, NONFINITE, TIMEOUT, UNSUPPORTED. */
+int tcdtw_batch_nn(const tcdtw_dataset *sets, int32_t nsets, const tcdtw_opts *opts,
+                   tcdtw_stats *stats, void *stream);
+
+/* Number of compiled DTW band tiles, and the shape of tile t: G lanes per pair,
+ * R rows per lane (host outputs).  Returns INVALID for an unknown t. */
+int tcdtw_tile_count(void);
+int tcdtw_tile_info(int32_t t, int32_t *G, int32_t *R, int32_t *maxD);
+
+/* Static message for an error code. */
+const char *tcdtw_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TCDTW_H */

@@ -1,0 +1,15 @@
+// api_internal.h -- helpers shared by the host-side API translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tc {
+int num_sms();
+int dmax_for(int D);
+bool tile_valid(int tile, int G, int W);
+bool choose_tile(int64_t P, int L, int D, int W, int need_div, int *tile, int *G);
+int blocks_for(int tile, int which, int64_t groups, int G);
+int ckpt_rows(int L, int W);
+int64_t ckpt_floats(int64_t P, int L, int W);
+int cuda_err(cudaError_t e);
+}  // namespace tc
