@@ -104,6 +104,8 @@ void tcdtw_default_opts(tcdtw_opts *opts);
  *   out   host: receives the new index; it owns its device workspaces.
  * Validates the shapes, scans the candidates for non-finite values (if
  * opts->check_finite), allocates the per-block workspaces and chooses the DTW tile.
+ * LB_PC is switched off (results are unchanged, only pruning) when its cell keys
+ * Lq^D do not fit in 63 bits.
  * Errors: INVALID, NOMEM, CUDA, NONFINITE, UNSUPPORTED.
  */
 int tcdtw_build(const float *cand, int64_t N, int32_t L, int32_t D, int32_t W, int32_t K,

@@ -1,0 +1,475 @@
+// api_nn.cu -- C ABI of the exact DTW-NN search (Def. 1; the search loop of
+// Sections 6-7 laid out as a GPU pipeline) and of its individual stages.
+//
+// Per block of Mb queries, everything stays on the device:
+//   1  envelopes, neighbour distances, LB_PC boxes          (prep.cu)
+//   2  LB_MV of every (query, candidate) pair              (lb.cu, HBM/L2 stream)
+//   3  seeds: per query the seed_s smallest LB_MV, their DTW lowers best-so-far
+//   4  compaction of pairs with LB_MV <= threshold         (ordered, flat list)
+//   5  gated LB_PC / LB_TI on the survivors (e*bsf < LB_MV < bsf, Section 6)
+//   6  banded DTW of the survivors, abandoning against the live best-so-far
+//   7  candidates whose FP32 DTW is within the rounding margin of the best are
+//      recomputed in FP64; the FP64 minimum (smallest index on ties) is the answer.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "api_internal.h"
+#include "common.cuh"
+#include "dtw_tiles.cuh"
+#include "lb_kernels.cuh"
+
+using namespace tc;
+
+namespace tc {
+
+// Pruning factor rho = (1+g32)/(1-g32) * (1+g64)/(1-g64) with g = n*u/(1-n*u),
+// n = 2L+D+2 roundings along a warping path (cell cost and DP additions), u the
+// unit roundoff.  Rounded up to float.
+float prune_rho(int L, int D) {
+    const double n = 2.0 * L + D + 2.0;
+    const double u32 = ldexp(1.0, -24), u64 = ldexp(1.0, -53);
+    const double g32 = n * u32 / (1.0 - n * u32), g64 = n * u64 / (1.0 - n * u64);
+    const double rho = (1.0 + g32) / (1.0 - g32) * (1.0 + g64) / (1.0 - g64);
+    float r = (float)rho;
+    if ((double)r < rho) r = nextafterf(r, INFINITY);
+    return r;
+}
+
+bool pc_key_fits(int Lq, int D) {
+    // Lq^D must fit below 2^63 (mixed-radix cell key)
+    long double v = 1;
+    for (int p = 0; p < D; ++p) {
+        v *= Lq;
+        if (v > 9.2e18L) return false;
+    }
+    return true;
+}
+
+// Smallest-R valid tile of the D bucket (FP64 refine: registers are doubled).
+bool choose_refine_tile(int D, int W, int *tile, int *G) {
+    const int dm = dmax_for(D);
+    int bestR = 1 << 30;
+    bool found = false;
+    for (int t = 0; t < kNumTiles; ++t) {
+        if (kTiles[t].DMAX != dm) continue;
+        for (int g = 4; g <= 32; g *= 2) {
+            if (!tile_valid(t, g, W)) continue;
+            const int cost = kTiles[t].R * 64 + g;
+            if (cost < bestR) { bestR = cost; *tile = t; *G = g; found = true; }
+        }
+    }
+    if (!found) return choose_tile(1, W + 1, D, W, 0, tile, G);
+    return true;
+}
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    return cudaMalloc((void **)p, n * sizeof(T));
+}
+
+enum Counter { kStarted = 0, kAbandoned, kCells, kPrunedDtw, kPrunedMv, kPrunedPc, kPrunedTi, kRefined, kNumCounters };
+enum Scalar { kSurvTotal = 0, kCursorSeed, kCursorSurv, kRefineCount, kNumScalars };
+
+}  // namespace tc
+
+struct tcdtw_index {
+    const float *cand = nullptr;
+    int64_t N = 0;
+    int L = 0, D = 0, W = 0, K = 0;
+    tcdtw_opts opts;
+    int Mb = 0, Mb_pad = 0, S = 0, G_pc = 0;
+    int64_t ldE = 0;
+    float rho = 1.f;
+    int tile = 0, G = 32, tile_ref = 0, G_ref = 32, sms = 1;
+    int blocks_nn = 1, blocks_ref = 1;
+    // workspaces
+    float *U = nullptr, *Lo = nullptr, *dq_lo = nullptr, *dq_hi = nullptr, *boxes = nullptr, *lbm = nullptr;
+    int32_t *box_counts = nullptr;
+    uint32_t *seeds = nullptr, *surv = nullptr, *refine = nullptr;
+    float *seed_dtw = nullptr, *surv_lb = nullptr, *surv_dtw = nullptr;
+    double *refine_d64 = nullptr;
+    int32_t *row_counts = nullptr, *row_offsets = nullptr, *scalars = nullptr;
+    unsigned long long *bsf = nullptr, *best64 = nullptr, *best_idx = nullptr, *counters = nullptr;
+    DevStatus *status = nullptr;
+    int64_t refine_cap = 0;
+};
+
+namespace {
+
+void free_index(tcdtw_index *x) {
+    if (!x) return;
+    void *ptrs[] = {x->U, x->Lo, x->dq_lo, x->dq_hi, x->boxes, x->lbm, x->box_counts, x->seeds, x->surv,
+                    x->refine, x->seed_dtw, x->surv_lb, x->surv_dtw, x->refine_d64, x->row_counts,
+                    x->row_offsets, x->scalars, x->bsf, x->best64, x->best_idx, x->counters, x->status};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete x;
+}
+
+int validate_shape(int64_t N, int L, int D, int W, int K) {
+    if (N < 1 || L < 1 || D < 1 || W < 0 || K < 1) return TCDTW_ERR_INVALID;
+    if (D > TCDTW_MAX_D) return TCDTW_ERR_UNSUPPORTED;
+    return TCDTW_OK;
+}
+
+#define TC_TRY(expr)                                  \
+    do {                                              \
+        cudaError_t e_ = (expr);                      \
+        if (e_ != cudaSuccess) return cuda_err(e_);   \
+    } while (0)
+
+int alloc_index(tcdtw_index *x) {
+    const int64_t Mb = x->Mb, N = x->N;
+    const int L = x->L, D = x->D;
+    TC_TRY(dalloc(&x->U, (size_t)x->Mb_pad * x->ldE));
+    TC_TRY(dalloc(&x->Lo, (size_t)x->Mb_pad * x->ldE));
+    TC_TRY(dalloc(&x->dq_lo, (size_t)Mb * L));
+    TC_TRY(dalloc(&x->dq_hi, (size_t)Mb * L));
+    if (x->opts.use_pc) {
+        TC_TRY(dalloc(&x->boxes, (size_t)Mb * x->G_pc * x->K * 2 * D));
+        TC_TRY(dalloc(&x->box_counts, (size_t)Mb * x->G_pc));
+    }
+    TC_TRY(dalloc(&x->lbm, (size_t)Mb * N));
+    TC_TRY(dalloc(&x->seeds, (size_t)Mb * x->S));
+    TC_TRY(dalloc(&x->seed_dtw, (size_t)Mb * x->S));
+    TC_TRY(dalloc(&x->surv, (size_t)Mb * N));
+    TC_TRY(dalloc(&x->surv_lb, (size_t)Mb * N));
+    TC_TRY(dalloc(&x->surv_dtw, (size_t)Mb * N));
+    x->refine_cap = Mb * (N + x->S);
+    TC_TRY(dalloc(&x->refine, (size_t)x->refine_cap));
+    TC_TRY(dalloc(&x->refine_d64, (size_t)x->refine_cap));
+    TC_TRY(dalloc(&x->row_counts, (size_t)Mb));
+    TC_TRY(dalloc(&x->row_offsets, (size_t)Mb));
+    TC_TRY(dalloc(&x->scalars, (size_t)kNumScalars));
+    TC_TRY(dalloc(&x->bsf, (size_t)Mb));
+    TC_TRY(dalloc(&x->best64, (size_t)Mb));
+    TC_TRY(dalloc(&x->best_idx, (size_t)Mb));
+    TC_TRY(dalloc(&x->counters, (size_t)kNumCounters));
+    TC_TRY(dalloc(&x->status, 1));
+    TC_TRY(cudaMemset(x->status, 0, sizeof(DevStatus)));
+    TC_TRY(cudaMemset(x->counters, 0, sizeof(unsigned long long) * kNumCounters));
+    return TCDTW_OK;
+}
+
+// One block of Mb_cur queries.  All launches on stream s; no host synchronisation.
+cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_out, double *dist_out,
+                      cudaStream_t s) {
+    const int L = x->L, D = x->D, W = x->W;
+    const int64_t N = x->N;
+    const int E = L * D;
+    cudaError_t e;
+    if (x->opts.check_finite) {
+        e = launch_check_finite(q, (int64_t)Mb_cur * E, x->status, 1, s);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaMemsetAsync(x->scalars, 0, sizeof(int32_t) * kNumScalars, s);
+    if (e != cudaSuccess) return e;
+    if ((e = launch_init_block(Mb_cur, x->bsf, x->best64, x->best_idx, s)) != cudaSuccess) return e;
+    // 1. query-side preparation
+    if ((e = launch_envelope(q, Mb_cur, L, D, W, x->U, x->Lo, (int)x->ldE, s)) != cudaSuccess) return e;
+    if (x->opts.use_ti && (e = launch_query_dq(q, Mb_cur, L, D, x->dq_lo, x->dq_hi, s)) != cudaSuccess) return e;
+    if (x->opts.use_pc &&
+        (e = launch_pc_boxes(q, Mb_cur, L, D, W, x->K, x->opts.Lq, x->opts.w, x->boxes, x->box_counts, s)) !=
+            cudaSuccess)
+        return e;
+    // 2. LB_MV of all pairs
+    LbMvArgs mv;
+    mv.cand = x->cand; mv.N = N; mv.E = E; mv.U = x->U; mv.Lo = x->Lo; mv.ldE = x->ldE; mv.Mb = Mb_cur;
+    mv.lb = x->lbm; mv.ldLb = N; mv.sms = x->sms;
+    if ((e = launch_lb_mv(mv, s)) != cudaSuccess) return e;
+    // 3. seeds and their DTW
+    if ((e = launch_seed_topk(x->lbm, Mb_cur, N, N, x->S, x->seeds, s)) != cudaSuccess) return e;
+    DtwNnArgs dn;
+    dn.Q = q; dn.C = x->cand; dn.L = L; dn.D = D; dn.W = W; dn.G = x->G; dn.N = N;
+    dn.pairs = x->seeds; dn.lb = nullptr; dn.count = nullptr; dn.n_static = Mb_cur * x->S;
+    dn.cursor = x->scalars + kCursorSeed; dn.bsf = x->bsf; dn.rho = x->rho; dn.dtw = x->seed_dtw;
+    dn.counters = x->counters;
+    if ((e = dtw_nn_launch(x->tile, x->blocks_nn, s, dn)) != cudaSuccess) return e;
+    // 4. compaction against the seeded best-so-far
+    CompactArgs ca;
+    memset(&ca, 0, sizeof(ca));
+    ca.lb = x->lbm; ca.M = Mb_cur; ca.N = N; ca.ldLb = N; ca.thresh = nullptr; ca.bsf = x->bsf; ca.rho = x->rho;
+    ca.counts = x->row_counts; ca.offsets = x->row_offsets; ca.total = x->scalars + kSurvTotal;
+    ca.pairs = x->surv; ca.lbs = x->surv_lb; ca.pruned = x->counters + kPrunedMv;
+    if ((e = launch_compact(ca, s)) != cudaSuccess) return e;
+    // 5. gated tight bounds
+    PairListArgs pl;
+    pl.Q = q; pl.C = x->cand; pl.L = L; pl.D = D; pl.W = W; pl.pairs = x->surv;
+    pl.count = x->scalars + kSurvTotal; pl.n_static = 0; pl.N = N; pl.lb = x->surv_lb;
+    const int64_t hint = (int64_t)Mb_cur * 64;
+    if (x->opts.use_pc &&
+        (e = launch_lb_pc_list(pl, x->boxes, x->box_counts, x->K, x->opts.w, x->bsf, x->rho, x->opts.e_pc,
+                               x->counters + kPrunedPc, hint, x->sms, s)) != cudaSuccess)
+        return e;
+    if (x->opts.use_ti &&
+        (e = launch_lb_ti_list(pl, x->dq_lo, x->dq_hi, x->opts.P, x->bsf, x->rho, x->opts.e_ti,
+                               x->counters + kPrunedTi, hint, x->sms, s)) != cudaSuccess)
+        return e;
+    // 6. DTW of the survivors
+    dn.pairs = x->surv; dn.lb = x->surv_lb; dn.count = x->scalars + kSurvTotal; dn.n_static = 0;
+    dn.cursor = x->scalars + kCursorSurv; dn.dtw = x->surv_dtw;
+    if ((e = dtw_nn_launch(x->tile, x->blocks_nn, s, dn)) != cudaSuccess) return e;
+    // 7. refine near-ties in FP64 and select
+    if ((e = launch_refine_select(x->seeds, x->seed_dtw, nullptr, (int64_t)Mb_cur * x->S, N, x->bsf, x->rho,
+                                  x->refine, x->scalars + kRefineCount, x->refine_cap, x->sms, s)) != cudaSuccess)
+        return e;
+    if ((e = launch_refine_select(x->surv, x->surv_dtw, x->scalars + kSurvTotal, 0, N, x->bsf, x->rho, x->refine,
+                                  x->scalars + kRefineCount, x->refine_cap, x->sms, s)) != cudaSuccess)
+        return e;
+    DtwRefineArgs rf;
+    rf.Q = q; rf.C = x->cand; rf.L = L; rf.D = D; rf.W = W; rf.G = x->G_ref; rf.N = N;
+    rf.pairs = x->refine; rf.count = x->scalars + kRefineCount; rf.d64 = x->refine_d64; rf.best64 = x->best64;
+    if ((e = dtw_refine_launch(x->tile_ref, x->blocks_ref, s, rf)) != cudaSuccess) return e;
+    if ((e = launch_refine_pick(x->refine, x->refine_d64, x->scalars + kRefineCount, N, x->best64, x->best_idx,
+                                x->sms, s)) != cudaSuccess)
+        return e;
+    if ((e = launch_count_add(x->counters + kRefined, x->scalars + kRefineCount, s)) != cudaSuccess) return e;
+    return launch_finalize(Mb_cur, x->best64, x->best_idx, idx_out, dist_out, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+int tcdtw_build(const float *cand, int64_t N, int32_t L, int32_t D, int32_t W, int32_t K, const tcdtw_opts *opts,
+                void *stream, tcdtw_index **out) {
+    if (!out) return TCDTW_ERR_INVALID;
+    *out = nullptr;
+    if (!cand) return TCDTW_ERR_INVALID;
+    int rc = validate_shape(N, L, D, W, K);
+    if (rc) return rc;
+    tcdtw_opts o;
+    if (opts) o = *opts; else tcdtw_default_opts(&o);
+    if (o.P < 1 || o.Lq < 1 || o.w < 1 || o.seed_s < 1 || o.seed_s > 8 || o.qblock < 0) return TCDTW_ERR_INVALID;
+    // LB_PC only changes speed: skip it when the cell keys (Lq^D) do not fit 63 bits
+    if (o.use_pc && !pc_key_fits(o.Lq, D)) o.use_pc = 0;
+    if (W > L - 1) W = L - 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    tcdtw_index *x = new (std::nothrow) tcdtw_index();
+    if (!x) return TCDTW_ERR_NOMEM;
+    x->cand = cand; x->N = N; x->L = L; x->D = D; x->W = W; x->K = K; x->opts = o;
+    x->S = (int)(o.seed_s < N ? o.seed_s : N);
+    x->sms = num_sms();
+    x->G_pc = (L + o.w - 1) / o.w;
+    x->ldE = ((int64_t)L * D + 31) / 32 * 32;
+    x->rho = prune_rho(L, D);
+    // query block: bounded by the u32 pair ids and by ~4 GB of workspace
+    int64_t Mb = o.qblock > 0 ? o.qblock : 256;
+    const double per_q = (double)N * 20.0 + (double)x->ldE * 8.0 + (o.use_pc ? (double)x->G_pc * K * 2 * D * 4.0 : 0);
+    while (Mb > 1 && per_q * Mb > 4.0e9) Mb >>= 1;
+    while (Mb > 1 && (double)Mb * (double)N >= 4.29e9) Mb >>= 1;
+    x->Mb = (int)Mb;
+    x->Mb_pad = (int)((Mb + 31) / 32 * 32);
+    if (o.tile >= 0) {
+        if (o.tile >= kNumTiles || kTiles[o.tile].DMAX < D) { free_index(x); return TCDTW_ERR_INVALID; }
+        x->tile = o.tile;
+        x->G = 0;
+        for (int g = 4; g <= 32; g *= 2)
+            if (tile_valid(o.tile, g, W)) { x->G = g; break; }
+        if (!x->G) { free_index(x); return TCDTW_ERR_INVALID; }
+    } else if (!choose_tile((int64_t)x->Mb * 64, L, D, W, 0, &x->tile, &x->G)) {
+        free_index(x);
+        return TCDTW_ERR_UNSUPPORTED;
+    }
+    if (!choose_refine_tile(D, W, &x->tile_ref, &x->G_ref)) { free_index(x); return TCDTW_ERR_UNSUPPORTED; }
+    x->blocks_nn = dtw_occupancy(x->tile, 1) * x->sms;
+    if (x->blocks_nn < 1) x->blocks_nn = x->sms;
+    x->blocks_ref = x->sms * 2;
+    rc = alloc_index(x);
+    if (rc) { free_index(x); return rc; }
+    if (o.check_finite) {
+        cudaError_t e = launch_check_finite(cand, N * (int64_t)L * D, x->status, 0, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { free_index(x); return cuda_err(e); }
+        DevStatus st;
+        if (cudaMemcpy(&st, x->status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            free_index(x);
+            return TCDTW_ERR_CUDA;
+        }
+        if (st.code) { free_index(x); return st.code; }
+    }
+    *out = x;
+    return TCDTW_OK;
+}
+
+int tcdtw_nn(tcdtw_index *x, const float *q, int64_t M, int64_t *idx, double *dist, tcdtw_stats *stats,
+             void *stream) {
+    if (!x || M < 0) return TCDTW_ERR_INVALID;
+    if (M == 0) {
+        if (stats) memset(stats, 0, sizeof(*stats));
+        return TCDTW_OK;
+    }
+    if (!q || !idx || !dist) return TCDTW_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t E = (int64_t)x->L * x->D;
+    const bool sync = stats != nullptr || x->opts.check_finite;
+    if (sync) {
+        TC_TRY(cudaMemsetAsync(x->counters, 0, sizeof(unsigned long long) * kNumCounters, s));
+        TC_TRY(cudaMemsetAsync(x->status, 0, sizeof(DevStatus), s));
+    }
+    for (int64_t m0 = 0; m0 < M; m0 += x->Mb) {
+        const int Mb_cur = (int)((M - m0) < x->Mb ? (M - m0) : x->Mb);
+        TC_TRY(run_block(x, q + m0 * E, Mb_cur, idx + m0, dist + m0, s));
+    }
+    if (!sync) return TCDTW_OK;
+    TC_TRY(cudaStreamSynchronize(s));
+    DevStatus st;
+    TC_TRY(cudaMemcpy(&st, x->status, sizeof(st), cudaMemcpyDeviceToHost));
+    if (st.code) return st.code;
+    if (stats) {
+        unsigned long long c[kNumCounters];
+        TC_TRY(cudaMemcpy(c, x->counters, sizeof(c), cudaMemcpyDeviceToHost));
+        const uint64_t seeds = (uint64_t)M * (uint64_t)x->S;
+        stats->pairs = (uint64_t)M * (uint64_t)x->N;
+        stats->pruned_mv = c[kPrunedMv] - seeds + c[kPrunedDtw];
+        stats->pruned_pc = c[kPrunedPc];
+        stats->pruned_ti = c[kPrunedTi];
+        stats->dtw_started = c[kStarted];
+        stats->dtw_abandoned = c[kAbandoned];
+        stats->cells = c[kCells];
+        stats->refined = c[kRefined];
+    }
+    return TCDTW_OK;
+}
+
+void tcdtw_free(tcdtw_index *x) {
+    if (!x) return;
+    cudaDeviceSynchronize();
+    free_index(x);
+}
+
+// ------------------------------------------------------------------ stage entry points
+int tcdtw_envelope(const float *q, int64_t M, int32_t L, int32_t D, int32_t W, float *U, float *Lo, void *stream) {
+    if (M < 0 || L < 1 || D < 1 || W < 0) return TCDTW_ERR_INVALID;
+    if (M == 0) return TCDTW_OK;
+    if (!q || !U || !Lo) return TCDTW_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int64_t m0 = 0; m0 < M; m0 += 65535) {
+        const int64_t mc = (M - m0) < 65535 ? (M - m0) : 65535;
+        const int64_t off = m0 * L * D;
+        TC_TRY(launch_envelope(q + off, mc, L, D, W, U + off, Lo + off, L * D, s));
+    }
+    return TCDTW_OK;
+}
+
+int tcdtw_query_dq(const float *q, int64_t M, int32_t L, int32_t D, float *dq_lo, float *dq_hi, void *stream) {
+    if (M < 0 || L < 1 || D < 1) return TCDTW_ERR_INVALID;
+    if (M == 0) return TCDTW_OK;
+    if (!q || !dq_lo || !dq_hi) return TCDTW_ERR_INVALID;
+    return cuda_err(launch_query_dq(q, M, L, D, dq_lo, dq_hi, (cudaStream_t)stream));
+}
+
+int tcdtw_pc_boxes(const float *q, int64_t M, int32_t L, int32_t D, int32_t W, int32_t K, int32_t Lq, int32_t w,
+                   float *boxes, int32_t *counts, void *stream) {
+    if (M < 0 || L < 1 || D < 1 || W < 0 || K < 1 || Lq < 1 || w < 1) return TCDTW_ERR_INVALID;
+    if (D > TCDTW_MAX_D) return TCDTW_ERR_UNSUPPORTED;
+    if (!pc_key_fits(Lq, D)) return TCDTW_ERR_INVALID;
+    if (M == 0) return TCDTW_OK;
+    if (!q || !boxes || !counts) return TCDTW_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int G = (L + w - 1) / w;
+    for (int64_t m0 = 0; m0 < M; m0 += 65535) {
+        const int64_t mc = (M - m0) < 65535 ? (M - m0) : 65535;
+        TC_TRY(launch_pc_boxes(q + m0 * L * D, mc, L, D, W, K, Lq, w, boxes + m0 * G * K * 2 * D, counts + m0 * G,
+                               s));
+    }
+    return TCDTW_OK;
+}
+
+int tcdtw_compact(const float *lb, int64_t M, int64_t N, const float *thresh, int32_t *out_idx, int32_t *count,
+                  void *stream) {
+    if (M < 0 || N < 0) return TCDTW_ERR_INVALID;
+    if (M == 0) return TCDTW_OK;
+    if (!lb || !thresh || !out_idx || !count) return TCDTW_ERR_INVALID;
+    if (N >= (int64_t)1 << 31) return TCDTW_ERR_UNSUPPORTED;
+    CompactArgs ca;
+    memset(&ca, 0, sizeof(ca));
+    ca.lb = lb; ca.M = M; ca.N = N; ca.ldLb = N; ca.thresh = thresh; ca.counts = count; ca.ldOut = N;
+    ca.idx_out = out_idx;
+    return cuda_err(launch_compact(ca, (cudaStream_t)stream));
+}
+
+int tcdtw_lower_bounds(const float *q, int64_t M, const float *c, int64_t N, int32_t L, int32_t D, int32_t W,
+                       int32_t K, const tcdtw_opts *opts, int32_t which, float *out, void *stream) {
+    if (M < 0 || N < 0 || L < 1 || D < 1 || W < 0 || K < 1) return TCDTW_ERR_INVALID;
+    if (which < TCDTW_LB_MV || which > TCDTW_LB_TI) return TCDTW_ERR_INVALID;
+    if (D > TCDTW_MAX_D) return TCDTW_ERR_UNSUPPORTED;
+    if (M == 0 || N == 0) return TCDTW_OK;
+    if (!q || !c || !out) return TCDTW_ERR_INVALID;
+    tcdtw_opts o;
+    if (opts) o = *opts; else tcdtw_default_opts(&o);
+    if (which == TCDTW_LB_PC && !pc_key_fits(o.Lq, D)) return TCDTW_ERR_INVALID;
+    if (o.P < 1 || o.Lq < 1 || o.w < 1) return TCDTW_ERR_INVALID;
+    if (W > L - 1) W = L - 1;
+    if ((double)M * (double)N >= 4.29e9) return TCDTW_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int sms = num_sms();
+    const int E = L * D;
+    int rc = TCDTW_OK;
+    if (which == TCDTW_LB_MV) {
+        const int64_t ldE = ((int64_t)E + 31) / 32 * 32;
+        const int64_t Mp = (M + 31) / 32 * 32;
+        float *U = nullptr, *Lo = nullptr;
+        if (cudaMalloc(&U, sizeof(float) * Mp * ldE) != cudaSuccess) return TCDTW_ERR_NOMEM;
+        if (cudaMalloc(&Lo, sizeof(float) * Mp * ldE) != cudaSuccess) { cudaFree(U); return TCDTW_ERR_NOMEM; }
+        cudaError_t e = cudaSuccess;
+        for (int64_t m0 = 0; m0 < M && e == cudaSuccess; m0 += 65535) {
+            const int64_t mc = (M - m0) < 65535 ? (M - m0) : 65535;
+            e = launch_envelope(q + m0 * E, mc, L, D, W, U + m0 * ldE, Lo + m0 * ldE, (int)ldE, s);
+        }
+        if (e == cudaSuccess) {
+            LbMvArgs mv;
+            mv.cand = c; mv.N = N; mv.E = E; mv.U = U; mv.Lo = Lo; mv.ldE = ldE; mv.Mb = (int)M; mv.lb = out;
+            mv.ldLb = N; mv.sms = sms;
+            e = launch_lb_mv(mv, s);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        rc = cuda_err(e);
+        cudaFree(U);
+        cudaFree(Lo);
+        return rc;
+    }
+    // LB_PC / LB_TI: every pair listed once, no gate (e = -1), threshold +inf
+    const int64_t P = M * N;
+    uint32_t *pairs = nullptr;
+    unsigned long long *bsf = nullptr;
+    float *aux1 = nullptr, *aux2 = nullptr;
+    int32_t *cnts = nullptr;
+    cudaError_t e = cudaMalloc(&pairs, sizeof(uint32_t) * P);
+    if (e == cudaSuccess) e = cudaMalloc(&bsf, sizeof(unsigned long long) * M);
+    if (e == cudaSuccess) e = launch_iota_pairs(pairs, P, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, sizeof(float) * P, s);
+    if (e == cudaSuccess) e = launch_init_block(M, bsf, nullptr, nullptr, s);
+    PairListArgs pl;
+    pl.Q = q; pl.C = c; pl.L = L; pl.D = D; pl.W = W; pl.pairs = pairs; pl.count = nullptr; pl.n_static = P;
+    pl.N = N; pl.lb = out;
+    const float rho = 1.0f;
+    if (which == TCDTW_LB_PC) {
+        const int G = (L + o.w - 1) / o.w;
+        if (e == cudaSuccess) e = cudaMalloc(&aux1, sizeof(float) * M * G * K * 2 * D);
+        if (e == cudaSuccess) e = cudaMalloc(&cnts, sizeof(int32_t) * M * G);
+        for (int64_t m0 = 0; m0 < M && e == cudaSuccess; m0 += 65535) {
+            const int64_t mc = (M - m0) < 65535 ? (M - m0) : 65535;
+            e = launch_pc_boxes(q + m0 * E, mc, L, D, W, K, o.Lq, o.w, aux1 + m0 * G * K * 2 * D, cnts + m0 * G, s);
+        }
+        if (e == cudaSuccess) e = launch_lb_pc_list(pl, aux1, cnts, K, o.w, bsf, rho, -1.0f, nullptr, P, sms, s);
+    } else {
+        if (e == cudaSuccess) e = cudaMalloc(&aux1, sizeof(float) * M * L);
+        if (e == cudaSuccess) e = cudaMalloc(&aux2, sizeof(float) * M * L);
+        if (e == cudaSuccess) e = launch_query_dq(q, M, L, D, aux1, aux2, s);
+        if (e == cudaSuccess) e = launch_lb_ti_list(pl, aux1, aux2, o.P, bsf, rho, -1.0f, nullptr, P, sms, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    rc = cuda_err(e);
+    cudaFree(pairs); cudaFree(bsf); cudaFree(aux1); cudaFree(aux2); cudaFree(cnts);
+    return rc;
+}
+
+}  // extern "C"

@@ -53,58 +53,3 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 }  // namespace tc
 
-// ---------------------------------------------------------------- host-side launchers
-// Each kernel translation unit exports plain host functions that the API file calls.
-namespace tc {
-
-struct Workspace;  // defined in api.cu
-
-// prep.cu
-cudaError_t launch_check_finite(const float *x, int64_t n, DevStatus *st, int where, cudaStream_t s);
-cudaError_t launch_envelope(const float *q, int64_t M, int L, int D, int W, float *U, float *Lo,
-                            int ldE, cudaStream_t s);
-cudaError_t launch_query_dq(const float *q, int64_t M, int L, int D, float *dq_lo, float *dq_hi,
-                            cudaStream_t s);
-cudaError_t launch_pc_boxes(const float *q, int64_t M, int L, int D, int W, int K, int Lq, int w,
-                            float *boxes, int32_t *counts, cudaStream_t s);
-
-// lb.cu
-struct LbMvArgs {
-    const float *cand;    // [N][E]   (E = L*D)
-    int64_t N;
-    int E;                // elements per series
-    const float *U;       // [Mb][ldE] envelope upper (padded with +inf)
-    const float *Lo;      // [Mb][ldE] envelope lower (padded with -inf)
-    int ldE;              // padded row stride of U/Lo (multiple of 32)
-    int Mb;               // queries in the block
-    float *lb;            // [Mb][ldLb] output, rounded down
-    int64_t ldLb;
-};
-cudaError_t launch_lb_mv(const LbMvArgs &a, const void *tmap /* CUtensorMap or null */,
-                         cudaStream_t s);
-bool lb_mv_can_tma(const float *cand, int64_t N, int E);
-cudaError_t make_lb_mv_tmap(const float *cand, int64_t N, int E, void *tmap_out /*128B*/);
-
-// Tight bounds for listed pairs (query m, candidate n) -> out[e] (rounded down).
-struct PairListArgs {
-    const float *Q;       // [Mb][L][D]
-    const float *C;       // [N][L][D]
-    int L, D, W;
-    const uint32_t *pairs;   // entry e: m * N + n
-    const int32_t *count;    // device count of entries (or null: use n_static)
-    int64_t n_static;
-    int64_t N;
-    float *lb;               // in/out per entry
-};
-cudaError_t launch_lb_pc_list(const PairListArgs &a, const float *boxes, const int32_t *counts,
-                              int K, int w, int G, const unsigned long long *bsf, float rho,
-                              const float *e_gate, float *lb_mv_in, cudaStream_t s);
-cudaError_t launch_lb_ti_list(const PairListArgs &a, const float *dq_lo, const float *dq_hi, int P,
-                              const unsigned long long *bsf, float rho, const float *e_gate,
-                              float *lb_mv_in, cudaStream_t s);
-
-cudaError_t launch_compact_rows(const float *lb, int64_t M, int64_t N, int64_t ldLb,
-                                const float *thresh, int32_t *out_idx, int64_t ldOut, int32_t *count,
-                                cudaStream_t s);
-
-}  // namespace tc

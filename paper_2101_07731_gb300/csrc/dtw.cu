@@ -284,12 +284,12 @@ template <int R, int DMAX>
 __global__ void __launch_bounds__(128) k_dtw_nn(const float *__restrict__ Q, const float *__restrict__ Cand,
                                                  int L, int D, int W, int G, int64_t N,
                                                  const uint32_t *__restrict__ pairs, const float *__restrict__ lb,
-                                                 const int32_t *__restrict__ count, int *__restrict__ cursor,
+                                                 const int32_t *__restrict__ count, int n_static, int *__restrict__ cursor,
                                                  unsigned long long *bsf, float rho, float *__restrict__ dtw,
                                                  unsigned long long *__restrict__ counters /* started, abandoned, cells, pruned */) {
     Grp g = make_grp(G);
     const int nv = (L + R - 1) / R;
-    const int n_entries = *count;
+    const int n_entries = count ? *count : n_static;
     unsigned long long started = 0, aband = 0, ncells = 0, pruned = 0;
     for (;;) {
         int e = 0;
@@ -297,11 +297,15 @@ __global__ void __launch_bounds__(128) k_dtw_nn(const float *__restrict__ Q, con
         e = __shfl_sync(g.mask, e, (threadIdx.x & 31) & ~(G - 1));  // from the group's first lane
         if (e >= n_entries) break;
         const uint32_t pid = pairs[e];
+        if (pid == 0xffffffffu) {
+            if (g.lig == 0) dtw[e] = TC_INF;
+            continue;
+        }
         const int m = (int)(pid / (uint32_t)N);
         const int64_t n = (int64_t)(pid - (uint32_t)m * (uint32_t)N);
-        const float lbe = lb[e];
+        const float lbe = lb ? lb[e] : 0.f;
         const float thr = prune_threshold(ld_volatile_u64(bsf + m), rho);
-        if (!(lbe <= thr)) {
+        if (!(lbe <= thr) || lbe == TC_INF) {
             if (g.lig == 0) { dtw[e] = TC_INF; if (lbe != TC_INF) ++pruned; }
             continue;
         }
@@ -500,7 +504,7 @@ struct TileKernels {
         return cudaGetLastError();
     }
     static cudaError_t nn(dim3 grid, dim3 block, cudaStream_t s, const DtwNnArgs &x) {
-        k_dtw_nn<R, DMAX><<<grid, block, 0, s>>>(x.Q, x.C, x.L, x.D, x.W, x.G, x.N, x.pairs, x.lb, x.count, x.cursor,
+        k_dtw_nn<R, DMAX><<<grid, block, 0, s>>>(x.Q, x.C, x.L, x.D, x.W, x.G, x.N, x.pairs, x.lb, x.count, x.n_static, x.cursor,
                                                  x.bsf, x.rho, x.dtw, x.counters);
         return cudaGetLastError();
     }

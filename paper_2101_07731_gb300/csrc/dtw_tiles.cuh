@@ -33,7 +33,8 @@ struct DtwNnArgs {
     int64_t N;
     const uint32_t *pairs; // entry -> m*N + n
     const float *lb;       // entry -> best lower bound (+inf = pruned)
-    const int32_t *count;  // number of entries
+    const int32_t *count;  // number of entries (device), or null: n_static
+    int n_static;
     int *cursor;           // work counter (zeroed before launch)
     unsigned long long *bsf;  // [Mb] packed best-so-far
     float rho;

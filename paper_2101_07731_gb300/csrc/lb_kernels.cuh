@@ -1,0 +1,86 @@
+// lb_kernels.cuh -- launch records and launchers of the preparation, lower-bound,
+// compaction and selection kernels (prep.cu, lb.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace tc {
+
+// prep.cu
+cudaError_t launch_check_finite(const float *x, int64_t n, DevStatus *st, int where, cudaStream_t s);
+cudaError_t launch_envelope(const float *q, int64_t M, int L, int D, int W, float *U, float *Lo, int ldE,
+                            cudaStream_t s);
+cudaError_t launch_query_dq(const float *q, int64_t M, int L, int D, float *dq_lo, float *dq_hi, cudaStream_t s);
+size_t pc_boxes_smem(int L, int D, int W, int K, int w, int *npow2_out);
+cudaError_t launch_pc_boxes(const float *q, int64_t M, int L, int D, int W, int K, int Lq, int w, float *boxes,
+                            int32_t *counts, cudaStream_t s);
+
+// lb.cu -- LB_MV over all (query, candidate) pairs of a block
+struct LbMvArgs {
+    const float *cand;  // [N][E], E = L*D
+    int64_t N;
+    int E;
+    const float *U;     // [>=Mb][ldE] envelope, padded with +inf beyond E
+    const float *Lo;    // [>=Mb][ldE] envelope, padded with -inf beyond E
+    int64_t ldE;        // multiple of 32
+    int Mb;
+    float *lb;          // [Mb][ldLb]
+    int64_t ldLb;
+    int sms;
+};
+cudaError_t launch_lb_mv(const LbMvArgs &a, cudaStream_t s);
+
+// compaction of rows of a bound matrix against per-row thresholds
+struct CompactArgs {
+    const float *lb;
+    int64_t M, N, ldLb;
+    const float *thresh;             // [M] or null
+    const unsigned long long *bsf;   // used when thresh is null
+    float rho;
+    int32_t *counts;                 // [M]
+    int32_t *offsets;                // [M] flat-list mode, or null for per-row mode
+    int32_t *total;                  // flat-list mode
+    int64_t ldOut;                   // per-row mode: row stride of idx_out
+    uint32_t *pairs;                 // flat-list mode: m*N + n
+    float *lbs;                      // flat-list mode: bound of each entry
+    int32_t *idx_out;                // per-row mode: n
+    unsigned long long *pruned;      // optional counter of dropped entries
+};
+cudaError_t launch_compact(const CompactArgs &a, cudaStream_t s);
+cudaError_t launch_seed_topk(float *lb, int64_t M, int64_t N, int64_t ldLb, int S, uint32_t *seeds, cudaStream_t s);
+
+// tight bounds on listed pairs
+struct PairListArgs {
+    const float *Q;          // [Mb][L][D]
+    const float *C;          // [N][L][D]
+    int L, D, W;
+    const uint32_t *pairs;   // entry -> m*N + n (UINT32_MAX = empty)
+    const int32_t *count;    // device entry count, or null (n_static)
+    int64_t n_static;
+    int64_t N;
+    float *lb;               // in/out bound per entry (+inf = dropped)
+};
+cudaError_t launch_lb_pc_list(const PairListArgs &a, const float *boxes, const int32_t *counts, int K, int w,
+                              const unsigned long long *bsf, float rho, float e_gate, unsigned long long *stat_pruned,
+                              int64_t n_hint, int sms, cudaStream_t s);
+cudaError_t launch_lb_ti_list(const PairListArgs &a, const float *dq_lo, const float *dq_hi, int P,
+                              const unsigned long long *bsf, float rho, float e_gate, unsigned long long *stat_pruned,
+                              int64_t n_hint, int sms, cudaStream_t s);
+
+// refine / select
+cudaError_t launch_refine_select(const uint32_t *pairs, const float *dtw, const int32_t *count, int64_t n_static,
+                                 int64_t N, const unsigned long long *bsf, float rho, uint32_t *out,
+                                 int32_t *out_count, int64_t cap, int sms, cudaStream_t s);
+cudaError_t launch_refine_pick(const uint32_t *pairs, const double *d64, const int32_t *count, int64_t N,
+                               const unsigned long long *best64, unsigned long long *best_idx, int sms,
+                               cudaStream_t s);
+cudaError_t launch_finalize(int64_t Mb, const unsigned long long *best64, const unsigned long long *best_idx,
+                            int64_t *idx, double *dist, cudaStream_t s);
+cudaError_t launch_init_block(int64_t Mb, unsigned long long *bsf, unsigned long long *best64,
+                              unsigned long long *best_idx, cudaStream_t s);
+cudaError_t launch_count_add(unsigned long long *acc, const int32_t *v, cudaStream_t s);
+cudaError_t launch_iota_pairs(uint32_t *p, int64_t n, cudaStream_t s);
+
+}  // namespace tc

@@ -1,0 +1,116 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point
+declared in include/tcdtw.h; host-side argument validation and the host-only
+helpers behave as documented (no kernel is launched here)."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tcdtw.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2101_07731_gb300 import build as B
+    path = B.build()
+    return C.CDLL(path)
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tcdtw_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("tcdtw_build", "tcdtw_nn", "tcdtw_free", "tcdtw_dtw_pairs", "tcdtw_dtw_pairs_backward",
+                     "tcdtw_dtw_pairs_ckpt_bytes", "tcdtw_batch_nn", "tcdtw_strerror"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib._name], stdout=subprocess.PIPE, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\bT (tcdtw_[a-z_0-9]+)\b", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    for n in declared_functions():
+        assert getattr(lib, n) is not None
+
+
+def test_strerror_and_default_opts(lib):
+    lib.tcdtw_strerror.restype = C.c_char_p
+    assert lib.tcdtw_strerror(0) == b"ok"
+    assert b"invalid" in lib.tcdtw_strerror(1)
+    assert b"non-finite" in lib.tcdtw_strerror(5)
+    import paper_2101_07731_gb300 as tc
+    o = tc.default_opts()
+    assert (o.P, o.Lq, o.w, o.use_pc, o.use_ti, o.seed_s, o.check_finite) == (5, 2, 6, 1, 1, 4, 1)
+    assert abs(o.e_pc - 0.1) < 1e-7 and abs(o.e_ti - 0.1) < 1e-7
+
+
+def test_tile_table(lib):
+    n = lib.tcdtw_tile_count()
+    assert n >= 8
+    R, D = C.c_int32(), C.c_int32()
+    seen = set()
+    for t in range(n):
+        assert lib.tcdtw_tile_info(t, None, C.byref(R), C.byref(D)) == 0
+        assert R.value >= 1 and D.value >= 1
+        seen.add(D.value)
+    assert max(seen) >= 64
+    assert lib.tcdtw_tile_info(n, None, C.byref(R), C.byref(D)) == 1
+
+
+def test_ckpt_bytes_formula(lib):
+    b = C.c_int64()
+    # one band row (2W+1 floats) per 48 rows, except after the last segment
+    assert lib.tcdtw_dtw_pairs_ckpt_bytes(C.c_int64(1024), 512, 8, 51, C.byref(b)) == 0
+    n_seg = -(-512 // 48)
+    assert b.value == 1024 * (n_seg - 1) * 103 * 4
+    assert lib.tcdtw_dtw_pairs_ckpt_bytes(C.c_int64(3), 10, 2, 50, C.byref(b)) == 0   # W clamped to L-1
+    assert b.value == 0
+    assert lib.tcdtw_dtw_pairs_ckpt_bytes(C.c_int64(3), 0, 2, 5, C.byref(b)) == 1
+
+
+def test_host_validation_rejects_bad_shapes_without_touching_the_gpu(lib):
+    P = C.c_void_p
+    lib.tcdtw_dtw_pairs.argtypes = [P, P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, P, P, C.c_int64, P]
+    dummy = P(16)
+    assert lib.tcdtw_dtw_pairs(dummy, dummy, 4, 0, 3, 2, dummy, None, 0, None) == 1      # L < 1
+    assert lib.tcdtw_dtw_pairs(dummy, dummy, 4, 8, 0, 2, dummy, None, 0, None) == 1      # D < 1
+    assert lib.tcdtw_dtw_pairs(dummy, dummy, 4, 8, 3, -1, dummy, None, 0, None) == 1     # W < 0
+    assert lib.tcdtw_dtw_pairs(None, dummy, 4, 8, 3, 2, dummy, None, 0, None) == 1       # null
+    assert lib.tcdtw_dtw_pairs(dummy, dummy, 0, 8, 3, 2, dummy, None, 0, None) == 0      # nothing to do
+    assert lib.tcdtw_dtw_pairs(dummy, dummy, 4, 8, 65, 2, dummy, None, 0, None) == 6     # D > max
+    lib.tcdtw_build.argtypes = [P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, P, C.POINTER(P)]
+    h = P()
+    assert lib.tcdtw_build(dummy, 0, 8, 3, 2, 4, None, None, C.byref(h)) == 1             # N < 1
+    assert lib.tcdtw_build(dummy, 10, 8, 3, 2, 0, None, None, C.byref(h)) == 1            # K < 1
+    assert lib.tcdtw_build(None, 10, 8, 3, 2, 4, None, None, C.byref(h)) == 1             # null
+    assert h.value is None
+    lib.tcdtw_nn.argtypes = [P, P, C.c_int64, P, P, P, P]
+    assert lib.tcdtw_nn(None, dummy, 3, dummy, dummy, None, None) == 1
+    lib.tcdtw_pc_boxes.argtypes = [P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                   C.c_int32, P, P, P]
+    assert lib.tcdtw_pc_boxes(dummy, 2, 64, 64, 4, 8, 3, 6, dummy, dummy, None) == 1     # 3^64 overflows
+    lib.tcdtw_batch_nn.argtypes = [P, C.c_int32, P, P, P]
+    assert lib.tcdtw_batch_nn(None, 2, None, None, None) == 1
+    assert lib.tcdtw_batch_nn(None, 0, None, None, None) == 0
+
+
+def test_product_path_has_no_cpu_fallback():
+    """The package refuses CPU tensors instead of computing on the host."""
+    import torch
+    import paper_2101_07731_gb300 as tc
+    x = torch.zeros(2, 8, 3)
+    with pytest.raises(ValueError, match="CUDA"):
+        tc.dtw_pairs(x, x, 2)
+    with pytest.raises(ValueError, match="CUDA"):
+        tc.Index(x, 2)
+    src = open(os.path.join(ROOT, "paper_2101_07731_gb300", "__init__.py")).read()
+    assert "import oracle" not in src and "from oracle" not in src

@@ -1,0 +1,224 @@
+"""GPU parity of the search pipeline against the FP64 oracle, stage by stage and
+end to end.
+
+Bars: envelopes, LB_PC boxes, box counts and compaction are bit-exact; lower
+bounds are rounded down (never above the FP64 bound, never above the FP64 DTW) and
+within 1e-5 relative of it, or of the directed-rounding error bound where that is
+larger (see _lb_rtol); NN indices are bit-exact (ties to the smallest index)
+and distances within 1e-5 relative of FP64.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+tc = pytest.importorskip("paper_2101_07731_gb300")
+DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
+RTOL = 1e-5
+
+
+def _gpu(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+
+
+def _set(kind, M, N, L, D, seed, n_proto=5, sigma=0.1):
+    spec = synth.SeriesSpec(kind, L, D, seed, n_proto=n_proto, sigma=sigma)
+    return synth.generate(spec, synth.ROLE_QUERY, M), synth.generate(spec, synth.ROLE_CAND, N)
+
+
+# ------------------------------------------------------------------ stages
+
+@pytest.mark.parametrize("M,L,D,W", [(5, 70, 3, 7), (3, 257, 5, 26), (2, 40, 12, 0), (2, 33, 2, 100),
+                                     (4, 1, 3, 0), (2, 300, 32, 30)])
+def test_envelope_bit_exact(M, L, D, W):
+    Q, _ = _set("random_walk", M, 1, L, D, 11)
+    U, Lo = tc.envelope(_gpu(Q), W)
+    U, Lo = U.cpu().numpy(), Lo.cpu().numpy()
+    for m in range(M):
+        rU, rL = O.envelope(Q[m], W)
+        assert np.array_equal(U[m].astype(np.float64), rU)
+        assert np.array_equal(Lo[m].astype(np.float64), rL)
+
+
+def test_query_dq_interval_contains_exact():
+    Q, _ = _set("random_walk", 4, 1, 97, 6, 12)
+    lo, hi = tc.query_dq(_gpu(Q))
+    lo, hi = lo.cpu().numpy().astype(np.float64), hi.cpu().numpy().astype(np.float64)
+    for m in range(4):
+        ref = O.query_dq(Q[m])
+        assert np.all(lo[m] <= ref) and np.all(ref <= hi[m])
+        np.testing.assert_allclose(lo[m], ref, rtol=1e-6)
+        np.testing.assert_allclose(hi[m], ref, rtol=1e-6)
+
+
+@pytest.mark.parametrize("L,D,W,K,Lq,w", [(64, 3, 5, 4, 2, 6), (256, 5, 26, 16, 2, 6), (100, 4, 9, 3, 3, 4),
+                                          (50, 2, 60, 8, 2, 1), (90, 32, 10, 64, 2, 6), (30, 6, 3, 1, 2, 6)])
+def test_pc_boxes_bit_exact(L, D, W, K, Lq, w):
+    Q, _ = _set("proto_warp", 3, 1, L, D, 13)
+    boxes, counts = tc.pc_boxes(_gpu(Q), W, K, Lq, w)
+    boxes, counts = boxes.cpu().numpy(), counts.cpu().numpy()
+    for m in range(3):
+        rb, rc = O.pc_boxes(Q[m], W, K, Lq, w)
+        assert np.array_equal(counts[m], rc)
+        for g in range(len(rc)):
+            assert np.array_equal(boxes[m, g, :rc[g]].astype(np.float64), rb[g, :rc[g]])
+
+
+def _lb_rtol(L, D):
+    """Closeness bar for a rounded-down bound: every operation rounds the same
+    way, so errors add up instead of cancelling.  The longest chain of round-down
+    operations feeding one bound is at most D (one point's terms) + 32 (one chunk or
+    one lane's points) + L*D/32 (chunk sums) + 8 (warp reduction, sqrt), each
+    costing at most 2^-23 relative; 1e-5 is the floor."""
+    return max(1e-5, (D + 32 + (L * D + 31) // 32 + 8) * 2.0 ** -23)
+
+
+@pytest.mark.parametrize("which", [tc.LB_MV, tc.LB_PC, tc.LB_TI])
+@pytest.mark.parametrize("L,D,W", [(64, 3, 6), (129, 5, 13), (50, 8, 0), (40, 2, 60), (70, 33, 7)])
+def test_lower_bounds_rounded_down_and_close(which, L, D, W):
+    Q, Cn = _set("proto_warp", 4, 37, L, D, 14)
+    K = 8
+    out = tc.lower_bounds(_gpu(Q), _gpu(Cn), W, which=which, K=K).cpu().numpy().astype(np.float64)
+    for m in range(4):
+        for n in range(37):
+            if which == tc.LB_MV:
+                ref = O.lb_mv(Q[m], Cn[n], W)
+            elif which == tc.LB_PC:
+                ref = O.lb_pc(Q[m], Cn[n], W, K, 2, 6)
+            else:
+                ref = O.lb_ti(Q[m], Cn[n], W, 5)
+            g = out[m, n]
+            assert g <= ref * (1 + 1e-12) + 1e-30, (m, n, g, ref)
+            assert g >= ref * (1 - _lb_rtol(L, D)) - 1e-6, (m, n, g, ref)
+    # never above the DTW distance
+    for m in range(2):
+        for n in range(10):
+            assert out[m, n] <= O.dtw(Q[m], Cn[n], W) * (1 + 1e-12)
+
+
+def test_lower_bounds_large_ragged_lb_mv():
+    # several CTA tiles of candidates and queries, E = L*D not a multiple of 32 or of 4
+    Q, Cn = _set("random_walk", 45, 300, 67, 3, 15)
+    out = tc.lower_bounds(_gpu(Q), _gpu(Cn), 6, which=tc.LB_MV).cpu().numpy().astype(np.float64)
+    for m in (0, 17, 44):
+        for n in (0, 127, 128, 299):
+            ref = O.lb_mv(Q[m], Cn[n], 6)
+            assert out[m, n] <= ref * (1 + 1e-12) and out[m, n] >= ref * (1 - _lb_rtol(67, 3)) - 1e-6
+
+
+def test_compact_bit_exact():
+    rng = np.random.default_rng(0)
+    lb = rng.random((7, 1000)).astype(np.float32)
+    lb[3, :] = np.inf
+    thr = np.array([0.1, 0.5, 0.0, 1.0, 2.0, 0.25, 0.999], np.float32)
+    idx, cnt = tc.compact(_gpu(lb), _gpu(thr))
+    idx, cnt = idx.cpu().numpy(), cnt.cpu().numpy()
+    for m in range(7):
+        ref = np.nonzero(lb[m] <= thr[m])[0]
+        assert cnt[m] == len(ref)
+        assert np.array_equal(idx[m, :cnt[m]], ref)
+
+
+# ------------------------------------------------------------------ end to end
+
+def _check_nn(Q, Cn, W, K=16, **opts):
+    index = tc.Index(_gpu(Cn), W, K, **opts)
+    idx, dist, st = index.nn(_gpu(Q), stats=True)
+    index.close()
+    ridx, rdist = O.nn_brute(Q, Cn, W)
+    gi, gd = idx.cpu().numpy(), dist.cpu().numpy()
+    assert np.array_equal(gi, ridx), np.nonzero(gi != ridx)
+    np.testing.assert_allclose(gd, rdist, rtol=RTOL, atol=0)
+    M, N = len(Q), len(Cn)
+    assert st["pairs"] == M * N
+    assert st["pruned_mv"] + st["pruned_pc"] + st["pruned_ti"] + st["dtw_started"] == st["pairs"], st
+    assert st["refined"] >= M
+    return gd, rdist, st
+
+
+def test_nn_rw_16x256_L128_D3_W13_exact():
+    wl = synth.RW_16x256_L128
+    gd, rd, st = _check_nn(wl.queries(), wl.candidates(), wl.W, wl.K)
+    # the refined distances are the FP64 values themselves
+    assert np.array_equal(gd, rd)
+
+
+@pytest.mark.parametrize("use_pc,use_ti", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_nn_proto_warp_cascade_settings(use_pc, use_ti):
+    Q, Cn = _set("proto_warp", 24, 1500, 96, 4, 21, n_proto=6)
+    _check_nn(Q, Cn, 10, 8, use_pc=use_pc, use_ti=use_ti, e_pc=0.0, e_ti=0.0)
+
+
+@pytest.mark.parametrize("seed_s,qblock", [(1, 7), (8, 0), (3, 32)])
+def test_nn_query_blocks_and_seeds(seed_s, qblock):
+    Q, Cn = _set("proto_warp", 50, 700, 64, 3, 22)
+    _check_nn(Q, Cn, 6, 8, seed_s=seed_s, qblock=qblock)
+
+
+@pytest.mark.parametrize("M,N,L,D,W", [(1, 1, 16, 2, 3), (3, 5, 1, 3, 0), (4, 9, 20, 1, 0), (5, 40, 30, 2, 100),
+                                       (2, 300, 50, 12, 5), (2, 80, 40, 32, 4), (2, 60, 24, 64, 3)])
+def test_nn_edge_shapes(M, N, L, D, W):
+    Q, Cn = _set("random_walk", M, N, L, D, 23)
+    _check_nn(Q, Cn, W, 4)
+
+
+def test_nn_duplicates_tie_to_smallest_index():
+    _, Cn = _set("random_walk", 1, 64, 40, 3, 24)
+    Cn = np.concatenate([Cn, Cn[[10, 5, 10]]])          # copies at 64, 65, 66
+    Q = (Cn[[10, 5, 33]] + np.float32(0.01)).astype(np.float32)
+    index = tc.Index(_gpu(Cn), 4, 4)
+    idx, dist = index.nn(_gpu(Q))
+    assert idx.cpu().tolist() == [10, 5, 33]
+    # the query equal to a candidate: distance 0, smallest duplicate index
+    idx2, dist2 = index.nn(_gpu(Cn[[65, 66]]))
+    assert idx2.cpu().tolist() == [5, 10] and dist2.cpu().tolist() == [0.0, 0.0]
+
+
+def test_nn_constant_series():
+    Cn = np.zeros((20, 32, 3), np.float32)
+    Cn[7] += 1.0
+    Q = np.zeros((2, 32, 3), np.float32)
+    Q[1] += 0.9
+    index = tc.Index(_gpu(Cn), 3, 4)
+    idx, dist = index.nn(_gpu(Q))
+    assert idx.cpu().tolist() == [0, 7]
+
+
+def test_nn_rejects_non_finite():
+    Q, Cn = _set("random_walk", 2, 30, 20, 2, 25)
+    Cbad = Cn.copy()
+    Cbad[3, 4, 1] = np.nan
+    with pytest.raises(tc.TcdtwError) as ei:
+        tc.Index(_gpu(Cbad), 3, 4)
+    assert ei.value.code == 5
+    index = tc.Index(_gpu(Cn), 3, 4)
+    Qbad = Q.copy()
+    Qbad[1, 0, 0] = np.inf
+    with pytest.raises(tc.TcdtwError) as ei:
+        index.nn(_gpu(Qbad))
+    assert ei.value.code == 5
+    # the index stays usable
+    idx, _ = index.nn(_gpu(Q))
+    ridx, _ = O.nn_brute(Q, Cn, 3)
+    assert np.array_equal(idx.cpu().numpy(), ridx)
+
+
+def test_nn_proto_256x20000_L256_D5_W26_sampled():
+    """The full 256 x 20,000 search (L=256, D=5, W=26, K=16); the oracle checks a
+    sample of 24 queries by brute force over all 20,000 candidates."""
+    wl = synth.PROTO_256x20000_L256
+    Q, Cn = wl.queries(), wl.candidates()
+    index = tc.Index(_gpu(Cn), wl.W, wl.K)
+    idx, dist, st = index.nn(_gpu(Q), stats=True)
+    gi, gd = idx.cpu().numpy(), dist.cpu().numpy()
+    sample = np.random.default_rng(3).choice(wl.M, 24, replace=False)
+    ridx, rdist = O.nn_brute(Q[sample], Cn, wl.W)
+    assert np.array_equal(gi[sample], ridx)
+    np.testing.assert_allclose(gd[sample], rdist, rtol=RTOL, atol=0)
+    assert st["pruned_mv"] + st["pruned_pc"] + st["pruned_ti"] + st["dtw_started"] == st["pairs"]
+    # pruning must avoid most DTWs on this prototype data
+    assert st["dtw_started"] < 0.5 * st["pairs"]
