@@ -1,0 +1,385 @@
+"""Benchmark of exact DTW 1-NN search on GB300 (one JSON line on stdout).
+
+A step is one exact nearest-neighbour search of a batch of 256 queries against
+20,000 resident candidates (L=256, D=5, Sakoe-Chiba W=26, LB_PC K=16; seeded
+prototype-warp data): envelopes, LB_MV, seeds, compaction, gated LB_PC / LB_TI,
+abandoning DTW and FP64 refine -- the whole hot path, all in the library's
+kernels.  The value is whole-job queries/s; the L2 is flushed between timed steps
+(the candidate set, 102 MB, would otherwise stay resident in the 129 MB L2).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank searches its own replica of the batch (weak
+scaling, no collective on the data path); the slowest rank's time counts.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "NN queries/s & DTW cell-updates/s at exact NN; % of HBM/FP32 roofline"
+WORKLOAD = synth.PROTO_256x20000_L256
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_COUNT_NOMINAL = 152
+FP32_LANES_PER_SM = 128
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-extra", action="store_true", help="skip the unpruned and end-to-end legs")
+    return ap.parse_args()
+
+
+def _dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _config(extra=None):
+    wl = WORKLOAD
+    c = {"workload": wl.name, "M": wl.M, "N": wl.N, "L": wl.spec.L, "D": wl.spec.D, "W": wl.W, "K": wl.K,
+         "generator": "prototype-warp, 20 prototypes, sigma 0.1, z-normalised, seed 0",
+         "l2": "flushed between timed steps (256 MB write)", "parallelism": "replicas"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ----------------------------------------------------------------- CPU oracle legs
+
+def cpu_oracle_sample(Q, Cn, W, K, target_s):
+    """The paper's pruned search (FP64 oracle, OpenMP over queries) on a bounded
+    sample of queries sized for about target_s seconds; returns (queries/s, cores,
+    sample description, seconds)."""
+    import oracle
+    cores = oracle.num_threads()
+    n = min(len(Q), max(cores, 16))
+    t0 = time.perf_counter()
+    oracle.nn_pruned(Q[:n], Cn, W, K=K)
+    t = time.perf_counter() - t0
+    if t < target_s * 0.5 and n < len(Q):
+        n2 = int(min(len(Q), max(n + 1, n * target_s / max(t, 1e-3))))
+        t0 = time.perf_counter()
+        oracle.nn_pruned(Q[:n2], Cn, W, K=K)
+        t = time.perf_counter() - t0
+        n = n2
+    return n / t, cores, f"{n} of {len(Q)} queries x all {len(Cn)} candidates (pruned FP64 search)", t
+
+
+def cpu_brute_sample(Q, Cn, W, n):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.nn_brute(Q[:n], Cn, W)
+    return n / (time.perf_counter() - t0)
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------- roofline helpers
+
+def _peaks():
+    try:
+        return json.load(open(PEAKS_FILE))
+    except (OSError, ValueError):
+        return {}
+
+
+def _profile_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary of `kernel`, if the
+    kernel source has not changed since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", f"ncu_{kernel}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    h = re.search(r"source_sha256:\s*([0-9a-f]+)", text)
+    src = re.search(r"source_file:\s*(\S+)", text)
+    if not (m and h and src):
+        return None
+    try:
+        cur = hashlib.sha256(open(os.path.join(ROOT, src.group(1)), "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return float(m.group(1)) if cur.startswith(h.group(1)) else None
+
+
+# ----------------------------------------------------------------- our arm
+
+def run_ours(a):
+    import torch
+    world, rank, local = _dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2101_07731_gb300 as tc
+
+    wl = WORKLOAD
+    Qn, Cn = wl.queries(), wl.candidates()
+    cand = torch.from_numpy(Cn).to(dev)
+    q = torch.from_numpy(Qn).to(dev)
+    index = tc.Index(cand, wl.W, wl.K)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(a.warmup):
+        index.nn(q)
+    torch.cuda.synchronize()
+    _, _, st = index.nn(q, stats=True)
+
+    # ---- timed region: K device-resident steps, L2 flushed between them
+    index.set_profiling(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    launches0 = tc.kernel_launches()
+    with ClockSampler(local) as clocks:
+        barrier()
+        torch.cuda.synchronize()
+        for k in range(a.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            index.nn(q)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    launches = tc.kernel_launches() - launches0
+    stage_ms, n_blocks = index.stage_times()
+    index.set_profiling(False)
+    step_ms = [s.elapsed_time(e) for s, e in ev]
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms_per_step = total_ms / a.steps
+    value = world * wl.M * a.steps / (total_ms / 1e3)
+
+    # cell counts and rates
+    band = synth.band_cells(wl.spec.L, wl.W)
+    cells_full = wl.M * wl.N * band                       # full-band cells of every pair
+    dtw_ms = stage_ms["dtw"] / a.steps + stage_ms["seed"] / a.steps
+    res = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": _config({"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
+           "cell_updates_per_s": {"computed_over_dtw_time": st["cells"] / (dtw_ms / 1e3) if dtw_ms > 0 else None,
+                                  "effective_full_band_over_step": world * cells_full / (ms_per_step / 1e3)},
+           "pruning": {"pairs": st["pairs"], "dtw_started": st["dtw_started"],
+                       "rate": 1.0 - st["dtw_started"] / st["pairs"], "pruned_mv": st["pruned_mv"],
+                       "pruned_pc": st["pruned_pc"], "pruned_ti": st["pruned_ti"],
+                       "dtw_abandoned": st["dtw_abandoned"], "cells": st["cells"], "refined": st["refined"]},
+           "stage_ms_per_step": {k: v / a.steps for k, v in stage_ms.items()},
+           "gpu_launches": int(launches)}
+    res["clocks"] = clocks.summary()
+
+    # ---- roofline of the dominant stage
+    peaks = _peaks()
+    dom = max(stage_ms, key=stage_ms.get)
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = n_sm * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12      # T FP32 lane-instr/s
+    D = wl.spec.D
+    per = stage_ms[dom] / a.steps / 1e3                            # seconds per step
+    if dom == "lb_mv":
+        instr = wl.M * wl.N * wl.spec.L * D * 4.0                  # clamp(2) + sub + fma per element
+        kern = "k_lb_mv"
+    elif dom in ("dtw", "seed"):
+        instr = st["cells"] * (2.0 * D + 3.0)                     # D sub + D fma + 2 min + add per cell
+        kern = "k_dtw_nn"
+        per = (stage_ms["dtw"] + stage_ms["seed"]) / a.steps / 1e3
+    else:
+        instr, kern = None, dom
+    if instr is not None:
+        ach = instr / per / 1e12
+        res["roofline"] = {"bound": "alu", "kernel": kern, "achieved": ach, "peak": alu_peak, "unit": "Tinstr/s",
+                           "frac": ach / alu_peak, "traffic": _profile_traffic(kern),
+                           "peak_note": f"{n_sm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (max clock), "
+                                        "algorithmic FP32 instructions of the stage / its event time"}
+    # the LB_MV stream against HBM for reference: bytes = candidates read per query tile pass
+    if "lb_mv" in stage_ms and stage_ms["lb_mv"] > 0:
+        qtiles = -(-wl.M // 32)
+        bytes_mv = wl.N * wl.spec.L * D * 4.0 * qtiles
+        hbm = peaks.get("hbm_gbs", 6790.0)
+        res["lb_mv_hbm"] = {"achieved_gbs": bytes_mv / (stage_ms["lb_mv"] / a.steps / 1e3) / 1e9, "peak_gbs": hbm,
+                            "frac": bytes_mv / (stage_ms["lb_mv"] / a.steps / 1e3) / 1e9 / hbm,
+                            "note": "candidate bytes of all query-tile passes; most are L2 hits"}
+
+    if not a.no_extra:
+        # ---- unpruned GPU DTW (every pair, no bounds, no abandoning)
+        raw = tc.Index(cand, wl.W, wl.K, no_prune=1)
+        raw.nn(q)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 2
+        e0.record(stream)
+        for _ in range(reps):
+            ri, rd = raw.nn(q)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        raw_ms = e0.elapsed_time(e1) / reps
+        idx, _ = index.nn(q)
+        assert torch.equal(idx, ri), "unpruned and pruned searches disagree"
+        raw.close()
+        res["unpruned_gpu"] = {"ms_per_step": raw_ms, "queries_per_s": wl.M / (raw_ms / 1e3),
+                               "cell_updates_per_s": cells_full / (raw_ms / 1e3),
+                               "speedup_of_pruning": raw_ms / ms_per_step}
+        # ---- end to end through the public API, host buffers, copies in the timed region
+        qh = torch.from_numpy(Qn).pin_memory()
+        idx_h = torch.empty(wl.M, dtype=torch.int64).pin_memory()
+        dist_h = torch.empty(wl.M, dtype=torch.float64).pin_memory()
+        qd = torch.empty_like(q)
+        for _ in range(2):
+            qd.copy_(qh, non_blocking=True)
+            i2, d2 = index.nn(qd)
+            idx_h.copy_(i2, non_blocking=True)
+            dist_h.copy_(d2, non_blocking=True)
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(a.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            qd.copy_(qh, non_blocking=True)
+            i2, d2 = index.nn(qd)
+            idx_h.copy_(i2, non_blocking=True)
+            dist_h.copy_(d2, non_blocking=True)
+            s1.record(stream)
+            s1.synchronize()
+            tot += s0.elapsed_time(s1)
+        res["e2e"] = {"value": world * wl.M * a.steps / (tot / 1e3), "unit": "queries/s",
+                      "h2d_bytes_per_step": int(qh.numel() * 4), "d2h_bytes_per_step": int(wl.M * 16)}
+    index.close()
+
+    if rank == 0 and world == 1 and not a.no_cpu:
+        qps, cores, sample, secs = cpu_oracle_sample(Qn, Cn, wl.W, wl.K, a.cpu_seconds)
+        res["cpu_baseline"] = {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                               "sample": sample, "seconds": secs}
+        nb = max(cores, 4)
+        res["cpu_bruteforce"] = {"value": cpu_brute_sample(Qn, Cn, wl.W, nb), "unit": "queries/s", "cores": cores,
+                                 "sample": f"{nb} queries x all candidates, FP64 DTW of every pair"}
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------- reference arm
+
+def run_reference(a):
+    """The oracle (the paper's pruned search in FP64, OpenMP) timed on the host
+    cores, on the same workload and metric; each step is a bounded sample of
+    queries against all candidates."""
+    world, rank, _ = _dist_env()
+    if rank != 0:
+        return
+    import oracle
+    wl = WORKLOAD
+    Qn, Cn = wl.queries(), wl.candidates()
+    cores = oracle.num_threads()
+    n = max(cores, 8)
+    for k in range(a.warmup):
+        oracle.nn_pruned(Qn[:n], Cn, wl.W, K=wl.K)
+    t0 = time.perf_counter()
+    for k in range(a.steps):
+        lo = (k * n) % (wl.M - n + 1)
+        oracle.nn_pruned(Qn[lo:lo + n], Cn, wl.W, K=wl.K)
+    secs = time.perf_counter() - t0
+    value = n * a.steps / secs
+    res = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": secs / a.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": _config({"parallelism": "host cores (OpenMP)"}),
+           "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                            "sample": f"{n} queries x all {wl.N} candidates per step (pruned FP64 search)"},
+           "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)

@@ -63,6 +63,9 @@ typedef struct tcdtw_index tcdtw_index; /* opaque; created by tcdtw_build */
  *  qblock  queries per pipeline block (0 = chosen from free memory).
  *  tile    DTW band-tile id (-1 = autotuned; see tcdtw_tile_count()).
  *  check_finite  1 = scan inputs and fail with TCDTW_ERR_NONFINITE on NaN/Inf (1).
+ *  no_prune  1 = the "default windowed DTW without lower bounds" the paper measures
+ *          its speedups against (Section 7.2): the full DTW of every pair, no bound,
+ *          no abandoning; the answer is the same (0).
  */
 typedef struct {
     int32_t P;
@@ -76,6 +79,7 @@ typedef struct {
     int32_t qblock;
     int32_t tile;
     int32_t check_finite;
+    int32_t no_prune;
 } tcdtw_opts;
 
 /* Counters of one tcdtw_nn call, summed over its queries. */
@@ -129,6 +133,29 @@ int tcdtw_nn(tcdtw_index *index, const float *q, int64_t M, int64_t *idx, double
 
 /* Release an index and its workspaces (NULL is accepted). */
 void tcdtw_free(tcdtw_index *index);
+
+/* The DTW band tile the index uses (autotuned at build unless opts->tile was set),
+ * its lanes per pair G, and the query block size (host outputs, each may be NULL).
+ * Errors: INVALID. */
+int tcdtw_index_info(tcdtw_index *index, int32_t *tile, int32_t *G, int32_t *qblock);
+
+/*
+ * Per-stage timing of tcdtw_nn (tracing; not in the paper).  With profiling on,
+ * every query block records CUDA events on the caller's stream at the stage
+ * boundaries below and tcdtw_nn synchronises at its end to add the elapsed times.
+ * Stages: 0 non-finite scan, 1 query preparation (envelope, dq, boxes), 2 LB_MV,
+ * 3 seeds (selection and their DTW), 4 compaction, 5 LB_PC / LB_TI cascade,
+ * 6 DTW of the survivors, 7 FP64 refine and selection.
+ * tcdtw_set_profiling: enable != 0 turns it on; either way the totals are reset.
+ * tcdtw_stage_times: host ms[TCDTW_NUM_STAGES] receives the summed milliseconds,
+ * host *blocks (may be NULL) the number of query blocks timed.  Errors: INVALID.
+ */
+#define TCDTW_NUM_STAGES 8
+int tcdtw_set_profiling(tcdtw_index *index, int32_t enable);
+int tcdtw_stage_times(tcdtw_index *index, double *ms, int64_t *blocks);
+
+/* Number of kernels the library has launched in this process (host counter). */
+uint64_t tcdtw_kernel_launches(void);
 
 /*
  * tcdtw_dtw_pairs -- DTW distance of P independent pairs (A[p], B[p]) (Eq. 1 in the

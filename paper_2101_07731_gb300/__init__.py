@@ -46,7 +46,7 @@ class Opts(C.Structure):
     _fields_ = [("P", C.c_int32), ("Lq", C.c_int32), ("w", C.c_int32), ("e_pc", C.c_float),
                 ("e_ti", C.c_float), ("use_pc", C.c_int32), ("use_ti", C.c_int32),
                 ("seed_s", C.c_int32), ("qblock", C.c_int32), ("tile", C.c_int32),
-                ("check_finite", C.c_int32)]
+                ("check_finite", C.c_int32), ("no_prune", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -81,6 +81,10 @@ _SIGS = {
     "tcdtw_compact": (C.c_int, [_P, _I64, _I64, _P, _P, _P, _P]),
     "tcdtw_batch_nn": (C.c_int, [C.POINTER(Dataset), _I32, C.POINTER(Opts), C.POINTER(Stats), _P]),
     "tcdtw_tile_count": (C.c_int, []),
+    "tcdtw_set_profiling": (C.c_int, [_P, _I32]),
+    "tcdtw_stage_times": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(_I64)]),
+    "tcdtw_kernel_launches": (C.c_uint64, []),
+    "tcdtw_index_info": (C.c_int, [_P, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32)]),
     "tcdtw_tile_info": (C.c_int, [_I32, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32)]),
 }
 
@@ -231,6 +235,27 @@ class Index:
         _call("tcdtw_nn", self._h, _ptr(q), M, _ptr(idx), _ptr(dist), C.byref(st) if stats else None, _stream())
         return (idx, dist, st.as_dict()) if stats else (idx, dist)
 
+    def info(self):
+        """{tile, R, DM, G, qblock}: the band tile the search uses (autotuned at build)."""
+        t, g, qb = _I32(), _I32(), _I32()
+        _call("tcdtw_index_info", self._h, C.byref(t), C.byref(g), C.byref(qb))
+        r, dm = _I32(), _I32()
+        _call("tcdtw_tile_info", t.value, None, C.byref(r), C.byref(dm))
+        return {"tile": t.value, "R": r.value, "DM": dm.value, "G": g.value, "qblock": qb.value}
+
+    STAGES = ("check", "prep", "lb_mv", "seed", "compact", "cascade", "dtw", "refine")
+
+    def set_profiling(self, enable: bool = True):
+        """Record per-stage CUDA-event times in every nn() call (synchronises)."""
+        _call("tcdtw_set_profiling", self._h, int(bool(enable)))
+
+    def stage_times(self):
+        """{stage: milliseconds} summed over the profiled nn() calls, and block count."""
+        ms = (C.c_double * len(self.STAGES))()
+        nb = _I64(0)
+        _call("tcdtw_stage_times", self._h, ms, C.byref(nb))
+        return dict(zip(self.STAGES, list(ms))), int(nb.value)
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             _load().tcdtw_free(self._h)
@@ -241,6 +266,11 @@ class Index:
             self.close()
         except Exception:
             pass
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libtcdtw.so in this process so far."""
+    return int(_load().tcdtw_kernel_launches())
 
 
 def batch_nn(sets, stats: bool = False, **opts):

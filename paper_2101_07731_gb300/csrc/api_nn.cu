@@ -17,6 +17,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "api_internal.h"
 #include "common.cuh"
@@ -50,21 +51,80 @@ bool pc_key_fits(int Lq, int D) {
     return true;
 }
 
-// Smallest-R valid tile of the D bucket (FP64 refine: registers are doubled).
-bool choose_refine_tile(int D, int W, int *tile, int *G) {
+// ------------------------------------------------------------------ autotuner
+// Times every valid (tile, G) of the D bucket on a sample of real pairs (candidate k
+// against candidate k+1, full band, no abandoning) and keeps the fastest.  Results
+// are cached per (L, D, W) for the life of the process.
+struct TuneKey {
+    int L, D, W;
+    bool operator==(const TuneKey &o) const { return L == o.L && D == o.D && W == o.W; }
+};
+struct TuneVal {
+    int tile, G;
+};
+static std::vector<std::pair<TuneKey, TuneVal>> g_tune_cache;
+
+bool autotune_nn_tile(const float *cand, int64_t N, int L, int D, int W, cudaStream_t s, int *tile, int *G) {
+    const TuneKey key{L, D, W};
+    for (auto &kv : g_tune_cache)
+        if (kv.first == key) { *tile = kv.second.tile; *G = kv.second.G; return true; }
     const int dm = dmax_for(D);
-    int bestR = 1 << 30;
+    if (dm < 0) return false;
+    // enough pairs to fill every SM even with 4-lane groups (8 pairs per warp), but
+    // at most ~4e9 band cells; runs of 64 pairs share a "query" (candidate m), as the
+    // survivor lists of a search do.
+    const double band = (double)L * (2 * W + 1) - (double)W * (W + 1);
+    int64_t P = (int64_t)(4.0e9 / band);
+    if (P > 65536) P = 65536;
+    if (P < 16384) P = 16384;
+    int64_t Mq = N < 4096 ? N : 4096;
+    while (Mq > 1 && (double)Mq * (double)N >= 4.29e9) Mq >>= 1;
+    uint32_t *pairs = nullptr;
+    unsigned long long *bsf = nullptr;
+    float *dtw = nullptr;
+    int *cursor = nullptr;
+    bool ok = cudaMalloc(&pairs, sizeof(uint32_t) * P) == cudaSuccess &&
+              cudaMalloc(&bsf, sizeof(unsigned long long) * Mq) == cudaSuccess &&
+              cudaMalloc(&dtw, sizeof(float) * P) == cudaSuccess && cudaMalloc(&cursor, sizeof(int)) == cudaSuccess;
+    std::vector<uint32_t> h(P);
+    for (int64_t i = 0; i < P; ++i) {
+        const int64_t m = (i / 64) % Mq, n = (i * 7919 + 13) % N;
+        h[i] = (uint32_t)(m * N + n);
+    }
+    ok = ok && cudaMemcpyAsync(pairs, h.data(), sizeof(uint32_t) * P, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    ok = ok && launch_init_block(Mq, bsf, nullptr, nullptr, s) == cudaSuccess;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ok = ok && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+    float best = 1e30f;
     bool found = false;
-    for (int t = 0; t < kNumTiles; ++t) {
+    for (int t = 0; ok && t < kNumTiles; ++t) {
         if (kTiles[t].DMAX != dm) continue;
-        for (int g = 4; g <= 32; g *= 2) {
+        for (int g = 4; g <= 32 && ok; g *= 2) {
             if (!tile_valid(t, g, W)) continue;
-            const int cost = kTiles[t].R * 64 + g;
-            if (cost < bestR) { bestR = cost; *tile = t; *G = g; found = true; }
+            DtwNnArgs dn;
+            dn.Q = cand; dn.C = cand; dn.L = L; dn.D = D; dn.W = W; dn.G = g; dn.N = N; dn.pairs = pairs;
+            dn.lb = nullptr; dn.count = nullptr; dn.n_static = (int)P; dn.cursor = cursor; dn.bsf = bsf;
+            dn.rho = INFINITY; dn.dtw = dtw; dn.counters = nullptr;
+            int blocks = dtw_occupancy(t, 1) * num_sms();
+            if (blocks < 1) blocks = num_sms();
+            float ms_best = 1e30f;
+            for (int rep = 0; rep < 3 && ok; ++rep) {
+                ok = cudaMemsetAsync(cursor, 0, sizeof(int), s) == cudaSuccess;
+                ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
+                ok = ok && dtw_nn_launch(t, blocks, s, dn) == cudaSuccess;
+                ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+                float ms = 0.f;
+                ok = ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+                if (ok && rep > 0 && ms < ms_best) ms_best = ms;  // rep 0 warms up
+            }
+            if (ok && ms_best < best) { best = ms_best; *tile = t; *G = g; found = true; }
         }
     }
-    if (!found) return choose_tile(1, W + 1, D, W, 0, tile, G);
-    return true;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(pairs); cudaFree(bsf); cudaFree(dtw); cudaFree(cursor);
+    if (found) g_tune_cache.push_back({key, TuneVal{*tile, *G}});
+    return found;
 }
 
 template <typename T>
@@ -86,8 +146,9 @@ struct tcdtw_index {
     tcdtw_opts opts;
     int Mb = 0, Mb_pad = 0, S = 0, G_pc = 0;
     int64_t ldE = 0;
-    float rho = 1.f;
-    int tile = 0, G = 32, tile_ref = 0, G_ref = 32, sms = 1;
+    float rho = 1.f;         // pruning / abandoning factor (+inf with no_prune)
+    float rho_ref = 1.f;     // refine factor (always the rounding margin)
+    int tile = 0, G = 32, R_ref = 1, sms = 1;
     int blocks_nn = 1, blocks_ref = 1;
     // workspaces
     float *U = nullptr, *Lo = nullptr, *dq_lo = nullptr, *dq_hi = nullptr, *boxes = nullptr, *lbm = nullptr;
@@ -99,12 +160,19 @@ struct tcdtw_index {
     unsigned long long *bsf = nullptr, *best64 = nullptr, *best_idx = nullptr, *counters = nullptr;
     DevStatus *status = nullptr;
     int64_t refine_cap = 0;
+    // per-stage CUDA-event profile (tcdtw_set_profiling)
+    bool profile = false;
+    std::vector<cudaEvent_t> events;   // (TCDTW_NUM_STAGES + 1) marks per block
+    int marks_used = 0;
+    double stage_ms[TCDTW_NUM_STAGES] = {0};
+    int64_t stage_blocks = 0;
 };
 
 namespace {
 
 void free_index(tcdtw_index *x) {
     if (!x) return;
+    for (cudaEvent_t ev : x->events) cudaEventDestroy(ev);
     void *ptrs[] = {x->U, x->Lo, x->dq_lo, x->dq_hi, x->boxes, x->lbm, x->box_counts, x->seeds, x->surv,
                     x->refine, x->seed_dtw, x->surv_lb, x->surv_dtw, x->refine_d64, x->row_counts,
                     x->row_offsets, x->scalars, x->bsf, x->best64, x->best_idx, x->counters, x->status};
@@ -158,6 +226,26 @@ int alloc_index(tcdtw_index *x) {
     return TCDTW_OK;
 }
 
+// Stage boundary k of the current block (profiling only).
+cudaError_t mark(tcdtw_index *x, int k, cudaStream_t s) {
+    if (!x->profile) return cudaSuccess;
+    const size_t slot = (size_t)x->marks_used;
+    if (slot >= x->events.size()) {
+        cudaEvent_t ev;
+        cudaError_t e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return e;
+        x->events.push_back(ev);
+    }
+    (void)k;
+    ++x->marks_used;
+    return cudaEventRecord(x->events[slot], s);
+}
+
+#define TC_MARK(k)                                            \
+    do {                                                      \
+        if ((e = mark(x, (k), s)) != cudaSuccess) return e;   \
+    } while (0)
+
 // One block of Mb_cur queries.  All launches on stream s; no host synchronisation.
 cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_out, double *dist_out,
                       cudaStream_t s) {
@@ -165,26 +253,34 @@ cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_o
     const int64_t N = x->N;
     const int E = L * D;
     cudaError_t e;
+    TC_MARK(0);
     if (x->opts.check_finite) {
         e = launch_check_finite(q, (int64_t)Mb_cur * E, x->status, 1, s);
         if (e != cudaSuccess) return e;
     }
+    TC_MARK(1);
     e = cudaMemsetAsync(x->scalars, 0, sizeof(int32_t) * kNumScalars, s);
     if (e != cudaSuccess) return e;
     if ((e = launch_init_block(Mb_cur, x->bsf, x->best64, x->best_idx, s)) != cudaSuccess) return e;
     // 1. query-side preparation
-    if ((e = launch_envelope(q, Mb_cur, L, D, W, x->U, x->Lo, (int)x->ldE, s)) != cudaSuccess) return e;
+    if ((e = launch_envelope_pairs(q, Mb_cur, L, D, W, x->U, x->Lo, (int)x->ldE, s)) != cudaSuccess) return e;
     if (x->opts.use_ti && (e = launch_query_dq(q, Mb_cur, L, D, x->dq_lo, x->dq_hi, s)) != cudaSuccess) return e;
     if (x->opts.use_pc &&
         (e = launch_pc_boxes(q, Mb_cur, L, D, W, x->K, x->opts.Lq, x->opts.w, x->boxes, x->box_counts, s)) !=
             cudaSuccess)
         return e;
     // 2. LB_MV of all pairs
-    LbMvArgs mv;
-    mv.cand = x->cand; mv.N = N; mv.E = E; mv.U = x->U; mv.Lo = x->Lo; mv.ldE = x->ldE; mv.Mb = Mb_cur;
-    mv.lb = x->lbm; mv.ldLb = N; mv.sms = x->sms;
-    if ((e = launch_lb_mv(mv, s)) != cudaSuccess) return e;
+    TC_MARK(2);
+    if (x->opts.no_prune) {
+        if ((e = cudaMemsetAsync(x->lbm, 0, sizeof(float) * (size_t)Mb_cur * N, s)) != cudaSuccess) return e;
+    } else {
+        LbMvArgs mv;
+        mv.cand = x->cand; mv.N = N; mv.E = E; mv.U = x->U; mv.Lo = x->Lo; mv.ldE = x->ldE; mv.Mb = Mb_cur;
+        mv.lb = x->lbm; mv.ldLb = N; mv.sms = x->sms;
+        if ((e = launch_lb_mv(mv, s)) != cudaSuccess) return e;
+    }
     // 3. seeds and their DTW
+    TC_MARK(3);
     if ((e = launch_seed_topk(x->lbm, Mb_cur, N, N, x->S, x->seeds, s)) != cudaSuccess) return e;
     DtwNnArgs dn;
     dn.Q = q; dn.C = x->cand; dn.L = L; dn.D = D; dn.W = W; dn.G = x->G; dn.N = N;
@@ -193,6 +289,7 @@ cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_o
     dn.counters = x->counters;
     if ((e = dtw_nn_launch(x->tile, x->blocks_nn, s, dn)) != cudaSuccess) return e;
     // 4. compaction against the seeded best-so-far
+    TC_MARK(4);
     CompactArgs ca;
     memset(&ca, 0, sizeof(ca));
     ca.lb = x->lbm; ca.M = Mb_cur; ca.N = N; ca.ldLb = N; ca.thresh = nullptr; ca.bsf = x->bsf; ca.rho = x->rho;
@@ -200,6 +297,7 @@ cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_o
     ca.pairs = x->surv; ca.lbs = x->surv_lb; ca.pruned = x->counters + kPrunedMv;
     if ((e = launch_compact(ca, s)) != cudaSuccess) return e;
     // 5. gated tight bounds
+    TC_MARK(5);
     PairListArgs pl;
     pl.Q = q; pl.C = x->cand; pl.L = L; pl.D = D; pl.W = W; pl.pairs = x->surv;
     pl.count = x->scalars + kSurvTotal; pl.n_static = 0; pl.N = N; pl.lb = x->surv_lb;
@@ -213,25 +311,29 @@ cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_o
                                x->counters + kPrunedTi, hint, x->sms, s)) != cudaSuccess)
         return e;
     // 6. DTW of the survivors
+    TC_MARK(6);
     dn.pairs = x->surv; dn.lb = x->surv_lb; dn.count = x->scalars + kSurvTotal; dn.n_static = 0;
     dn.cursor = x->scalars + kCursorSurv; dn.dtw = x->surv_dtw;
     if ((e = dtw_nn_launch(x->tile, x->blocks_nn, s, dn)) != cudaSuccess) return e;
     // 7. refine near-ties in FP64 and select
-    if ((e = launch_refine_select(x->seeds, x->seed_dtw, nullptr, (int64_t)Mb_cur * x->S, N, x->bsf, x->rho,
+    TC_MARK(7);
+    if ((e = launch_refine_select(x->seeds, x->seed_dtw, nullptr, (int64_t)Mb_cur * x->S, N, x->bsf, x->rho_ref,
                                   x->refine, x->scalars + kRefineCount, x->refine_cap, x->sms, s)) != cudaSuccess)
         return e;
-    if ((e = launch_refine_select(x->surv, x->surv_dtw, x->scalars + kSurvTotal, 0, N, x->bsf, x->rho, x->refine,
+    if ((e = launch_refine_select(x->surv, x->surv_dtw, x->scalars + kSurvTotal, 0, N, x->bsf, x->rho_ref, x->refine,
                                   x->scalars + kRefineCount, x->refine_cap, x->sms, s)) != cudaSuccess)
         return e;
     DtwRefineArgs rf;
-    rf.Q = q; rf.C = x->cand; rf.L = L; rf.D = D; rf.W = W; rf.G = x->G_ref; rf.N = N;
+    rf.Q = q; rf.C = x->cand; rf.L = L; rf.D = D; rf.W = W; rf.N = N;
     rf.pairs = x->refine; rf.count = x->scalars + kRefineCount; rf.d64 = x->refine_d64; rf.best64 = x->best64;
-    if ((e = dtw_refine_launch(x->tile_ref, x->blocks_ref, s, rf)) != cudaSuccess) return e;
+    if ((e = dtw_refine_launch(x->R_ref, x->blocks_ref, s, rf)) != cudaSuccess) return e;
     if ((e = launch_refine_pick(x->refine, x->refine_d64, x->scalars + kRefineCount, N, x->best64, x->best_idx,
                                 x->sms, s)) != cudaSuccess)
         return e;
     if ((e = launch_count_add(x->counters + kRefined, x->scalars + kRefineCount, s)) != cudaSuccess) return e;
-    return launch_finalize(Mb_cur, x->best64, x->best_idx, idx_out, dist_out, s);
+    if ((e = launch_finalize(Mb_cur, x->best64, x->best_idx, idx_out, dist_out, s)) != cudaSuccess) return e;
+    TC_MARK(8);
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -259,7 +361,9 @@ int tcdtw_build(const float *cand, int64_t N, int32_t L, int32_t D, int32_t W, i
     x->sms = num_sms();
     x->G_pc = (L + o.w - 1) / o.w;
     x->ldE = ((int64_t)L * D + 31) / 32 * 32;
-    x->rho = prune_rho(L, D);
+    x->rho_ref = prune_rho(L, D);
+    x->rho = o.no_prune ? INFINITY : x->rho_ref;
+    if (o.no_prune) { x->opts.use_pc = 0; x->opts.use_ti = 0; }
     // query block: bounded by the u32 pair ids and by ~4 GB of workspace
     int64_t Mb = o.qblock > 0 ? o.qblock : 256;
     const double per_q = (double)N * 20.0 + (double)x->ldE * 8.0 + (o.use_pc ? (double)x->G_pc * K * 2 * D * 4.0 : 0);
@@ -274,11 +378,13 @@ int tcdtw_build(const float *cand, int64_t N, int32_t L, int32_t D, int32_t W, i
         for (int g = 4; g <= 32; g *= 2)
             if (tile_valid(o.tile, g, W)) { x->G = g; break; }
         if (!x->G) { free_index(x); return TCDTW_ERR_INVALID; }
-    } else if (!choose_tile((int64_t)x->Mb * 64, L, D, W, 0, &x->tile, &x->G)) {
+    } else if (!autotune_nn_tile(cand, N, L, D, W, s, &x->tile, &x->G) &&
+               !choose_tile((int64_t)x->Mb * 64, L, D, W, 0, &x->tile, &x->G)) {
         free_index(x);
         return TCDTW_ERR_UNSUPPORTED;
     }
-    if (!choose_refine_tile(D, W, &x->tile_ref, &x->G_ref)) { free_index(x); return TCDTW_ERR_UNSUPPORTED; }
+    x->R_ref = refine_rows_for(W);
+    if (x->R_ref == 0) { free_index(x); return TCDTW_ERR_UNSUPPORTED; }
     x->blocks_nn = dtw_occupancy(x->tile, 1) * x->sms;
     if (x->blocks_nn < 1) x->blocks_nn = x->sms;
     x->blocks_ref = x->sms * 2;
@@ -309,7 +415,8 @@ int tcdtw_nn(tcdtw_index *x, const float *q, int64_t M, int64_t *idx, double *di
     if (!q || !idx || !dist) return TCDTW_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t E = (int64_t)x->L * x->D;
-    const bool sync = stats != nullptr || x->opts.check_finite;
+    const bool sync = stats != nullptr || x->opts.check_finite || x->profile;
+    x->marks_used = 0;
     if (sync) {
         TC_TRY(cudaMemsetAsync(x->counters, 0, sizeof(unsigned long long) * kNumCounters, s));
         TC_TRY(cudaMemsetAsync(x->status, 0, sizeof(DevStatus), s));
@@ -320,6 +427,17 @@ int tcdtw_nn(tcdtw_index *x, const float *q, int64_t M, int64_t *idx, double *di
     }
     if (!sync) return TCDTW_OK;
     TC_TRY(cudaStreamSynchronize(s));
+    if (x->profile) {
+        const int per = TCDTW_NUM_STAGES + 1;
+        for (int b = 0; b + per <= x->marks_used; b += per) {
+            for (int k = 0; k < TCDTW_NUM_STAGES; ++k) {
+                float ms = 0.f;
+                TC_TRY(cudaEventElapsedTime(&ms, x->events[b + k], x->events[b + k + 1]));
+                x->stage_ms[k] += ms;
+            }
+            ++x->stage_blocks;
+        }
+    }
     DevStatus st;
     TC_TRY(cudaMemcpy(&st, x->status, sizeof(st), cudaMemcpyDeviceToHost));
     if (st.code) return st.code;
@@ -336,6 +454,29 @@ int tcdtw_nn(tcdtw_index *x, const float *q, int64_t M, int64_t *idx, double *di
         stats->cells = c[kCells];
         stats->refined = c[kRefined];
     }
+    return TCDTW_OK;
+}
+
+int tcdtw_index_info(tcdtw_index *x, int32_t *tile, int32_t *G, int32_t *qblock) {
+    if (!x) return TCDTW_ERR_INVALID;
+    if (tile) *tile = x->tile;
+    if (G) *G = x->G;
+    if (qblock) *qblock = x->Mb;
+    return TCDTW_OK;
+}
+
+int tcdtw_set_profiling(tcdtw_index *x, int32_t enable) {
+    if (!x) return TCDTW_ERR_INVALID;
+    x->profile = enable != 0;
+    for (int k = 0; k < TCDTW_NUM_STAGES; ++k) x->stage_ms[k] = 0.0;
+    x->stage_blocks = 0;
+    return TCDTW_OK;
+}
+
+int tcdtw_stage_times(tcdtw_index *x, double *ms, int64_t *blocks) {
+    if (!x || !ms) return TCDTW_ERR_INVALID;
+    for (int k = 0; k < TCDTW_NUM_STAGES; ++k) ms[k] = x->stage_ms[k];
+    if (blocks) *blocks = x->stage_blocks;
     return TCDTW_OK;
 }
 
@@ -420,9 +561,9 @@ int tcdtw_lower_bounds(const float *q, int64_t M, const float *c, int64_t N, int
         if (cudaMalloc(&U, sizeof(float) * Mp * ldE) != cudaSuccess) return TCDTW_ERR_NOMEM;
         if (cudaMalloc(&Lo, sizeof(float) * Mp * ldE) != cudaSuccess) { cudaFree(U); return TCDTW_ERR_NOMEM; }
         cudaError_t e = cudaSuccess;
-        for (int64_t m0 = 0; m0 < M && e == cudaSuccess; m0 += 65535) {
-            const int64_t mc = (M - m0) < 65535 ? (M - m0) : 65535;
-            e = launch_envelope(q + m0 * E, mc, L, D, W, U + m0 * ldE, Lo + m0 * ldE, (int)ldE, s);
+        for (int64_t m0 = 0; m0 < M && e == cudaSuccess; m0 += 65534) {  // even chunks keep the pair layout
+            const int64_t mc = (M - m0) < 65534 ? (M - m0) : 65534;
+            e = launch_envelope_pairs(q + m0 * E, mc, L, D, W, U + m0 * ldE, Lo + m0 * ldE, (int)ldE, s);
         }
         if (e == cudaSuccess) {
             LbMvArgs mv;

@@ -11,7 +11,12 @@
 #include "common.cuh"
 #include "dtw_tiles.cuh"
 
+#include <atomic>
+
 namespace tc {
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 int num_sms() {
     static int sms = 0;
@@ -137,6 +142,7 @@ void tcdtw_default_opts(tcdtw_opts *o) {
     o->qblock = 0;
     o->tile = -1;
     o->check_finite = 1;
+    o->no_prune = 0;
 }
 
 const char *tcdtw_strerror(int code) {
@@ -153,6 +159,8 @@ const char *tcdtw_strerror(int code) {
 }
 
 int tcdtw_tile_count(void) { return kNumTiles; }
+
+uint64_t tcdtw_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int tcdtw_tile_info(int32_t t, int32_t *G, int32_t *R, int32_t *maxD) {
     if (t < 0 || t >= kNumTiles) return TCDTW_ERR_INVALID;

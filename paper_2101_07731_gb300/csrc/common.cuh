@@ -40,8 +40,9 @@ __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned lon
 // Pruning threshold: any candidate whose FP32 DTW exceeds bsf*rho, or whose
 // rounded-down lower bound exceeds it, cannot be the exact nearest neighbour
 // (rho covers the FP32 DTW rounding error both ways and an FP64 margin).
+// rho = +inf disables pruning (the threshold is +inf even when the best is 0).
 __device__ __forceinline__ float prune_threshold(unsigned long long key, float rho) {
-    return __fmul_ru(best_dist(key), rho);
+    return rho == __int_as_float(0x7f800000) ? rho : __fmul_ru(best_dist(key), rho);
 }
 
 // ---------------------------------------------------------------- three-way min/max
@@ -50,6 +51,9 @@ __device__ __forceinline__ float fmax3(float a, float b, float c) { return fmaxf
 
 // ---------------------------------------------------------------- launch helpers
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Host-side count of kernel launches issued by the library (tcdtw_kernel_launches).
+void note_launch();
 
 }  // namespace tc
 

@@ -1,0 +1,653 @@
+// dtw_core.cuh -- banded DTW dynamic programme (Eq. 1 with the Sakoe-Chiba window,
+// Section 2) on sm_103a: device code and kernel templates, instantiated per band
+// tile by dtw_inst_*.cu.
+//
+// Work decomposition ("row-block systolic sweep").  A group of G lanes (G = 4, 8,
+// 16 or 32, several groups per warp) computes one pair.  The L rows are cut into
+// "virtual lanes" of R consecutive rows; virtual lane v (rows vR .. vR+R-1) visits
+// the columns of its band, j in [vR-W, vR+R-1+W] clipped to [0, L-1], one column
+// per time step, and computes all R cells of that column from R query points held
+// in registers and one candidate point loaded per step (so each loaded candidate
+// point serves R cells).  Virtual lane v processes column j at time t = j + v,
+// exactly one step after virtual lane v-1 did, so the only value crossing lanes per
+// step is the bottom cell of the lane above, passed with one shuffle.  Physical lane
+// l of the group runs virtual lanes l, l+G, l+2G, ...; they never overlap in time
+// when G*(R+1) >= 2W+R, which the host checks when it picks a tile.
+//
+// The squared-Euclidean cell costs of two adjacent rows are computed together with
+// packed f32x2 subtract / fused multiply-add (two cells per instruction, each cell
+// rounded exactly as a scalar fmaf chain); the recurrence uses the three-input min.
+//
+// Early abandoning (Section 7.1).  Define tau(i,j) = floor(i/R) + j.  Along any
+// warping path tau grows by 0, 1 or 2 per step, so every path from (0,0) to
+// (L-1,L-1) has a cell with tau in {t-1, t}; along the backtracked argmin path the
+// computed values never decrease.  Hence if every cell computed at times t-1 and t
+// exceeds the threshold, so does the final value, and the pair can be dropped.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "dtw_tiles.cuh"
+
+namespace tc {
+
+// ------------------------------------------------------------------ packed FP32 pairs
+typedef unsigned long long f2;  // two floats: low word first
+__device__ __forceinline__ f2 pk(float lo, float hi) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// ------------------------------------------------------------------ cp.async staging
+__device__ __forceinline__ void cp_async_4(float *smem, const float *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_16(float *smem, const float *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+// 0, computed from v in a way the compiler cannot see through: a copy whose
+// destination depends on it cannot be issued before v (a shared-memory read) is in.
+__device__ __forceinline__ unsigned opaque_zero(float v) {
+    unsigned z;
+    asm volatile("and.b32 %0, %1, 0;" : "=r"(z) : "r"(__float_as_uint(v)));
+    return z;
+}
+// Copy rows [i0, i0+nrows) of a [L][D] series (contiguous nrows*D floats) to dst.
+// vec4: the block starts 16-byte aligned and nrows*D is a multiple of 4 when
+// nrows == R; a shorter last block falls back to 4-byte copies.
+__device__ __forceinline__ void stage_rows(float *dst, const float *A, int i0, int nrows, int D, bool vec4) {
+    const float *src = A + (size_t)i0 * D;
+    const int n = nrows * D;
+    if (vec4 && (n % 4) == 0 && ((((uintptr_t)src) & 15) == 0)) {
+        for (int k = 0; k < n; k += 4) cp_async_16(dst + k, src + k);
+    } else {
+        for (int k = 0; k < n; ++k) cp_async_4(dst + k, src + k);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+// Lane-group geometry inside a warp.
+struct Grp {
+    int G;          // lanes per group
+    int lig;        // lane index in group
+    unsigned mask;  // lanes of this group
+    int src;        // warp lane of the predecessor (cyclic) in the group
+    int first;      // warp lane of the group's first lane
+};
+__device__ __forceinline__ Grp make_grp(int G) {
+    Grp g;
+    const int lane = threadIdx.x & 31;
+    g.G = G;
+    g.lig = lane & (G - 1);
+    g.first = lane - g.lig;
+    g.mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << g.first);
+    g.src = g.first + ((g.lig + G - 1) & (G - 1));
+    return g;
+}
+template <typename T>
+__device__ __forceinline__ T grp_min(T v, const Grp &g) {
+    for (int o = g.G >> 1; o > 0; o >>= 1) {
+        T w = __shfl_xor_sync(g.mask, v, o);
+        v = v < w ? v : w;
+    }
+    return v;
+}
+
+// Columns visited by virtual lane v: [jlo, jhi].
+__device__ __forceinline__ int v_jlo(int v, int R, int W) { return max(0, v * R - W); }
+__device__ __forceinline__ int v_jhi(int v, int R, int W, int L) { return min(L - 1, v * R + R - 1 + W); }
+
+// Rows r in [lo, hi] of [0, R) as a bit mask (empty if lo > hi after clipping).
+__device__ __forceinline__ unsigned row_mask(int lo, int hi, int R) {
+    lo = max(lo, 0);
+    hi = min(hi, R - 1);
+    if (lo > hi) return 0u;
+    return (0xffffffffu >> (31 - hi)) & (0xffffffffu << lo);
+}
+
+constexpr int kAbandonEvery = 8;
+
+// Hook sets.  top(j): row above the first virtual lane of a pass (v0 > 0).
+// cell(i, j, val): every in-band cell (kCells).  after_col(i0, j, bottom): once per
+// computed column of a virtual lane.  abandon(m): every kAbandonEvery steps with the
+// group-wide frontier minimum (kAbandon).
+struct NoHooks {
+    static constexpr bool kAbandon = false;
+    static constexpr bool kCells = false;
+    __device__ __forceinline__ float top(int) const { return TC_INF; }
+    __device__ __forceinline__ bool abandon(float) { return false; }
+    __device__ __forceinline__ void cell(int, int, float) {}
+    __device__ __forceinline__ void after_col(int, int, float) {}
+};
+
+// One pass of the band DP over virtual lanes [v0, v1) of one pair.
+//   A: rows series [L][D] (float32), B: columns series.
+//   v0 > 0: the row above (v0*R-1) comes from hooks.top(j); v0 == 0: the DP origin.
+// Returns R(L-1, L-1) on the lane that computed it (other lanes: +inf), or +inf
+// on every lane of a group whose hooks abandoned the pass.  *cells counts cells.
+// All lanes of g.mask must call band_pass together: with g.mask covering the whole
+// warp (lockstep kernels) every group of the warp runs the same time loop; a group
+// with live == false only takes part in the shuffles.  An abandoned group turns
+// idle; the loop ends early once no lane under g.mask has work left.
+// stage (may be null): this lane's shared-memory slot of R*D floats, used to copy
+// the rows of the lane's next virtual lane with cp.async while it works on the
+// current one (a virtual-lane start then reads shared memory, not global memory).
+template <int R, int DM, class Hooks>
+__device__ __forceinline__ float band_pass(const float *__restrict__ A, const float *__restrict__ B, int L, int D,
+                                           int W, int v0, int v1, const Grp &g, Hooks &hooks, bool live,
+                                           bool *abandoned, long long *cells, float *stage = nullptr) {
+    const bool stage_vec4 = (((uintptr_t)A) & 15) == 0;
+    static_assert(R % 2 == 0, "rows are processed in pairs");
+    constexpr int RP = R / 2;
+    const float INF = TC_INF;
+    f2 a2[RP][DM];     // rows (2k, 2k+1) of the virtual lane, dimension p
+    float col[R];      // R(i0 + r, j-1) -> R(i0 + r, j)
+    float b[DM];
+    float bottom = INF, prev_in = INF, result = INF, mn_prev = INF;
+    int v = live ? v0 + g.lig : v1;
+    const int vlast = (L - 1) / R;
+    const int tau0 = v_jlo(v0, R, W) + v0;
+    const int tau_end = v_jhi(v1 - 1, R, W, L) + (v1 - 1);
+    bool dead = !live;
+    // current virtual lane: active for tau in [tlo, thi]
+    int tlo = v < v1 ? v_jlo(v, R, W) + v : 1 << 30;
+    int thi = v < v1 ? v_jhi(v, R, W, L) + v : -1;
+    bool loaded = false, staged = false;
+    long long ncell = 0;
+    *abandoned = false;
+    for (int tau = tau0; tau <= tau_end; ++tau) {
+        const float in = __shfl_sync(g.mask, bottom, g.src);
+        if (tau > thi && v < v1) {
+            v += g.G;
+            loaded = false;
+            tlo = v < v1 ? v_jlo(v, R, W) + v : 1 << 30;
+            thi = v < v1 ? v_jhi(v, R, W, L) + v : -1;
+        }
+        float step_min = INF;
+        if (tau >= tlo && tau <= thi) {
+            const int j = tau - v;
+            const int i0 = v * R;
+            if (!loaded) {
+                if (staged) {
+                    // rows were copied to this lane's shared slot one virtual lane ago
+                    cp_async_wait_all();
+#pragma unroll
+                    for (int k = 0; k < RP; ++k) {
+                        const int i = i0 + 2 * k;
+#pragma unroll
+                        for (int p = 0; p < DM; ++p) {
+                            const float lo = (i < L && p < D) ? stage[(2 * k) * D + p] : 0.f;
+                            const float hi = (i + 1 < L && p < D) ? stage[(2 * k + 1) * D + p] : 0.f;
+                            a2[k][p] = pk(lo, hi);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < RP; ++k) {
+                        const int i = i0 + 2 * k;
+#pragma unroll
+                        for (int p = 0; p < DM; ++p) {
+                            const float lo = (i < L && p < D) ? __ldg(A + (size_t)i * D + p) : 0.f;
+                            const float hi = (i + 1 < L && p < D) ? __ldg(A + (size_t)(i + 1) * D + p) : 0.f;
+                            a2[k][p] = pk(lo, hi);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r) col[r] = INF;
+                loaded = true;
+                // start copying the rows of this lane's next virtual lane (after the
+                // reads of the slot above have completed: opaque data dependency)
+                const bool had = staged;
+                staged = false;
+                if (stage && v + g.G < v1) {
+                    float last_lo, last_hi;
+                    upk(a2[RP - 1][DM - 1], last_lo, last_hi);
+                    const unsigned z = had ? opaque_zero(last_hi) : 0u;
+                    stage_rows(stage + z, A, (v + g.G) * R, min(R, L - (v + g.G) * R), D, stage_vec4);
+                    staged = true;
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < DM; ++p) b[p] = (p < D) ? __ldg(B + (size_t)j * D + p) : 0.f;
+            float up, diag;
+            if (v == v0) {
+                if (v0 == 0) {
+                    up = INF;
+                    diag = (j == 0) ? 0.f : INF;
+                } else {
+                    up = (j <= i0 - 1 + W) ? hooks.top(j) : INF;
+                    diag = (j >= 1 && j <= i0 + W) ? hooks.top(j - 1) : INF;
+                }
+            } else {
+                up = (j <= i0 - 1 + W) ? in : INF;
+                diag = (j >= 1 && j <= i0 + W) ? prev_in : INF;
+            }
+            // rows of this column inside the band: r in [j-W-i0, j+W-i0] and i < L
+            const unsigned vm = row_mask(j - W - i0, min(j + W - i0, L - 1 - i0), R);
+            f2 bb[DM];
+#pragma unroll
+            for (int p = 0; p < DM; ++p) bb[p] = pk(b[p], b[p]);
+#pragma unroll
+            for (int k = 0; k < RP; ++k) {
+                float c0, c1;
+                f2 s = 0ull;
+#pragma unroll
+                for (int p = 0; p < DM; ++p) {
+                    const f2 t = sub2(a2[k][p], bb[p]);
+                    s = fma2(t, t, s);
+                }
+                upk(s, c0, c1);
+                // row 2k
+                float left = col[2 * k];
+                float val = __fadd_rn(c0, min3f(up, left, diag));
+                val = ((vm >> (2 * k)) & 1u) ? val : INF;
+                diag = left;
+                up = val;
+                col[2 * k] = val;
+                if (Hooks::kCells && ((vm >> (2 * k)) & 1u)) hooks.cell(i0 + 2 * k, j, val);
+                // row 2k+1
+                float left1 = col[2 * k + 1];
+                float val1 = __fadd_rn(c1, min3f(up, left1, diag));
+                val1 = ((vm >> (2 * k + 1)) & 1u) ? val1 : INF;
+                diag = left1;
+                up = val1;
+                col[2 * k + 1] = val1;
+                if (Hooks::kCells && ((vm >> (2 * k + 1)) & 1u)) hooks.cell(i0 + 2 * k + 1, j, val1);
+                if (Hooks::kAbandon) step_min = min3f(step_min, val, val1);
+            }
+            bottom = col[R - 1];
+            hooks.after_col(i0, j, bottom);
+            ncell += __popc(vm);
+            if (v == vlast && j == L - 1) {
+                const int rl = (L - 1) - i0;
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (r == rl) result = col[r];
+            }
+        }
+        prev_in = in;
+        if (Hooks::kAbandon) {
+            float fm = fminf(mn_prev, step_min);
+            mn_prev = step_min;
+            if (((tau - tau0) & (kAbandonEvery - 1)) == kAbandonEvery - 1) {
+                fm = grp_min(fm, g);
+                if (!dead && hooks.abandon(fm)) {
+                    dead = true;
+                    *abandoned = true;
+                    v = v1;  // no more work for this group
+                    tlo = 1 << 30;
+                    thi = -1;
+                }
+                if (__all_sync(g.mask, dead)) break;
+            }
+        }
+    }
+    *cells = ncell;
+    return *abandoned ? INF : result;
+}
+
+// ============================================================= pairs forward
+// Checkpoint layout: for pair p, nck = ceil(L/C)-1 rows; row k holds R(C*(k+1)-1, j)
+// for j = i-W .. i+W at index j-i+W (2W+1 floats; entries outside [0,L) unused).
+template <int R>
+struct CkptHooks {
+    float *ck;  // this pair's checkpoint rows, or null
+    int C, W, L;
+    static constexpr bool kAbandon = false;
+    static constexpr bool kCells = false;
+    __device__ __forceinline__ float top(int) const { return TC_INF; }
+    __device__ __forceinline__ bool abandon(float) { return false; }
+    __device__ __forceinline__ void cell(int, int, float) {}
+    // the bottom row i0+R-1 of a virtual lane is a checkpoint row when C | i0+R
+    __device__ __forceinline__ void after_col(int i0, int j, float bottom) {
+        const int i = i0 + R - 1;
+        if (ck && ((i + 1) % C) == 0 && i + 1 < L && j >= i - W && j <= i + W)
+            ck[(size_t)((i + 1) / C - 1) * (2 * W + 1) + (j - i + W)] = bottom;
+    }
+};
+
+// Shared memory of the pairs and search kernels: one staging slot of R*DM floats per
+// thread (rows of the next virtual lane).
+template <int R, int DM>
+constexpr size_t stage_bytes() { return (size_t)128 * R * DM * sizeof(float); }
+
+template <int R, int DM>
+__global__ void __launch_bounds__(128) k_dtw_pairs(const float *__restrict__ A, const float *__restrict__ B, int64_t P,
+                                                    int L, int D, int W, int G, float *__restrict__ dist,
+                                                    float *__restrict__ ckpt, int C) {
+    extern __shared__ float stage_smem[];
+    float *stage = stage_smem + (size_t)threadIdx.x * R * DM;
+    Grp g = make_grp(G);
+    g.mask = 0xffffffffu;  // lockstep: every group of the warp runs the same schedule
+    const int gpw = 32 / G;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int nv = (L + R - 1) / R;
+    const int nck = (L + C - 1) / C - 1;
+    for (int64_t base = warp * gpw; base < P; base += nwarps * gpw) {
+        const int64_t p = base + (threadIdx.x & 31) / G;
+        const bool live = p < P;
+        CkptHooks<R> h;
+        h.ck = (ckpt && live) ? ckpt + (size_t)p * nck * (2 * W + 1) : nullptr;
+        h.C = C;
+        h.W = W;
+        h.L = L;
+        bool ab = false;
+        long long cells;
+        const int64_t pp = live ? p : 0;
+        float r = band_pass<R, DM>(A + (size_t)pp * L * D, B + (size_t)pp * L * D, L, D, W, 0, nv, g, h, live, &ab,
+                                   &cells, stage);
+        r = grp_min(r, g);
+        if (live && g.lig == 0) dist[p] = r;
+    }
+}
+
+// ============================================================= NN search (FP32)
+struct NnHooks {
+    const unsigned long long *bsf;  // this query's packed best-so-far
+    float rho;
+    static constexpr bool kAbandon = true;
+    static constexpr bool kCells = false;
+    __device__ __forceinline__ float top(int) const { return TC_INF; }
+    __device__ __forceinline__ bool abandon(float fm) { return fm > prune_threshold(ld_volatile_u64(bsf), rho); }
+    __device__ __forceinline__ void cell(int, int, float) {}
+    __device__ __forceinline__ void after_col(int, int, float) {}
+};
+
+// Entries e in [0, count): pair (m = pairs[e] / N, n = pairs[e] % N); lb[e] is the
+// entry's best lower bound (+inf = already dropped; lb == null: 0).  Writes dtw[e]
+// (FP32 DTW, or +inf when pruned / abandoned) and lowers bsf[m].
+template <int R, int DM>
+__global__ void __launch_bounds__(128) k_dtw_nn(const float *__restrict__ Q, const float *__restrict__ Cand, int L,
+                                                 int D, int W, int G, int64_t N, const uint32_t *__restrict__ pairs,
+                                                 const float *__restrict__ lb, const int32_t *__restrict__ count,
+                                                 int n_static, int *__restrict__ cursor, unsigned long long *bsf,
+                                                 float rho, float *__restrict__ dtw,
+                                                 unsigned long long *__restrict__ counters) {
+    extern __shared__ float stage_smem[];
+    float *stage = stage_smem + (size_t)threadIdx.x * R * DM;
+    Grp g = make_grp(G);
+    g.mask = 0xffffffffu;  // lockstep: every group of the warp runs the same schedule
+    const int gpw = 32 / G;
+    const int nv = (L + R - 1) / R;
+    const int n_entries = count ? *count : n_static;
+    unsigned long long started = 0, aband = 0, ncells = 0, pruned = 0;
+    for (;;) {
+        // the warp takes gpw consecutive entries, one per group, and runs them together
+        int base = 0;
+        if ((threadIdx.x & 31) == 0) base = atomicAdd(cursor, gpw);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= n_entries) break;
+        const int e = base + (threadIdx.x & 31) / G;
+        bool live = e < n_entries;
+        const uint32_t pid = live ? pairs[e] : 0xffffffffu;
+        live = live && pid != 0xffffffffu;
+        int m = 0;
+        int64_t n = 0;
+        if (live) {
+            m = (int)(pid / (uint32_t)N);
+            n = (int64_t)(pid - (uint32_t)m * (uint32_t)N);
+            const float lbe = lb ? lb[e] : 0.f;
+            const float thr = prune_threshold(ld_volatile_u64(bsf + m), rho);
+            if (!(lbe <= thr) || lbe == TC_INF) {
+                if (g.lig == 0 && lbe != TC_INF) ++pruned;
+                live = false;
+            }
+        }
+        NnHooks h;
+        h.bsf = bsf + m;
+        h.rho = rho;
+        bool ab = false;
+        long long cells = 0;
+        float r = band_pass<R, DM>(Q + (size_t)m * L * D, Cand + (size_t)n * L * D, L, D, W, 0, nv, g, h, live, &ab,
+                                   &cells, stage);
+        r = grp_min(r, g);
+        long long cs = cells;
+        for (int o = G >> 1; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
+        if (e < n_entries && g.lig == 0) {
+            if (!live) {
+                dtw[e] = TC_INF;
+            } else {
+                ++started;
+                ncells += (unsigned long long)cs;
+                if (ab) {
+                    ++aband;
+                    dtw[e] = TC_INF;
+                } else {
+                    dtw[e] = r;
+                    atomicMin(bsf + m, pack_best(r, (uint32_t)n));
+                }
+            }
+        }
+    }
+    if (g.lig == 0 && counters && (started | pruned)) {
+        atomicAdd(counters + 0, started);
+        atomicAdd(counters + 1, aband);
+        atomicAdd(counters + 2, ncells);
+        atomicAdd(counters + 3, pruned);
+    }
+}
+
+// ============================================================= backward (adjoint)
+// Segment hooks: store every computed cell of rows [row0, row0+C) into shared
+// memory S[(i-row0+1)*(2W+1) + (j-i+W)]; the row above the segment comes from
+// the checkpoint row, copied into S row 0.
+struct SegHooks {
+    float *S;
+    int row0, W;
+    static constexpr bool kAbandon = false;
+    static constexpr bool kCells = true;
+    __device__ __forceinline__ float top(int j) const { return S[j - (row0 - 1) + W]; }
+    __device__ __forceinline__ bool abandon(float) { return false; }
+    __device__ __forceinline__ void cell(int i, int j, float val) {
+        S[(size_t)(i - row0 + 1) * (2 * W + 1) + (j - i + W)] = val;
+    }
+    __device__ __forceinline__ void after_col(int, int, float) {}
+};
+
+// One group per pair.  Shared memory per group: (C+1) * (2W+1) floats.
+template <int R, int DM>
+__global__ void __launch_bounds__(128) k_dtw_backward(const float *__restrict__ A, const float *__restrict__ B,
+                                                       const float *__restrict__ ckpt, int C,
+                                                       const float *__restrict__ gdist, int64_t P, int L, int D, int W,
+                                                       int G, float *__restrict__ gA, float *__restrict__ gB) {
+    extern __shared__ float smem[];
+    Grp g = make_grp(G);
+    const int groups_per_block = blockDim.x / G;
+    const int grp_in_block = threadIdx.x / G;
+    const int BW = 2 * W + 1;
+    float *S = smem + (size_t)grp_in_block * (C + 1) * BW;
+    const int64_t gid = (int64_t)blockIdx.x * groups_per_block + grp_in_block;
+    const int64_t stride = (int64_t)gridDim.x * groups_per_block;
+    const int nseg = (L + C - 1) / C;
+    const int nck = nseg - 1;
+    constexpr int KD = (DM + 3) / 4;  // dims per lane (G >= 4)
+    const float INF = TC_INF;
+    for (int64_t p = gid; p < P; p += stride) {
+        const float *a = A + (size_t)p * L * D;
+        const float *b = B + (size_t)p * L * D;
+        const float *ck = ckpt + (size_t)p * nck * BW;
+        float *ga = gA + (size_t)p * L * D;
+        float *gb = gB + (size_t)p * L * D;
+        const float gscale = gdist[p];
+        float acc_a[KD], acc_b[KD];
+#pragma unroll
+        for (int k = 0; k < KD; ++k) {
+            acc_a[k] = 0.f;
+            acc_b[k] = 0.f;
+        }
+        int ci = L - 1, cj = L - 1;  // path cursor
+        bool done = false;
+        for (int s = nseg - 1; s >= 0 && !done; --s) {
+            const int row0 = s * C;
+            const int row1 = min(L, row0 + C);
+            for (int k = g.lig; k < BW; k += G) S[k] = (s == 0) ? INF : ck[(size_t)(s - 1) * BW + k];
+            __syncwarp(g.mask);
+            SegHooks h;
+            h.S = S;
+            h.row0 = row0;
+            h.W = W;
+            bool ab;
+            long long cells;
+            band_pass<R, DM>(a, b, L, D, W, row0 / R, (row1 + R - 1) / R, g, h, true, &ab, &cells);
+            __syncwarp(g.mask);
+            while (ci >= row0) {
+#pragma unroll
+                for (int k = 0; k < KD; ++k) {
+                    const int pp = g.lig + k * G;
+                    if (pp < D) {
+                        const float diff = a[(size_t)ci * D + pp] - b[(size_t)cj * D + pp];
+                        acc_a[k] += 2.f * diff;
+                        acc_b[k] -= 2.f * diff;
+                    }
+                }
+                if (ci == 0 && cj == 0) {
+                    done = true;
+                    break;
+                }
+                auto Rv = [&](int i, int j) -> float {
+                    if (i < 0 || j < 0 || abs(i - j) > W) return INF;
+                    return S[(size_t)(i - row0 + 1) * BW + (j - i + W)];
+                };
+                const float vd = Rv(ci - 1, cj - 1), vu = Rv(ci - 1, cj), vl = Rv(ci, cj - 1);
+                int ni = ci - 1, nj = cj - 1;
+                float best = vd;
+                if (vu < best) { best = vu; ni = ci - 1; nj = cj; }
+                if (vl < best) { best = vl; ni = ci; nj = cj - 1; }
+                if (ni != ci) {  // leaving row ci
+#pragma unroll
+                    for (int k = 0; k < KD; ++k) {
+                        const int pp = g.lig + k * G;
+                        if (pp < D) ga[(size_t)ci * D + pp] = gscale * acc_a[k];
+                        acc_a[k] = 0.f;
+                    }
+                }
+                if (nj != cj) {  // leaving column cj
+#pragma unroll
+                    for (int k = 0; k < KD; ++k) {
+                        const int pp = g.lig + k * G;
+                        if (pp < D) gb[(size_t)cj * D + pp] = gscale * acc_b[k];
+                        acc_b[k] = 0.f;
+                    }
+                }
+                ci = ni;
+                cj = nj;
+            }
+            __syncwarp(g.mask);
+        }
+#pragma unroll
+        for (int k = 0; k < KD; ++k) {
+            const int pp = g.lig + k * G;
+            if (pp < D) {
+                ga[pp] = gscale * acc_a[k];
+                gb[pp] = gscale * acc_b[k];
+            }
+        }
+        __syncwarp(g.mask);
+    }
+}
+
+// ============================================================= per-tile launchers
+template <int R, int DM>
+struct TileKernels {
+    static cudaError_t prepare() {  // allow the staging slots above 48 KB (once)
+        static bool done = false;
+        if (done) return cudaSuccess;
+        const int sb = (int)stage_bytes<R, DM>();
+        cudaError_t e = cudaFuncSetAttribute(k_dtw_pairs<R, DM>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_dtw_nn<R, DM>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+        done = e == cudaSuccess;
+        return e;
+    }
+    static cudaError_t pairs(int G, int blocks, cudaStream_t s, const float *A, const float *B, int64_t P, int L,
+                             int D, int W, float *dist, float *ck, int C) {
+        cudaError_t e = prepare();
+        if (e != cudaSuccess) return e;
+        k_dtw_pairs<R, DM><<<blocks, 128, stage_bytes<R, DM>(), s>>>(A, B, P, L, D, W, G, dist, ck, C);
+        note_launch();
+        return cudaGetLastError();
+    }
+    static cudaError_t nn(int blocks, cudaStream_t s, const DtwNnArgs &x) {
+        cudaError_t e = prepare();
+        if (e != cudaSuccess) return e;
+        k_dtw_nn<R, DM><<<blocks, 128, stage_bytes<R, DM>(), s>>>(x.Q, x.C, x.L, x.D, x.W, x.G, x.N, x.pairs, x.lb,
+                                                                   x.count, x.n_static, x.cursor, x.bsf, x.rho, x.dtw,
+                                                                   x.counters);
+        note_launch();
+        return cudaGetLastError();
+    }
+    static cudaError_t backward(int G, int blocks, int threads, size_t smem, cudaStream_t s, const float *A,
+                                const float *B, const float *ck, int C, const float *gd, int64_t P, int L, int D,
+                                int W, float *gA, float *gB) {
+        if (smem > 227 * 1024) return cudaErrorInvalidValue;
+        auto k = k_dtw_backward<R, DM>;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        k<<<blocks, threads, smem, s>>>(A, B, ck, C, gd, P, L, D, W, G, gA, gB);
+        note_launch();
+        return cudaGetLastError();
+    }
+    static int occupancy(int which) {
+        int n = 0;
+        if (prepare() != cudaSuccess) return 0;
+        if (which == 0)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dtw_pairs<R, DM>, 128, stage_bytes<R, DM>());
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dtw_nn<R, DM>, 128, stage_bytes<R, DM>());
+        return n;
+    }
+};
+
+// Per-tile entry points (defined in the instantiation units).
+#define TC_TILE_DECL(id, R, DM)                                                                                     \
+    cudaError_t tile##id##_pairs(int G, int blocks, cudaStream_t s, const float *A, const float *B, int64_t P,     \
+                                 int L, int D, int W, float *dist, float *ck, int C);                              \
+    cudaError_t tile##id##_nn(int blocks, cudaStream_t s, const DtwNnArgs &x);                                     \
+    cudaError_t tile##id##_backward(int G, int blocks, int threads, size_t smem, cudaStream_t s, const float *A,   \
+                                    const float *B, const float *ck, int C, const float *gd, int64_t P, int L,     \
+                                    int D, int W, float *gA, float *gB);                                           \
+    int tile##id##_occupancy(int which);
+
+#define TC_TILE_DEF(id, R, DM)                                                                                      \
+    cudaError_t tile##id##_pairs(int G, int blocks, cudaStream_t s, const float *A, const float *B, int64_t P,     \
+                                 int L, int D, int W, float *dist, float *ck, int C) {                             \
+        return TileKernels<R, DM>::pairs(G, blocks, s, A, B, P, L, D, W, dist, ck, C);                              \
+    }                                                                                                               \
+    cudaError_t tile##id##_nn(int blocks, cudaStream_t s, const DtwNnArgs &x) {                                    \
+        return TileKernels<R, DM>::nn(blocks, s, x);                                                                \
+    }                                                                                                               \
+    cudaError_t tile##id##_backward(int G, int blocks, int threads, size_t smem, cudaStream_t s, const float *A,   \
+                                    const float *B, const float *ck, int C, const float *gd, int64_t P, int L,     \
+                                    int D, int W, float *gA, float *gB) {                                          \
+        return TileKernels<R, DM>::backward(G, blocks, threads, smem, s, A, B, ck, C, gd, P, L, D, W, gA, gB);      \
+    }                                                                                                               \
+    int tile##id##_occupancy(int which) { return TileKernels<R, DM>::occupancy(which); }
+
+}  // namespace tc

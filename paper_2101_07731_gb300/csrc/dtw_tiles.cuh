@@ -1,27 +1,32 @@
-// dtw_tiles.cuh -- compiled band tiles of the DTW kernels and their launch records.
-// A tile fixes R (rows per lane, i.e. reuse of each loaded candidate point) and
-// DMAX (dimensions held in registers; D <= DMAX, the rest zero-padded).  The
-// group width G (lanes per pair) is a run-time choice with G*(R+1) >= 2W+R.
+// dtw_tiles.cuh -- compiled band tiles of the FP32 DTW kernels and their launch
+// records.  A tile fixes R (rows per lane: each loaded candidate point serves R
+// cells) and DM (dimensions held in registers; D <= DM, the rest zero-padded; for
+// D <= 8 there is a tile with DM == D).  The group width G (lanes per pair) is a
+// run-time choice with G*(R+1) >= 2W+R.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-// X(id, R, DMAX)
-#define TC_TILES(X)                                   \
-    X(0, 4, 4) X(1, 8, 4) X(2, 16, 4)                 \
-    X(3, 4, 6) X(4, 8, 6) X(5, 16, 6)                 \
-    X(6, 4, 8) X(7, 8, 8)                             \
-    X(8, 4, 12) X(9, 8, 12)                           \
-    X(10, 4, 16) X(11, 8, 16)                         \
-    X(12, 2, 32) X(13, 4, 32) X(14, 6, 32)            \
-    X(15, 2, 64)
+// X(id, R, DM), split over three translation units compiled in parallel
+#define TC_TILES_A(X)                                                                                      \
+    X(0, 4, 1) X(1, 8, 1) X(2, 16, 1) X(3, 4, 2) X(4, 8, 2) X(5, 16, 2) X(6, 4, 3) X(7, 8, 3) X(8, 16, 3) \
+    X(9, 4, 4) X(10, 8, 4) X(11, 16, 4)
+#define TC_TILES_B(X)                                                                                           \
+    X(12, 4, 5) X(13, 8, 5) X(14, 16, 5) X(15, 4, 6) X(16, 8, 6) X(17, 16, 6) X(18, 4, 7) X(19, 8, 7) X(20, 16, 7) \
+    X(21, 4, 8) X(22, 8, 8) X(23, 16, 8)
+#define TC_TILES_C(X) \
+    X(24, 4, 12) X(25, 8, 12) X(26, 4, 16) X(27, 8, 16) X(28, 2, 32) X(29, 4, 32) X(30, 6, 32) X(31, 2, 64)
+#define TC_TILES(X) TC_TILES_A(X) TC_TILES_B(X) TC_TILES_C(X)
+
+// FP64 refine: rows per lane (one warp per pair, G = 32)
+#define TC_REFINE_RS(X) X(1) X(2) X(4) X(6) X(8) X(16)
 
 namespace tc {
 
 struct TileInfo {
     int R, DMAX;
 };
-#define TC_TILE_INFO(id, R, DMAX) {R, DMAX},
+#define TC_TILE_INFO(id, R, DM) {R, DM},
 static const TileInfo kTiles[] = {TC_TILES(TC_TILE_INFO)};
 #undef TC_TILE_INFO
 constexpr int kNumTiles = (int)(sizeof(kTiles) / sizeof(kTiles[0]));
@@ -32,7 +37,7 @@ struct DtwNnArgs {
     int L, D, W, G;
     int64_t N;
     const uint32_t *pairs; // entry -> m*N + n
-    const float *lb;       // entry -> best lower bound (+inf = pruned)
+    const float *lb;       // entry -> best lower bound (+inf = pruned), or null
     const int32_t *count;  // number of entries (device), or null: n_static
     int n_static;
     int *cursor;           // work counter (zeroed before launch)
@@ -45,7 +50,7 @@ struct DtwNnArgs {
 struct DtwRefineArgs {
     const float *Q;
     const float *C;
-    int L, D, W, G;
+    int L, D, W;
     int64_t N;
     const uint32_t *pairs;
     const int32_t *count;
@@ -56,7 +61,9 @@ struct DtwRefineArgs {
 cudaError_t dtw_pairs_launch(int tile, int G, int blocks, cudaStream_t s, const float *A, const float *B, int64_t P,
                              int L, int D, int W, float *dist, float *ck, int C);
 cudaError_t dtw_nn_launch(int tile, int blocks, cudaStream_t s, const DtwNnArgs &x);
-cudaError_t dtw_refine_launch(int tile, int blocks, cudaStream_t s, const DtwRefineArgs &x);
+// FP64 refine with R rows per lane (R in TC_REFINE_RS, one warp per pair)
+cudaError_t dtw_refine_launch(int R, int blocks, cudaStream_t s, const DtwRefineArgs &x);
+int refine_rows_for(int W);  // smallest compiled R with 32*(R+1) >= 2W+R, or 0
 cudaError_t dtw_backward_launch(int tile, int G, int blocks, size_t smem, cudaStream_t s, const float *A,
                                 const float *B, const float *ck, int C, const float *gd, int64_t P, int L, int D,
                                 int W, float *gA, float *gB, int threads);

@@ -14,14 +14,19 @@
 namespace tc {
 
 // ============================================================== LB_MV stream
-// CTA tile: 128 candidates (one per thread) x QB queries.  The flat elements
-// e = 0 .. E-1 (E = L*D; LB_MV is a sum over (point, dimension) elements, each
-// against the query envelope at the same element) are streamed in chunks of 32:
-// the candidate chunk [128][32] and the envelope chunks [QB][32] are copied to
-// shared memory with cp.async (16-byte copies when aligned), double buffered.
-// A candidate row is 128 bytes; its eight 16-byte segments are stored XOR-swizzled
-// by (row & 7) so that the per-thread 16-byte reads are free of bank conflicts.
-// Every thread reads the envelope values of the same element (broadcast).
+// CTA tile: 128 candidates (one per thread) x QB queries.  LB_MV is a sum over the
+// flat (point, dimension) elements e = 0 .. E-1 (E = L*D), each candidate element
+// against the query envelope at the same element, so the elements are streamed in
+// chunks of 32: the candidate chunk [128][32] and the envelope chunk of the tile's
+// queries are copied to shared memory with cp.async (16-byte copies when aligned),
+// double buffered.  A candidate row is 128 bytes; its eight 16-byte segments are
+// stored XOR-swizzled by (row & 7) so the per-thread 16-byte reads are free of bank
+// conflicts.  The envelope is stored query-pair interleaved, [q/2][e][q%2], so one
+// 16-byte broadcast read gives two elements of two queries.
+// Per element and query:  m = max(c -rd U, Lo -rd c, 0)  (one three-input max),
+// acc += m*m rounded down; the subtractions and the multiply-adds of two queries go
+// in one packed f32x2 instruction each.  Sums are two-level (32 elements of a chunk,
+// then the chunk sums), so a round-down chain is at most 32 + E/32 long.
 constexpr int kMvRows = 128;
 constexpr int kMvChunk = 32;
 
@@ -37,17 +42,56 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 pk(float lo, float hi) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 sub2_rd(f2 a, f2 b) {
+    f2 r;
+    asm("sub.rm.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 fma2_rd(f2 a, f2 b, f2 c) {
+    f2 r;
+    asm("fma.rm.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ f2 add2_rd(f2 a, f2 b) {
+    f2 r;
+    asm("add.rm.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // squared distance of x to [lo, hi], rounded down, accumulated into acc
 __device__ __forceinline__ float acc_box(float x, float lo, float hi, float acc) {
-    const float cl = fminf(fmaxf(x, lo), hi);
-    const float d = __fsub_rz(x, cl);
-    return __fmaf_rd(d, d, acc);
+    const float m = max3f(__fsub_rd(x, hi), __fsub_rd(lo, x), 0.f);
+    return __fmaf_rd(m, m, acc);
+}
+
+// one packed step: element value c2 = {x, x} against two queries' (U, Lo)
+__device__ __forceinline__ f2 mv_step(f2 c2, float u0, float u1, float l0, float l1, f2 part) {
+    float a0, a1, b0, b1;
+    upk(sub2_rd(c2, pk(u0, u1)), a0, a1);
+    upk(sub2_rd(pk(l0, l1), c2), b0, b1);
+    const float m0 = max3f(a0, b0, 0.f), m1 = max3f(a1, b1, 0.f);
+    const f2 m2 = pk(m0, m1);
+    return fma2_rd(m2, m2, part);
 }
 
 template <int QB>
-__device__ __forceinline__ void mv_issue(const float *__restrict__ cand, int64_t N, int E, bool vec4, const float *U,
-                                         const float *Lo, int64_t ldE, int Mb, int64_t n0, int q0, int e0, float *sc,
-                                         float *su, float *sl) {
+__device__ __forceinline__ void mv_issue(const float *__restrict__ cand, int64_t N, int E, bool vec4,
+                                         const float *UI, const float *LI, int64_t ldE, int n_qp, int64_t n0, int q0,
+                                         int e0, float *sc, float *su, float *sl) {
     const int tid = threadIdx.x;
     if (vec4) {
 #pragma unroll
@@ -72,19 +116,20 @@ __device__ __forceinline__ void mv_issue(const float *__restrict__ cand, int64_t
             cp_async4(sc + row * kMvChunk + ((seg ^ (row & 7)) << 2) + (el & 3), src, ok ? 4 : 0);
         }
     }
-    // envelope chunk: QB rows x 8 segments, for U and Lo
-    for (int idx = tid; idx < QB * 16; idx += 128) {
-        const int which = idx / (QB * 8);
-        const int r = (idx % (QB * 8)) >> 3, seg = idx & 7;
-        const int qrow = min(q0 + r, Mb - 1);
-        const float *src = (which ? Lo : U) + (size_t)qrow * ldE + e0 + seg * 4;
-        cp_async16((which ? sl : su) + r * kMvChunk + seg * 4, src, 16);
+    // envelope chunk: QB/2 query pairs x 32 elements x 2 floats (256 bytes), U and Lo
+    for (int idx = tid; idx < (QB / 2) * 16 * 2; idx += 128) {
+        const int which = idx / ((QB / 2) * 16);
+        const int r = idx % ((QB / 2) * 16);
+        const int qp = r >> 4, seg = r & 15;
+        const int qpg = min(q0 / 2 + qp, n_qp - 1);
+        const float *src = (which ? LI : UI) + ((size_t)qpg * ldE + e0) * 2 + seg * 4;
+        cp_async16((which ? sl : su) + qp * 2 * kMvChunk + seg * 4, src, 16);
     }
 }
 
 template <int QB>
 __global__ void __launch_bounds__(128) k_lb_mv(const float *__restrict__ cand, int64_t N, int E, int vec4,
-                                               const float *__restrict__ U, const float *__restrict__ Lo,
+                                               const float *__restrict__ UI, const float *__restrict__ LI,
                                                int64_t ldE, int Mb, float *__restrict__ lb, int64_t ldLb,
                                                int n_ctiles, int n_qtiles) {
     __shared__ __align__(16) float sc[2][kMvRows * kMvChunk];
@@ -93,55 +138,61 @@ __global__ void __launch_bounds__(128) k_lb_mv(const float *__restrict__ cand, i
     const int tid = threadIdx.x;
     const int nchunks = (E + kMvChunk - 1) / kMvChunk;
     const int ntiles = n_ctiles * n_qtiles;
+    const int n_qp = (Mb + 1) / 2;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int ct = tile / n_qtiles, qt = tile % n_qtiles;
         const int64_t n0 = (int64_t)ct * kMvRows;
         const int q0 = qt * QB;
-        float acc[QB];
+        f2 acc[QB / 2];
 #pragma unroll
-        for (int q = 0; q < QB; ++q) acc[q] = 0.f;
-        mv_issue<QB>(cand, N, E, vec4, U, Lo, ldE, Mb, n0, q0, 0, sc[0], su[0], sl[0]);
+        for (int k = 0; k < QB / 2; ++k) acc[k] = 0ull;
+        mv_issue<QB>(cand, N, E, vec4, UI, LI, ldE, n_qp, n0, q0, 0, sc[0], su[0], sl[0]);
         cp_async_commit();
         for (int c = 0; c < nchunks; ++c) {
             const int buf = c & 1;
             if (c + 1 < nchunks) {
-                mv_issue<QB>(cand, N, E, vec4, U, Lo, ldE, Mb, n0, q0, (c + 1) * kMvChunk, sc[buf ^ 1], su[buf ^ 1],
-                             sl[buf ^ 1]);
+                mv_issue<QB>(cand, N, E, vec4, UI, LI, ldE, n_qp, n0, q0, (c + 1) * kMvChunk, sc[buf ^ 1],
+                             su[buf ^ 1], sl[buf ^ 1]);
                 cp_async_commit();
                 cp_async_wait<1>();
             } else {
                 cp_async_wait<0>();
             }
             __syncthreads();
-            float x[kMvChunk];
+            f2 c2[kMvChunk];
 #pragma unroll
             for (int s = 0; s < 8; ++s) {
                 const float4 v = *reinterpret_cast<const float4 *>(&sc[buf][tid * kMvChunk + ((s ^ (tid & 7)) << 2)]);
-                x[4 * s] = v.x; x[4 * s + 1] = v.y; x[4 * s + 2] = v.z; x[4 * s + 3] = v.w;
+                c2[4 * s] = pk(v.x, v.x);
+                c2[4 * s + 1] = pk(v.y, v.y);
+                c2[4 * s + 2] = pk(v.z, v.z);
+                c2[4 * s + 3] = pk(v.w, v.w);
             }
-            // two-level sum: a chunk's 32 terms, then the chunk sums (a chain of at
-            // most 32 + E/32 round-down additions instead of E)
 #pragma unroll
-            for (int q = 0; q < QB; ++q) {
-                float a = 0.f;
+            for (int qp = 0; qp < QB / 2; ++qp) {
+                f2 part = 0ull;
+                const float *u = &su[buf][qp * 2 * kMvChunk];
+                const float *l = &sl[buf][qp * 2 * kMvChunk];
 #pragma unroll
-                for (int s = 0; s < 8; ++s) {
-                    const float4 u = *reinterpret_cast<const float4 *>(&su[buf][q * kMvChunk + 4 * s]);
-                    const float4 l = *reinterpret_cast<const float4 *>(&sl[buf][q * kMvChunk + 4 * s]);
-                    a = acc_box(x[4 * s], l.x, u.x, a);
-                    a = acc_box(x[4 * s + 1], l.y, u.y, a);
-                    a = acc_box(x[4 * s + 2], l.z, u.z, a);
-                    a = acc_box(x[4 * s + 3], l.w, u.w, a);
+                for (int e = 0; e < kMvChunk; e += 2) {
+                    const float4 u4 = *reinterpret_cast<const float4 *>(u + 2 * e);
+                    const float4 l4 = *reinterpret_cast<const float4 *>(l + 2 * e);
+                    part = mv_step(c2[e], u4.x, u4.y, l4.x, l4.y, part);
+                    part = mv_step(c2[e + 1], u4.z, u4.w, l4.z, l4.w, part);
                 }
-                acc[q] = __fadd_rd(acc[q], a);
+                acc[qp] = add2_rd(acc[qp], part);
             }
             __syncthreads();
         }
         const int64_t n = n0 + tid;
         if (n < N) {
 #pragma unroll
-            for (int q = 0; q < QB; ++q)
-                if (q0 + q < Mb) lb[(size_t)(q0 + q) * ldLb + n] = acc[q];
+            for (int qp = 0; qp < QB / 2; ++qp) {
+                float a0, a1;
+                upk(acc[qp], a0, a1);
+                if (q0 + 2 * qp < Mb) lb[(size_t)(q0 + 2 * qp) * ldLb + n] = a0;
+                if (q0 + 2 * qp + 1 < Mb) lb[(size_t)(q0 + 2 * qp + 1) * ldLb + n] = a1;
+            }
         }
     }
 }
@@ -157,22 +208,21 @@ cudaError_t launch_lb_mv(const LbMvArgs &a, cudaStream_t s) {
     else if (a.Mb <= 16) QB = 16;
     const int n_qtiles = (a.Mb + QB - 1) / QB;
     int occ = 0;
-    cudaError_t e;
-#define TC_MV_LAUNCH(QBV)                                                                              \
-    do {                                                                                               \
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lb_mv<QBV>, 128, 0);                     \
-        int64_t tiles = (int64_t)n_ctiles * n_qtiles;                                                  \
-        int64_t grid = (int64_t)(occ > 0 ? occ : 1) * a.sms;                                           \
-        if (grid > tiles) grid = tiles;                                                                \
+#define TC_MV_LAUNCH(QBV)                                                                                       \
+    do {                                                                                                        \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lb_mv<QBV>, 128, 0);                              \
+        int64_t tiles = (int64_t)n_ctiles * n_qtiles;                                                           \
+        int64_t grid = (int64_t)(occ > 0 ? occ : 1) * a.sms;                                                    \
+        if (grid > tiles) grid = tiles;                                                                         \
         k_lb_mv<QBV><<<(int)grid, 128, 0, s>>>(a.cand, a.N, a.E, vec4, a.U, a.Lo, a.ldE, a.Mb, a.lb, a.ldLb, \
-                                               n_ctiles, n_qtiles);                                    \
+                                               n_ctiles, n_qtiles);                                             \
+        note_launch();                                                                                          \
     } while (0)
     if (QB == 8) TC_MV_LAUNCH(8);
     else if (QB == 16) TC_MV_LAUNCH(16);
     else TC_MV_LAUNCH(32);
 #undef TC_MV_LAUNCH
-    e = cudaGetLastError();
-    return e;
+    return cudaGetLastError();
 }
 
 // ============================================================== compaction
@@ -276,10 +326,13 @@ __global__ void k_write_rows(const float *__restrict__ lb, int64_t N, int64_t ld
 
 cudaError_t launch_compact(const CompactArgs &a, cudaStream_t s) {
     if (a.M <= 0) return cudaSuccess;
-    k_count_rows<<<(unsigned)a.M, 256, 0, s>>>(a.lb, a.N, a.ldLb, a.thresh, a.bsf, a.rho, a.counts, a.pruned);
-    if (a.offsets) k_scan_counts<<<1, 1024, 0, s>>>(a.counts, a.M, a.offsets, a.total);
+    k_count_rows<<<(unsigned)a.M, 256, 0, s>>>(a.lb, a.N, a.ldLb, a.thresh, a.bsf, a.rho, a.counts, a.pruned); note_launch();
+    if (a.offsets) {
+        k_scan_counts<<<1, 1024, 0, s>>>(a.counts, a.M, a.offsets, a.total);
+        note_launch();
+    }
     k_write_rows<<<(unsigned)a.M, 256, 0, s>>>(a.lb, a.N, a.ldLb, a.thresh, a.bsf, a.rho, a.offsets, a.ldOut, a.pairs,
-                                                a.lbs, a.idx_out);
+                                                a.lbs, a.idx_out); note_launch();
     return cudaGetLastError();
 }
 
@@ -361,7 +414,7 @@ __global__ void k_seed_topk(float *__restrict__ lb, int64_t N, int64_t ldLb, int
 cudaError_t launch_seed_topk(float *lb, int64_t M, int64_t N, int64_t ldLb, int S, uint32_t *seeds, cudaStream_t s) {
     if (M <= 0 || S <= 0) return cudaSuccess;
     if (S > kMaxSeeds) S = kMaxSeeds;
-    k_seed_topk<<<(unsigned)M, 256, 0, s>>>(lb, N, ldLb, S, seeds);
+    k_seed_topk<<<(unsigned)M, 256, 0, s>>>(lb, N, ldLb, S, seeds); note_launch();
     return cudaGetLastError();
 }
 
@@ -541,7 +594,7 @@ cudaError_t launch_lb_pc_list(const PairListArgs &a, const float *boxes, const i
                               int64_t n_hint, int sms, cudaStream_t s) {
     const int blocks = list_blocks(n_hint, sms);
 #define TC_PC_CALL(DM) k_lb_pc_list<DM><<<blocks, 128, 0, s>>>(a, boxes, counts, K, w, bsf, rho, e_gate, stat_pruned)
-    TC_DMAX_DISPATCH(a.D, TC_PC_CALL);
+    TC_DMAX_DISPATCH(a.D, TC_PC_CALL); note_launch();
 #undef TC_PC_CALL
     return cudaGetLastError();
 }
@@ -551,7 +604,7 @@ cudaError_t launch_lb_ti_list(const PairListArgs &a, const float *dq_lo, const f
                               int64_t n_hint, int sms, cudaStream_t s) {
     const int blocks = list_blocks(n_hint, sms);
 #define TC_TI_CALL(DM) k_lb_ti_list<DM><<<blocks, 128, 0, s>>>(a, dq_lo, dq_hi, P, bsf, rho, e_gate, stat_pruned)
-    TC_DMAX_DISPATCH(a.D, TC_TI_CALL);
+    TC_DMAX_DISPATCH(a.D, TC_TI_CALL); note_launch();
 #undef TC_TI_CALL
     return cudaGetLastError();
 }
@@ -617,36 +670,36 @@ __global__ void k_iota_pairs(uint32_t *p, int64_t n) {
 }
 
 cudaError_t launch_count_add(unsigned long long *acc, const int32_t *v, cudaStream_t s) {
-    k_count_add<<<1, 1, 0, s>>>(acc, v);
+    k_count_add<<<1, 1, 0, s>>>(acc, v); note_launch();
     return cudaGetLastError();
 }
 cudaError_t launch_iota_pairs(uint32_t *p, int64_t n, cudaStream_t s) {
     int64_t b = (n + 255) / 256;
     if (b > 65535) b = 65535;
-    k_iota_pairs<<<(unsigned)b, 256, 0, s>>>(p, n);
+    k_iota_pairs<<<(unsigned)b, 256, 0, s>>>(p, n); note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_refine_select(const uint32_t *pairs, const float *dtw, const int32_t *count, int64_t n_static,
                                  int64_t N, const unsigned long long *bsf, float rho, uint32_t *out,
                                  int32_t *out_count, int64_t cap, int sms, cudaStream_t s) {
-    k_refine_select<<<sms * 4, 256, 0, s>>>(pairs, dtw, count, n_static, N, bsf, rho, out, out_count, cap);
+    k_refine_select<<<sms * 4, 256, 0, s>>>(pairs, dtw, count, n_static, N, bsf, rho, out, out_count, cap); note_launch();
     return cudaGetLastError();
 }
 cudaError_t launch_refine_pick(const uint32_t *pairs, const double *d64, const int32_t *count, int64_t N,
                                const unsigned long long *best64, unsigned long long *best_idx, int sms,
                                cudaStream_t s) {
-    k_refine_pick<<<sms, 256, 0, s>>>(pairs, d64, count, N, best64, best_idx);
+    k_refine_pick<<<sms, 256, 0, s>>>(pairs, d64, count, N, best64, best_idx); note_launch();
     return cudaGetLastError();
 }
 cudaError_t launch_finalize(int64_t Mb, const unsigned long long *best64, const unsigned long long *best_idx,
                             int64_t *idx, double *dist, cudaStream_t s) {
-    k_finalize<<<(unsigned)((Mb + 255) / 256), 256, 0, s>>>(Mb, best64, best_idx, idx, dist);
+    k_finalize<<<(unsigned)((Mb + 255) / 256), 256, 0, s>>>(Mb, best64, best_idx, idx, dist); note_launch();
     return cudaGetLastError();
 }
 cudaError_t launch_init_block(int64_t Mb, unsigned long long *bsf, unsigned long long *best64,
                               unsigned long long *best_idx, cudaStream_t s) {
-    k_init_block<<<(unsigned)((Mb + 255) / 256), 256, 0, s>>>(Mb, bsf, best64, best_idx);
+    k_init_block<<<(unsigned)((Mb + 255) / 256), 256, 0, s>>>(Mb, bsf, best64, best_idx); note_launch();
     return cudaGetLastError();
 }
 

@@ -12,6 +12,10 @@ namespace tc {
 cudaError_t launch_check_finite(const float *x, int64_t n, DevStatus *st, int where, cudaStream_t s);
 cudaError_t launch_envelope(const float *q, int64_t M, int L, int D, int W, float *U, float *Lo, int ldE,
                             cudaStream_t s);
+// envelope in the query-pair interleaved layout of the LB_MV stream:
+// element e of query m at ((m/2)*ldE + e)*2 + m%2, entries e >= L*D set to +-inf
+cudaError_t launch_envelope_pairs(const float *q, int64_t M, int L, int D, int W, float *U, float *Lo, int ldE,
+                                  cudaStream_t s);
 cudaError_t launch_query_dq(const float *q, int64_t M, int L, int D, float *dq_lo, float *dq_hi, cudaStream_t s);
 size_t pc_boxes_smem(int L, int D, int W, int K, int w, int *npow2_out);
 cudaError_t launch_pc_boxes(const float *q, int64_t M, int L, int D, int W, int K, int Lq, int w, float *boxes,
@@ -22,8 +26,8 @@ struct LbMvArgs {
     const float *cand;  // [N][E], E = L*D
     int64_t N;
     int E;
-    const float *U;     // [>=Mb][ldE] envelope, padded with +inf beyond E
-    const float *Lo;    // [>=Mb][ldE] envelope, padded with -inf beyond E
+    const float *U;     // query-pair interleaved envelope [(Mb+1)/2][ldE][2], +inf beyond E
+    const float *Lo;    // likewise, -inf beyond E
     int64_t ldE;        // multiple of 32
     int Mb;
     float *lb;          // [Mb][ldLb]

@@ -26,7 +26,7 @@ cudaError_t launch_check_finite(const float *x, int64_t n, DevStatus *st, int wh
     if (n <= 0) return cudaSuccess;
     int64_t blocks = (n + 255) / 256;
     if (blocks > 4096) blocks = 4096;
-    k_check_finite<<<(int)blocks, 256, 0, s>>>(x, n, st, where);
+    k_check_finite<<<(int)blocks, 256, 0, s>>>(x, n, st, where); note_launch();
     return cudaGetLastError();
 }
 
@@ -39,9 +39,15 @@ cudaError_t launch_check_finite(const float *x, int64_t n, DevStatus *st, int wh
 // and -inf in Lo, so that a padded element never contributes to LB_MV.
 constexpr int kEnvTP = 64;
 
+// Output position of element e of query m: row-major (m*ldE + e) or, for the LB_MV
+// stream, query-pair interleaved (((m/2)*ldE + e)*2 + m%2).
+__device__ __forceinline__ size_t env_pos(int64_t m, int64_t e, int64_t ldE, bool pairs) {
+    return pairs ? (size_t)(((m >> 1) * ldE + e) * 2 + (m & 1)) : (size_t)(m * ldE + e);
+}
+
 template <bool STAGE>
 __global__ void k_envelope(const float *__restrict__ q, int L, int D, int W, float *__restrict__ U,
-                           float *__restrict__ Lo, int64_t ldE, int pad) {
+                           float *__restrict__ Lo, int64_t ldE, int pad, int pairs) {
     extern __shared__ float sh[];
     const int m = blockIdx.y;
     const int t0 = blockIdx.x * kEnvTP;
@@ -62,29 +68,40 @@ __global__ void k_envelope(const float *__restrict__ q, int L, int D, int W, flo
             u = fmaxf(u, v);
             l = fminf(l, v);
         }
-        U[(size_t)m * ldE + (size_t)i * D + p] = u;
-        Lo[(size_t)m * ldE + (size_t)i * D + p] = l;
+        U[env_pos(m, (int64_t)i * D + p, ldE, pairs)] = u;
+        Lo[env_pos(m, (int64_t)i * D + p, ldE, pairs)] = l;
     }
     if (pad && blockIdx.x == 0) {
         for (int64_t k = (int64_t)L * D + threadIdx.x; k < ldE; k += blockDim.x) {
-            U[(size_t)m * ldE + k] = TC_INF;
-            Lo[(size_t)m * ldE + k] = -TC_INF;
+            U[env_pos(m, k, ldE, pairs)] = TC_INF;
+            Lo[env_pos(m, k, ldE, pairs)] = -TC_INF;
         }
     }
 }
 
-cudaError_t launch_envelope(const float *q, int64_t M, int L, int D, int W, float *U, float *Lo, int ldE,
-                            cudaStream_t s) {
+static cudaError_t envelope_impl(const float *q, int64_t M, int L, int D, int W, float *U, float *Lo, int ldE,
+                                 int pairs, cudaStream_t s) {
     if (M <= 0) return cudaSuccess;
     if (W > L - 1) W = L - 1;
     dim3 grid((L + kEnvTP - 1) / kEnvTP, (unsigned)M);
     const size_t sh = (size_t)(kEnvTP + 2 * W) * D * sizeof(float);
     const int pad = ldE > L * D;
     if (sh <= 48 * 1024)
-        k_envelope<true><<<grid, 128, sh, s>>>(q, L, D, W, U, Lo, ldE, pad);
+        k_envelope<true><<<grid, 128, sh, s>>>(q, L, D, W, U, Lo, ldE, pad, pairs);
     else
-        k_envelope<false><<<grid, 128, 0, s>>>(q, L, D, W, U, Lo, ldE, pad);
+        k_envelope<false><<<grid, 128, 0, s>>>(q, L, D, W, U, Lo, ldE, pad, pairs);
+    note_launch();
     return cudaGetLastError();
+}
+
+cudaError_t launch_envelope(const float *q, int64_t M, int L, int D, int W, float *U, float *Lo, int ldE,
+                            cudaStream_t s) {
+    return envelope_impl(q, M, L, D, W, U, Lo, ldE, 0, s);
+}
+
+cudaError_t launch_envelope_pairs(const float *q, int64_t M, int L, int D, int W, float *U, float *Lo, int ldE,
+                                  cudaStream_t s) {
+    return envelope_impl(q, M, L, D, W, U, Lo, ldE, 1, s);
 }
 
 // ------------------------------------------------------------------ neighbour distances
@@ -120,7 +137,7 @@ __global__ void k_query_dq(const float *__restrict__ q, int64_t M, int L, int D,
 cudaError_t launch_query_dq(const float *q, int64_t M, int L, int D, float *dq_lo, float *dq_hi, cudaStream_t s) {
     const int64_t n = M * L;
     if (n <= 0) return cudaSuccess;
-    k_query_dq<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(q, M, L, D, dq_lo, dq_hi);
+    k_query_dq<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(q, M, L, D, dq_lo, dq_hi); note_launch();
     return cudaGetLastError();
 }
 
@@ -150,7 +167,6 @@ __global__ void k_pc_boxes(const float *__restrict__ q, int L, int D, int W, int
     float *mn = (float *)(dkeys + npow2);
     float *len = mn + TCDTW_MAX_D;
     int *box = (int *)(len + TCDTW_MAX_D);
-    __shared__ int ndist;
 
     const float *qm = q + (size_t)m * L * D;
     const int p0 = max(0, g * w - W), p1 = min(L - 1, g * w + w - 1 + W);
@@ -209,7 +225,6 @@ __global__ void k_pc_boxes(const float *__restrict__ q, int L, int D, int W, int
         if (first) dkeys[base + __popc(bal & ((1u << lane) - 1u))] = keys[t];
         base += __popc(bal);
     }
-    if (lane == 0) ndist = base;
     // empty boxes
     const int nb = min(base, K);
     for (int k = lane; k < nb * D; k += 32) {
@@ -268,7 +283,7 @@ cudaError_t launch_pc_boxes(const float *q, int64_t M, int L, int D, int W, int 
     }
     const int G = (L + w - 1) / w;
     dim3 grid(G, (unsigned)M);
-    k_pc_boxes<<<grid, 32, sh, s>>>(q, L, D, W, K, Lq, w, G, np2, boxes, counts);
+    k_pc_boxes<<<grid, 32, sh, s>>>(q, L, D, W, K, Lq, w, G, np2, boxes, counts); note_launch();
     return cudaGetLastError();
 }
 
