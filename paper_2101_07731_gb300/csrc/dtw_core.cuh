@@ -251,16 +251,6 @@ __device__ __forceinline__ float band_pass(const float *__restrict__ A, const fl
             f2 bb[DM];
 #pragma unroll
             for (int p = 0; p < DM; ++p) bb[p] = pk(b[p], b[p]);
-                const bool ok = (vm >> r) & 1u;
-#endif
-                val = ok ? val : INF;
-                diag = left;
-                up = val;
-                col[r] = val;
-                if (Hooks::kCells && ok) hooks.cell(i0 + r, j, val);
-                if (Hooks::kAbandon && (r & 1)) step_min = min3f(step_min, col[r - 1], val);
-            }
-#else
 #pragma unroll
             for (int k = 0; k < RP; ++k) {
                 float c0, c1;
