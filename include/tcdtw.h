@@ -222,6 +222,29 @@ int tcdtw_lower_bounds(const float *q, int64_t M, const float *c, int64_t N, int
                        int32_t W, int32_t K, const tcdtw_opts *opts, int32_t which, float *out,
                        void *stream);
 
+/*
+ * tcdtw_lb_mv_noalloc -- the same values as tcdtw_lower_bounds(..., TCDTW_LB_MV, ...)
+ * (all M*N LB_MV bounds, rounded down, out device [M][N] float32), but without any
+ * device allocation.  The paper has no counterpart: this is a deployment variant.
+ * Who needs it: code that runs while a stream is being captured into a CUDA graph
+ * (cudaMalloc is not a stream operation and is refused during capture), serving
+ * loops that must not stall (cudaMalloc / cudaFree can synchronise the whole device),
+ * and processes whose device memory is owned by a caching allocator or a fixed
+ * budget, where a raw cudaMalloc can fail although the application has memory.
+ * The envelope scratch is a fixed array inside the library (8 MiB: two halves of
+ * 2^20 floats); each loaded device keeps it until the process exits.  Limit:
+ * 2*ceil(M/2) * ceil32(L*D) <= 2^20, else TCDTW_ERR_UNSUPPORTED (no work is done).
+ * The first call on a device resolves the array's device address (set-up, once per
+ * device, with that device current): make that first call before any stream capture.
+ * Every call uses the same array, and the scratch keeps the last call's contents
+ * (each call rewrites every element it reads, so nothing needs clearing): calls whose
+ * kernels overlap on the GPU (different streams, or different host threads) race on
+ * it and must be serialised by the caller.  Asynchronous on `stream`.
+ * Errors: INVALID, UNSUPPORTED (too large), CUDA.
+ */
+int tcdtw_lb_mv_noalloc(const float *q, int64_t M, const float *c, int64_t N, int32_t L, int32_t D, int32_t W,
+                        float *out, void *stream);
+
 /* Survivor compaction: for each row m of lb [M][N], the column indices n with
  * lb[m][n] <= thresh[m], in increasing n, written to out_idx[m][0 .. count[m]-1]
  * (out_idx device [M][N] int32, count device [M] int32).  Errors: INVALID, CUDA. */

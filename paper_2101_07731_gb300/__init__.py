@@ -79,6 +79,7 @@ _SIGS = {
     "tcdtw_lower_bounds": (C.c_int, [_P, _I64, _P, _I64, _I32, _I32, _I32, _I32, C.POINTER(Opts), _I32, _P,
                                      _P]),
     "tcdtw_compact": (C.c_int, [_P, _I64, _I64, _P, _P, _P, _P]),
+    "tcdtw_lb_mv_noalloc": (C.c_int, [_P, _I64, _P, _I64, _I32, _I32, _I32, _P, _P]),
     "tcdtw_batch_nn": (C.c_int, [C.POINTER(Dataset), _I32, C.POINTER(Opts), C.POINTER(Stats), _P]),
     "tcdtw_tile_count": (C.c_int, []),
     "tcdtw_set_profiling": (C.c_int, [_P, _I32]),
@@ -344,3 +345,17 @@ def compact(lb: torch.Tensor, thresh: torch.Tensor):
     cnt = torch.empty(M, dtype=torch.int32, device=lb.device)
     _call("tcdtw_compact", _ptr(lb), M, N, _ptr(thresh), _ptr(idx), _ptr(cnt), _stream())
     return idx, cnt
+
+
+def lb_mv_noalloc(q: torch.Tensor, c: torch.Tensor, W: int, out: torch.Tensor | None = None):
+    """LB_MV of every (query, candidate) pair with no device allocation inside the
+    library (scratch in a fixed in-library array; see tcdtw_lb_mv_noalloc for who
+    needs that and for the size limit).  Pass ``out`` ([M][N] float32, on the GPU)
+    to avoid the one allocation this wrapper would otherwise make."""
+    q, c = _series(q, "q"), _series(c, "c")
+    M, L, D = q.shape
+    N = c.shape[0]
+    if out is None:
+        out = torch.empty(M, N, dtype=torch.float32, device=q.device)
+    _call("tcdtw_lb_mv_noalloc", _ptr(q), M, _ptr(c), N, L, D, int(W), _ptr(out), _stream())
+    return out
