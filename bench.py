@@ -204,8 +204,9 @@ def run_ours(a):
         if dist is not None:
             dist.barrier()
 
+    out = (torch.empty(wl.M, dtype=torch.int64, device=dev), torch.empty(wl.M, dtype=torch.float64, device=dev))
     for _ in range(a.warmup):
-        index.nn(q)
+        index.nn(q, out=out)
     torch.cuda.synchronize()
     _, _, st = index.nn(q, stats=True)
 
@@ -219,7 +220,7 @@ def run_ours(a):
         for k in range(a.steps):
             flush.zero_()
             ev[k][0].record(stream)
-            index.nn(q)
+            index.nn(q, out=out)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -250,6 +251,7 @@ def run_ours(a):
                        "pruned_pc": st["pruned_pc"], "pruned_ti": st["pruned_ti"],
                        "dtw_abandoned": st["dtw_abandoned"], "cells": st["cells"], "refined": st["refined"]},
            "stage_ms_per_step": {k: v / a.steps for k, v in stage_ms.items()},
+           "dtw_tile": index.info(),
            "gpu_launches": int(launches)}
     res["clocks"] = clocks.summary()
 
@@ -331,6 +333,27 @@ def run_ours(a):
         res["e2e"] = {"value": world * wl.M * a.steps / (tot / 1e3), "unit": "queries/s",
                       "h2d_bytes_per_step": int(qh.numel() * 4), "d2h_bytes_per_step": int(wl.M * 16)}
     index.close()
+
+    if not a.no_extra:
+        # ---- latency of a small search (16 queries x 256 candidates, L=128, D=3, W=13):
+        # launch-bound; repeated calls on the same buffers replay a CUDA graph
+        sw = synth.RW_16x256_L128
+        sc = torch.from_numpy(sw.candidates()).to(dev)
+        sq = torch.from_numpy(sw.queries()).to(dev)
+        small = tc.Index(sc, sw.W, sw.K)
+        sout = (torch.empty(sw.M, dtype=torch.int64, device=dev), torch.empty(sw.M, dtype=torch.float64, device=dev))
+        for _ in range(5):
+            small.nn(sq, out=sout)
+        torch.cuda.synchronize()
+        reps = 50
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            small.nn(sq, out=sout)
+        torch.cuda.synchronize()
+        lat = (time.perf_counter() - t0) / reps
+        res["small_workload"] = {"workload": sw.name, "ms_per_call": lat * 1e3, "queries_per_s": sw.M / lat,
+                                 "note": "host wall time per tcdtw_nn call (graph replay, synchronous)"}
+        small.close()
 
     if rank == 0 and world == 1 and not a.no_cpu:
         qps, cores, sample, secs = cpu_oracle_sample(Qn, Cn, wl.W, wl.K, a.cpu_seconds)

@@ -66,6 +66,8 @@ typedef struct tcdtw_index tcdtw_index; /* opaque; created by tcdtw_build */
  *  no_prune  1 = the "default windowed DTW without lower bounds" the paper measures
  *          its speedups against (Section 7.2): the full DTW of every pair, no bound,
  *          no abandoning; the answer is the same (0).
+ *  use_graph  1 = tcdtw_nn replays a captured CUDA graph of its kernel sequence when
+ *          called again with the same (q, M, idx, dist) (1).
  */
 typedef struct {
     int32_t P;
@@ -80,6 +82,7 @@ typedef struct {
     int32_t tile;
     int32_t check_finite;
     int32_t no_prune;
+    int32_t use_graph;
 } tcdtw_opts;
 
 /* Counters of one tcdtw_nn call, summed over its queries. */
@@ -279,6 +282,10 @@ int tcdtw_tile_info(int32_t t, int32_t *G, int32_t *R, int32_t *maxD);
 
 /* Static message for an error code. */
 const char *tcdtw_strerror(int code);
+
+/* Name and message of the last CUDA runtime error this thread's calls returned as
+ * TCDTW_ERR_CUDA or TCDTW_ERR_NOMEM ("" if none); valid until the thread's next such error. */
+const char *tcdtw_last_error_detail(void);
 
 #ifdef __cplusplus
 }

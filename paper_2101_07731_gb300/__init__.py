@@ -38,6 +38,10 @@ def lib_path() -> str:
 class TcdtwError(RuntimeError):
     def __init__(self, code: int, where: str):
         msg = _load().tcdtw_strerror(code).decode() if _lib is not None else str(code)
+        if code in (2, 3) and _lib is not None:
+            detail = _lib.tcdtw_last_error_detail().decode()
+            if detail:
+                msg += f" [{detail}]"
         super().__init__(f"{where}: {msg} (code {code})")
         self.code = code
 
@@ -46,7 +50,7 @@ class Opts(C.Structure):
     _fields_ = [("P", C.c_int32), ("Lq", C.c_int32), ("w", C.c_int32), ("e_pc", C.c_float),
                 ("e_ti", C.c_float), ("use_pc", C.c_int32), ("use_ti", C.c_int32),
                 ("seed_s", C.c_int32), ("qblock", C.c_int32), ("tile", C.c_int32),
-                ("check_finite", C.c_int32), ("no_prune", C.c_int32)]
+                ("check_finite", C.c_int32), ("no_prune", C.c_int32), ("use_graph", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -67,6 +71,7 @@ _P, _I32, _I64, _F = C.c_void_p, C.c_int32, C.c_int64, C.c_float
 _SIGS = {
     "tcdtw_default_opts": (None, [C.POINTER(Opts)]),
     "tcdtw_strerror": (C.c_char_p, [C.c_int]),
+    "tcdtw_last_error_detail": (C.c_char_p, []),
     "tcdtw_build": (C.c_int, [_P, _I64, _I32, _I32, _I32, _I32, C.POINTER(Opts), _P, C.POINTER(_P)]),
     "tcdtw_nn": (C.c_int, [_P, _P, _I64, _P, _P, C.POINTER(Stats), _P]),
     "tcdtw_free": (None, [_P]),
@@ -223,15 +228,22 @@ class Index:
               C.byref(h))
         self._h = h
 
-    def nn(self, q: torch.Tensor, stats: bool = False):
+    def nn(self, q: torch.Tensor, stats: bool = False, out=None):
         """(idx int64 [M], dist float64 [M]) of each query's nearest candidate;
-        with ``stats=True`` also the search counters (synchronises)."""
+        with ``stats=True`` also the search counters (synchronises).  ``out`` =
+        (idx, dist) reuses caller buffers; calls repeated with the same query and
+        output buffers replay a captured CUDA graph."""
         q = _series(q, "q")
         if q.shape[1:] != (self.L, self.D):
             raise ValueError("query shape must be [M][L][D] with the index's L and D")
         M = q.shape[0]
-        idx = torch.empty(M, dtype=torch.int64, device=q.device)
-        dist = torch.empty(M, dtype=torch.float64, device=q.device)
+        if out is not None:
+            idx, dist = out
+            if idx.dtype != torch.int64 or dist.dtype != torch.float64 or idx.numel() < M or dist.numel() < M:
+                raise ValueError("out must be (int64 [M], float64 [M]) tensors")
+        else:
+            idx = torch.empty(M, dtype=torch.int64, device=q.device)
+            dist = torch.empty(M, dtype=torch.float64, device=q.device)
         st = Stats()
         _call("tcdtw_nn", self._h, _ptr(q), M, _ptr(idx), _ptr(dist), C.byref(st) if stats else None, _stream())
         return (idx, dist, st.as_dict()) if stats else (idx, dist)

@@ -12,4 +12,5 @@ int blocks_for(int tile, int which, int64_t groups, int G);
 int ckpt_rows(int L, int W);
 int64_t ckpt_floats(int64_t P, int L, int W);
 int cuda_err(cudaError_t e);
+const char *last_detail();
 }  // namespace tc

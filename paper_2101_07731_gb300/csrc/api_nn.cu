@@ -166,6 +166,23 @@ struct tcdtw_index {
     int marks_used = 0;
     double stage_ms[TCDTW_NUM_STAGES] = {0};
     int64_t stage_blocks = 0;
+    // CUDA graphs of the per-call kernel sequence, keyed by the call's pointers
+    struct GraphEntry {
+        const float *q;
+        int64_t M;
+        int64_t *idx;
+        double *dist;
+        int seen;                      // eager calls made with this key
+        cudaGraphExec_t exec;          // null until captured
+        unsigned long long last_use;
+        int marks;                     // profiling event marks recorded by the graph
+        bool profiled;                 // captured with profiling on
+        int kernels;                   // kernel launches captured in the graph
+    };
+    std::vector<GraphEntry> graphs;
+    unsigned long long graph_clock = 0;
+    cudaStream_t cap_stream = nullptr;
+    bool capturing = false;
 };
 
 namespace {
@@ -173,6 +190,9 @@ namespace {
 void free_index(tcdtw_index *x) {
     if (!x) return;
     for (cudaEvent_t ev : x->events) cudaEventDestroy(ev);
+    for (auto &g : x->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (x->cap_stream) cudaStreamDestroy(x->cap_stream);
     void *ptrs[] = {x->U, x->Lo, x->dq_lo, x->dq_hi, x->boxes, x->lbm, x->box_counts, x->seeds, x->surv,
                     x->refine, x->seed_dtw, x->surv_lb, x->surv_dtw, x->refine_d64, x->row_counts,
                     x->row_offsets, x->scalars, x->bsf, x->best64, x->best_idx, x->counters, x->status};
@@ -238,6 +258,8 @@ cudaError_t mark(tcdtw_index *x, int k, cudaStream_t s) {
     }
     (void)k;
     ++x->marks_used;
+    // while capturing, an external record becomes a timing node of the graph
+    if (x->capturing) return cudaEventRecordWithFlags(x->events[slot], s, cudaEventRecordExternal);
     return cudaEventRecord(x->events[slot], s);
 }
 
@@ -336,6 +358,68 @@ cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_o
     return cudaSuccess;
 }
 
+// All query blocks of one call.  With use_graph, a key (q, M, idx, dist) seen once
+// before is captured into a CUDA graph (on an internal stream) and replayed on s;
+// the first call of a key runs eagerly so that any one-time setup (function
+// attributes, lazy module loading) happens outside capture.
+cudaError_t run_all_blocks(tcdtw_index *x, const float *q, int64_t M, int64_t *idx, double *dist, cudaStream_t s) {
+    const int64_t E = (int64_t)x->L * x->D;
+    auto eager = [&](cudaStream_t st) -> cudaError_t {
+        for (int64_t m0 = 0; m0 < M; m0 += x->Mb) {
+            const int Mb_cur = (int)((M - m0) < x->Mb ? (M - m0) : x->Mb);
+            cudaError_t e = run_block(x, q + m0 * E, Mb_cur, idx + m0, dist + m0, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
+    if (!x->opts.use_graph) return eager(s);
+    tcdtw_index::GraphEntry *ent = nullptr;
+    for (auto &g : x->graphs)
+        if (g.q == q && g.M == M && g.idx == idx && g.dist == dist && g.profiled == x->profile) ent = &g;
+    if (!ent) {
+        if (x->graphs.size() >= 8) {  // drop the least recently used key
+            size_t lru = 0;
+            for (size_t k = 1; k < x->graphs.size(); ++k)
+                if (x->graphs[k].last_use < x->graphs[lru].last_use) lru = k;
+            if (x->graphs[lru].exec) cudaGraphExecDestroy(x->graphs[lru].exec);
+            x->graphs.erase(x->graphs.begin() + lru);
+        }
+        x->graphs.push_back({q, M, idx, dist, 0, nullptr, 0, 0, x->profile, 0});
+        ent = &x->graphs.back();
+    }
+    ent->last_use = ++x->graph_clock;
+    if (!ent->exec && ent->seen == 0) {
+        ent->seen = 1;
+        return eager(s);
+    }
+    if (!ent->exec) {
+        cudaError_t e;
+        if (!x->cap_stream && (e = cudaStreamCreateWithFlags(&x->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return e;
+        // order the capture stream after the caller's prior work on s
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+        if ((e = cudaStreamBeginCapture(x->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+        x->marks_used = 0;
+        x->capturing = true;
+        const uint64_t k0 = tcdtw_kernel_launches();
+        cudaError_t run = eager(x->cap_stream);
+        ent->kernels = (int)(tcdtw_kernel_launches() - k0);
+        note_launches(-(int64_t)ent->kernels);  // captured, not launched yet
+        x->capturing = false;
+        ent->marks = x->marks_used;
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(x->cap_stream, &graph);
+        if (run != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return run; }
+        if (e != cudaSuccess) return e;
+        e = cudaGraphInstantiate(&ent->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) { ent->exec = nullptr; return e; }
+    }
+    x->marks_used = ent->marks;  // the graph records these profiling events
+    note_launches(ent->kernels);   // kernels the replay launches
+    return cudaGraphLaunch(ent->exec, s);
+}
+
 }  // namespace
 
 extern "C" {
@@ -421,10 +505,7 @@ int tcdtw_nn(tcdtw_index *x, const float *q, int64_t M, int64_t *idx, double *di
         TC_TRY(cudaMemsetAsync(x->counters, 0, sizeof(unsigned long long) * kNumCounters, s));
         TC_TRY(cudaMemsetAsync(x->status, 0, sizeof(DevStatus), s));
     }
-    for (int64_t m0 = 0; m0 < M; m0 += x->Mb) {
-        const int Mb_cur = (int)((M - m0) < x->Mb ? (M - m0) : x->Mb);
-        TC_TRY(run_block(x, q + m0 * E, Mb_cur, idx + m0, dist + m0, s));
-    }
+    TC_TRY(run_all_blocks(x, q, M, idx, dist, s));
     if (!sync) return TCDTW_OK;
     TC_TRY(cudaStreamSynchronize(s));
     if (x->profile) {

@@ -5,6 +5,7 @@
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
+#include <stdio.h>
 #include <string.h>
 
 #include "api_internal.h"
@@ -17,6 +18,7 @@ namespace tc {
 
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(int64_t n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
 int num_sms() {
     static int sms = 0;
@@ -117,11 +119,17 @@ int64_t ckpt_floats(int64_t P, int L, int W) {
     return P * (int64_t)nck * (2 * W + 1);
 }
 
+// Last CUDA error seen by this thread (name and message), for tcdtw_last_error_detail.
+static thread_local char g_last_detail[256];
+
 int cuda_err(cudaError_t e) {
     if (e == cudaSuccess) return TCDTW_OK;
+    snprintf(g_last_detail, sizeof(g_last_detail), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
     if (e == cudaErrorMemoryAllocation) return TCDTW_ERR_NOMEM;
     return TCDTW_ERR_CUDA;
 }
+
+const char *last_detail() { return g_last_detail; }
 
 }  // namespace tc
 
@@ -143,6 +151,7 @@ void tcdtw_default_opts(tcdtw_opts *o) {
     o->tile = -1;
     o->check_finite = 1;
     o->no_prune = 0;
+    o->use_graph = 1;
 }
 
 const char *tcdtw_strerror(int code) {
@@ -159,6 +168,8 @@ const char *tcdtw_strerror(int code) {
 }
 
 int tcdtw_tile_count(void) { return kNumTiles; }
+
+const char *tcdtw_last_error_detail(void) { return last_detail(); }
 
 uint64_t tcdtw_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 

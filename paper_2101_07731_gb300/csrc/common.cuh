@@ -54,6 +54,7 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 // Host-side count of kernel launches issued by the library (tcdtw_kernel_launches).
 void note_launch();
+void note_launches(int64_t n);  // graph replays: kernels in the replayed graph
 
 }  // namespace tc
 

@@ -222,3 +222,22 @@ def test_nn_proto_256x20000_L256_D5_W26_sampled():
     assert st["pruned_mv"] + st["pruned_pc"] + st["pruned_ti"] + st["dtw_started"] == st["pairs"]
     # pruning must avoid most DTWs on this prototype data
     assert st["dtw_started"] < 0.5 * st["pairs"]
+
+
+def test_nn_graph_replay_with_new_query_contents():
+    """Repeated calls with the same buffers run eagerly once, then capture and
+    replay a CUDA graph; the graph reads whatever the buffers hold at replay time."""
+    spec = synth.SeriesSpec("proto_warp", 80, 4, 27, n_proto=5, sigma=0.1)
+    Cn = synth.generate(spec, synth.ROLE_CAND, 900)
+    index = tc.Index(_gpu(Cn), 8, 8)
+    q = torch.empty(19, 80, 4, dtype=torch.float32, device=DEV)
+    idx = torch.empty(19, dtype=torch.int64, device=DEV)
+    dist = torch.empty(19, dtype=torch.float64, device=DEV)
+    for rep in range(4):
+        Qn = synth.generate(spec, synth.ROLE_QUERY, 19, start=19 * rep)
+        q.copy_(torch.from_numpy(Qn))
+        index.nn(q, out=(idx, dist))
+        ridx, rdist = O.nn_brute(Qn, Cn, 8)
+        assert np.array_equal(idx.cpu().numpy(), ridx), rep
+        np.testing.assert_allclose(dist.cpu().numpy(), rdist, rtol=RTOL, atol=0)
+    index.close()
