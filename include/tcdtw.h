@@ -256,24 +256,47 @@ int tcdtw_compact(const float *lb, int64_t M, int64_t N, const float *thresh, in
 
 /*
  * Batched search: many independent (candidate set, query set) problems of uneven
- * L, D, N, W in one persistent launch off a device work queue (not in the paper).
- * Each entry is searched exactly as tcdtw_nn would (same bounds, same exactness).
+ * L, D, N, W in one persistent launch off a device work queue (not in the paper; a
+ * deployment pattern).  Each entry is searched exactly as tcdtw_nn would search it
+ * (same bounds, same rounding margins, same FP64 refine), so idx/dist are the exact
+ * nearest neighbours under Eq. (1) with the band |i-j| <= W.
+ *
+ * Work items, in queue order: per query its envelope / neighbour distances / LB_PC
+ * boxes; per 32-query x 128-candidate tile its LB_MV bounds; per query the rest of
+ * the cascade (seeds, compaction, gated LB_PC and LB_TI, banded DTW with early
+ * abandoning, FP64 refine).  Items of one set wait for the earlier items they need on
+ * device counters; each wait gives up after about a second, and the call then
+ * returns TIMEOUT.  Entries with D > 12 or W beyond the FP64 refine's band are
+ * searched through tcdtw_build / tcdtw_nn, one after another, after the launch.
+ * The launch and its workspace are kept per distinct batch (the descriptors and
+ * opts, byte for byte; up to 4 batches): the second call with the same batch
+ * captures the launch into a CUDA graph (opts->use_graph), later calls replay it.
  */
 typedef struct {
-    const float *cand; /* device [N][L][D] */
+    const float *cand; /* device [N][L][D], row-major, N >= 1 */
     int64_t N;
-    int32_t L, D, W, K;
+    int32_t L, D, W, K; /* L >= 1, 1 <= D <= 64, W >= 0 (clamped to L-1), K >= 1 */
     const float *q;    /* device [M][L][D] */
-    int64_t M;
-    int64_t *idx;      /* device [M] */
-    double *dist;      /* device [M] */
+    int64_t M;         /* M >= 0; M == 0: entry skipped */
+    int64_t *idx;      /* device [M], output */
+    double *dist;      /* device [M], output */
 } tcdtw_dataset;
 
-/* sets: HOST array of nsets descriptors.  opts: NULL = defaults.  stats: host, may
- * be NULL (summed over all sets; synchronises when given).
- * Errors: INVALID, NOMEM, CUDA, NONFINITE, TIMEOUT, UNSUPPORTED. */
+/* sets: HOST array of nsets descriptors (the library keeps none of the pointers
+ * beyond the cached launch, which re-reads the same device buffers on replay).
+ * opts: NULL = defaults.  stats: host, may be NULL (summed over all sets).
+ * The call is synchronous on `stream` (it reads the launch's device status word).
+ * Errors: INVALID, NOMEM, CUDA, NONFINITE, TIMEOUT, UNSUPPORTED (D > 64). */
 int tcdtw_batch_nn(const tcdtw_dataset *sets, int32_t nsets, const tcdtw_opts *opts,
                    tcdtw_stats *stats, void *stream);
+
+/* Failure-detection self-test of the batched launch (no counterpart in the paper):
+ * one persistent launch whose only work item waits for a device counter that
+ * nothing increments, with a limit of spin_limit sleeps of ~256 ns.  The wait runs
+ * out, the launch records TIMEOUT in its status word and returns; the context stays
+ * usable.  Returns TIMEOUT on success of the self-test, INVALID for spin_limit < 1,
+ * CUDA on a runtime error.  Synchronous on `stream`. */
+int tcdtw_batch_selftest_timeout(int64_t spin_limit, void *stream);
 
 /* Number of compiled DTW band tiles, and the shape of tile t: G lanes per pair,
  * R rows per lane (host outputs).  Returns INVALID for an unknown t. */

@@ -20,7 +20,7 @@ import os
 
 import torch
 
-__all__ = ["Index", "dtw", "dtw_pairs", "dtw_pairs_backward", "batch_nn", "envelope", "query_dq",
+__all__ = ["Index", "dtw", "dtw_pairs", "dtw_pairs_backward", "batch_nn", "batch_selftest_timeout", "envelope", "query_dq",
            "pc_boxes", "lower_bounds", "compact", "Opts", "Stats", "TcdtwError", "lib_path",
            "LB_MV", "LB_PC", "LB_TI", "default_opts"]
 
@@ -29,6 +29,8 @@ _LIB_PATH = os.path.join(_PKG, "libtcdtw.so")
 _lib = None
 
 LB_MV, LB_PC, LB_TI = 0, 1, 2
+# status codes of the C ABI (tcdtw.h)
+OK, ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_NONFINITE, ERR_UNSUPPORTED = range(7)
 
 
 def lib_path() -> str:
@@ -86,6 +88,7 @@ _SIGS = {
     "tcdtw_compact": (C.c_int, [_P, _I64, _I64, _P, _P, _P, _P]),
     "tcdtw_lb_mv_noalloc": (C.c_int, [_P, _I64, _P, _I64, _I32, _I32, _I32, _P, _P]),
     "tcdtw_batch_nn": (C.c_int, [C.POINTER(Dataset), _I32, C.POINTER(Opts), C.POINTER(Stats), _P]),
+    "tcdtw_batch_selftest_timeout": (C.c_int, [_I64, _P]),
     "tcdtw_tile_count": (C.c_int, []),
     "tcdtw_set_profiling": (C.c_int, [_P, _I32]),
     "tcdtw_stage_times": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(_I64)]),
@@ -286,17 +289,32 @@ def kernel_launches() -> int:
     return int(_load().tcdtw_kernel_launches())
 
 
-def batch_nn(sets, stats: bool = False, **opts):
+def batch_nn(sets, stats: bool = False, out=None, **opts):
     """Search many independent (cand, q, W, K) problems in one persistent launch.
     ``sets``: iterable of dicts with keys cand, q, W and optionally K (16).
+    ``out``: optional list of (idx int64 [M], dist float64 [M]) device tensors, one
+    pair per set, written in place (the launch is cached per batch description, so
+    reusing the same tensors lets later calls replay a captured graph).
     Returns a list of (idx, dist) per set (and the summed counters if stats)."""
+    sets = list(sets)
+    if out is not None and len(out) != len(sets):
+        raise ValueError("out must hold one (idx, dist) pair per set")
     descs, outs, keep = [], [], []
-    for s in sets:
+    for k, s in enumerate(sets):
         cand, q = _series(s["cand"], "cand"), _series(s["q"], "q")
         N, L, D = cand.shape
         M = q.shape[0]
-        idx = torch.empty(M, dtype=torch.int64, device=q.device)
-        dist = torch.empty(M, dtype=torch.float64, device=q.device)
+        if q.shape[1:] != cand.shape[1:]:
+            raise ValueError(f"set {k}: query and candidate series differ in shape")
+        if out is not None:
+            idx, dist = out[k]
+            if (idx.dtype != torch.int64 or dist.dtype != torch.float64 or idx.numel() != M
+                    or dist.numel() != M or not idx.is_contiguous() or not dist.is_contiguous()
+                    or idx.device != q.device or dist.device != q.device):
+                raise ValueError(f"set {k}: out must be contiguous int64 / float64 [M] on the queries' device")
+        else:
+            idx = torch.empty(M, dtype=torch.int64, device=q.device)
+            dist = torch.empty(M, dtype=torch.float64, device=q.device)
         descs.append(Dataset(cand.data_ptr(), N, L, D, int(s["W"]), int(s.get("K", 16)), q.data_ptr(), M,
                              idx.data_ptr(), dist.data_ptr()))
         outs.append((idx, dist))
@@ -306,6 +324,12 @@ def batch_nn(sets, stats: bool = False, **opts):
     st = Stats()
     _call("tcdtw_batch_nn", arr, len(descs), C.byref(o), C.byref(st) if stats else None, _stream())
     return (outs, st.as_dict()) if stats else outs
+
+
+def batch_selftest_timeout(spin_limit: int = 200000) -> int:
+    """Run the batched launch's wait-limit self-test; returns the status code
+    (TIMEOUT when the device-side wait ran out and the launch ended by itself)."""
+    return int(_load().tcdtw_batch_selftest_timeout(int(spin_limit), _stream()))
 
 
 # ----------------------------------------------------------------- pipeline stages

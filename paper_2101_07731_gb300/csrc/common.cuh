@@ -45,6 +45,17 @@ __device__ __forceinline__ float prune_threshold(unsigned long long key, float r
     return rho == __int_as_float(0x7f800000) ? rho : __fmul_ru(best_dist(key), rho);
 }
 
+// ---------------------------------------------------------------- packed FP32 pairs
+typedef unsigned long long f2;  // two floats: low word first
+__device__ __forceinline__ f2 pk(float lo, float hi) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
 // ---------------------------------------------------------------- three-way min/max
 __device__ __forceinline__ float fmin3(float a, float b, float c) { return fminf(fminf(a, b), c); }
 __device__ __forceinline__ float fmax3(float a, float b, float c) { return fmaxf(fmaxf(a, b), c); }

@@ -13,71 +13,6 @@ namespace tc {
 
 TC_TILES(TC_TILE_DECL)
 
-// ------------------------------------------------------------------ FP64 band pass
-template <int R>
-__device__ double band_pass64(const float *__restrict__ A, const float *__restrict__ B, int L, int D, int W,
-                              const Grp &g) {
-    const double INF = __longlong_as_double(0x7ff0000000000000LL);
-    double col[R];
-    double bottom = INF, prev_in = INF, result = INF;
-    const int nv = (L + R - 1) / R;
-    const int vlast = (L - 1) / R;
-    int v = g.lig;
-    const int tau0 = 0;
-    const int tau_end = v_jhi(nv - 1, R, W, L) + (nv - 1);
-    int tlo = v < nv ? v_jlo(v, R, W) + v : 1 << 30;
-    int thi = v < nv ? v_jhi(v, R, W, L) + v : -1;
-    bool fresh = true;
-    for (int tau = tau0; tau <= tau_end; ++tau) {
-        const double in = __shfl_sync(g.mask, bottom, g.src);
-        if (tau > thi && v < nv) {
-            v += g.G;
-            fresh = true;
-            tlo = v < nv ? v_jlo(v, R, W) + v : 1 << 30;
-            thi = v < nv ? v_jhi(v, R, W, L) + v : -1;
-        }
-        if (tau >= tlo && tau <= thi) {
-            const int j = tau - v;
-            const int i0 = v * R;
-            if (fresh) {
-#pragma unroll
-                for (int r = 0; r < R; ++r) col[r] = INF;
-                fresh = false;
-            }
-            double up = (v == 0) ? INF : ((j <= i0 - 1 + W) ? in : INF);
-            double diag = (v == 0) ? ((j == 0) ? 0.0 : INF) : ((j >= 1 && j <= i0 + W) ? prev_in : INF);
-            const unsigned vm = row_mask(j - W - i0, min(j + W - i0, L - 1 - i0), R);
-            const float *bj = B + (size_t)j * D;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const double left = col[r];
-                double val = INF;
-                if ((vm >> r) & 1u) {
-                    const float *ai = A + (size_t)(i0 + r) * D;
-                    double s = 0.0;
-                    for (int p = 0; p < D; ++p) {
-                        const double t = __dsub_rn((double)__ldg(ai + p), (double)__ldg(bj + p));
-                        s = __dadd_rn(s, __dmul_rn(t, t));
-                    }
-                    val = __dadd_rn(s, fmin(fmin(up, left), diag));
-                }
-                diag = left;
-                up = val;
-                col[r] = val;
-            }
-            bottom = col[R - 1];
-            if (v == vlast && j == L - 1) {
-                const int rl = (L - 1) - i0;
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-                    if (r == rl) result = col[r];
-            }
-        }
-        prev_in = in;
-    }
-    return result;
-}
-
 // Entries e < *count: pair id m*N + n; stores the FP64 DTW in d64[e] and lowers
 // best64[m] (bit pattern of a non-negative double orders like its value).
 template <int R>

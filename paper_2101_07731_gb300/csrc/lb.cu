@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "lb_device.cuh"
 #include "lb_kernels.cuh"
 
 namespace tc {
@@ -27,106 +28,6 @@ namespace tc {
 // acc += m*m rounded down; the subtractions and the multiply-adds of two queries go
 // in one packed f32x2 instruction each.  Sums are two-level (32 elements of a chunk,
 // then the chunk sums), so a round-down chain is at most 32 + E/32 long.
-constexpr int kMvRows = 128;
-constexpr int kMvChunk = 32;
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
-    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes));
-}
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem, int src_bytes) {
-    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-
-typedef unsigned long long f2;
-__device__ __forceinline__ f2 pk(float lo, float hi) {
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void upk(f2 v, float &lo, float &hi) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ f2 sub2_rd(f2 a, f2 b) {
-    f2 r;
-    asm("sub.rm.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2 fma2_rd(f2 a, f2 b, f2 c) {
-    f2 r;
-    asm("fma.rm.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-__device__ __forceinline__ f2 add2_rd(f2 a, f2 b) {
-    f2 r;
-    asm("add.rm.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ float max3f(float a, float b, float c) {
-    float r;
-    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
-}
-
-// squared distance of x to [lo, hi], rounded down, accumulated into acc
-__device__ __forceinline__ float acc_box(float x, float lo, float hi, float acc) {
-    const float m = max3f(__fsub_rd(x, hi), __fsub_rd(lo, x), 0.f);
-    return __fmaf_rd(m, m, acc);
-}
-
-// one packed step: element value c2 = {x, x} against two queries' (U, Lo)
-__device__ __forceinline__ f2 mv_step(f2 c2, float u0, float u1, float l0, float l1, f2 part) {
-    float a0, a1, b0, b1;
-    upk(sub2_rd(c2, pk(u0, u1)), a0, a1);
-    upk(sub2_rd(pk(l0, l1), c2), b0, b1);
-    const float m0 = max3f(a0, b0, 0.f), m1 = max3f(a1, b1, 0.f);
-    const f2 m2 = pk(m0, m1);
-    return fma2_rd(m2, m2, part);
-}
-
-template <int QB>
-__device__ __forceinline__ void mv_issue(const float *__restrict__ cand, int64_t N, int E, bool vec4,
-                                         const float *UI, const float *LI, int64_t ldE, int n_qp, int64_t n0, int q0,
-                                         int e0, float *sc, float *su, float *sl) {
-    const int tid = threadIdx.x;
-    if (vec4) {
-#pragma unroll
-        for (int k = 0; k < (kMvRows * 8) / 128; ++k) {
-            const int idx = tid + 128 * k;
-            const int row = idx >> 3, seg = idx & 7;
-            const int64_t n = n0 + row;
-            const int e = e0 + seg * 4;
-            const bool ok = n < N && e < E;
-            const float *src = ok ? cand + (size_t)n * E + e : cand;
-            cp_async16(sc + row * kMvChunk + ((seg ^ (row & 7)) << 2), src, ok ? 16 : 0);
-        }
-    } else {
-        for (int k = 0; k < kMvRows * kMvChunk / 128; ++k) {
-            const int idx = tid + 128 * k;
-            const int row = idx >> 5, el = idx & 31;
-            const int64_t n = n0 + row;
-            const int e = e0 + el;
-            const bool ok = n < N && e < E;
-            const float *src = ok ? cand + (size_t)n * E + e : cand;
-            const int seg = el >> 2;
-            cp_async4(sc + row * kMvChunk + ((seg ^ (row & 7)) << 2) + (el & 3), src, ok ? 4 : 0);
-        }
-    }
-    // envelope chunk: QB/2 query pairs x 32 elements x 2 floats (256 bytes), U and Lo
-    for (int idx = tid; idx < (QB / 2) * 16 * 2; idx += 128) {
-        const int which = idx / ((QB / 2) * 16);
-        const int r = idx % ((QB / 2) * 16);
-        const int qp = r >> 4, seg = r & 15;
-        const int qpg = min(q0 / 2 + qp, n_qp - 1);
-        const float *src = (which ? LI : UI) + ((size_t)qpg * ldE + e0) * 2 + seg * 4;
-        cp_async16((which ? sl : su) + qp * 2 * kMvChunk + seg * 4, src, 16);
-    }
-}
-
 template <int QB>
 __global__ void __launch_bounds__(128) k_lb_mv(const float *__restrict__ cand, int64_t N, int E, int vec4,
                                                const float *__restrict__ UI, const float *__restrict__ LI,
@@ -135,65 +36,10 @@ __global__ void __launch_bounds__(128) k_lb_mv(const float *__restrict__ cand, i
     __shared__ __align__(16) float sc[2][kMvRows * kMvChunk];
     __shared__ __align__(16) float su[2][QB * kMvChunk];
     __shared__ __align__(16) float sl[2][QB * kMvChunk];
-    const int tid = threadIdx.x;
-    const int nchunks = (E + kMvChunk - 1) / kMvChunk;
     const int ntiles = n_ctiles * n_qtiles;
-    const int n_qp = (Mb + 1) / 2;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int ct = tile / n_qtiles, qt = tile % n_qtiles;
-        const int64_t n0 = (int64_t)ct * kMvRows;
-        const int q0 = qt * QB;
-        f2 acc[QB / 2];
-#pragma unroll
-        for (int k = 0; k < QB / 2; ++k) acc[k] = 0ull;
-        mv_issue<QB>(cand, N, E, vec4, UI, LI, ldE, n_qp, n0, q0, 0, sc[0], su[0], sl[0]);
-        cp_async_commit();
-        for (int c = 0; c < nchunks; ++c) {
-            const int buf = c & 1;
-            if (c + 1 < nchunks) {
-                mv_issue<QB>(cand, N, E, vec4, UI, LI, ldE, n_qp, n0, q0, (c + 1) * kMvChunk, sc[buf ^ 1],
-                             su[buf ^ 1], sl[buf ^ 1]);
-                cp_async_commit();
-                cp_async_wait<1>();
-            } else {
-                cp_async_wait<0>();
-            }
-            __syncthreads();
-            f2 c2[kMvChunk];
-#pragma unroll
-            for (int s = 0; s < 8; ++s) {
-                const float4 v = *reinterpret_cast<const float4 *>(&sc[buf][tid * kMvChunk + ((s ^ (tid & 7)) << 2)]);
-                c2[4 * s] = pk(v.x, v.x);
-                c2[4 * s + 1] = pk(v.y, v.y);
-                c2[4 * s + 2] = pk(v.z, v.z);
-                c2[4 * s + 3] = pk(v.w, v.w);
-            }
-#pragma unroll
-            for (int qp = 0; qp < QB / 2; ++qp) {
-                f2 part = 0ull;
-                const float *u = &su[buf][qp * 2 * kMvChunk];
-                const float *l = &sl[buf][qp * 2 * kMvChunk];
-#pragma unroll
-                for (int e = 0; e < kMvChunk; e += 2) {
-                    const float4 u4 = *reinterpret_cast<const float4 *>(u + 2 * e);
-                    const float4 l4 = *reinterpret_cast<const float4 *>(l + 2 * e);
-                    part = mv_step(c2[e], u4.x, u4.y, l4.x, l4.y, part);
-                    part = mv_step(c2[e + 1], u4.z, u4.w, l4.z, l4.w, part);
-                }
-                acc[qp] = add2_rd(acc[qp], part);
-            }
-            __syncthreads();
-        }
-        const int64_t n = n0 + tid;
-        if (n < N) {
-#pragma unroll
-            for (int qp = 0; qp < QB / 2; ++qp) {
-                float a0, a1;
-                upk(acc[qp], a0, a1);
-                if (q0 + 2 * qp < Mb) lb[(size_t)(q0 + 2 * qp) * ldLb + n] = a0;
-                if (q0 + 2 * qp + 1 < Mb) lb[(size_t)(q0 + 2 * qp + 1) * ldLb + n] = a1;
-            }
-        }
+        lb_mv_tile<QB>(cand, N, E, vec4, UI, LI, ldE, Mb, lb, ldLb, (int64_t)ct * kMvRows, qt * QB, sc, su, sl);
     }
 }
 
@@ -340,74 +186,14 @@ cudaError_t launch_compact(const CompactArgs &a, cudaStream_t s) {
 // Per row m (one CTA of 256 threads): the S candidates with the smallest bound
 // (ties: smaller n) become seed entries m*N + n (empty slots: UINT32_MAX), and
 // their bound in the row is replaced by +inf so they do not survive compaction.
-constexpr int kMaxSeeds = 8;
-
-__device__ __forceinline__ bool lex_less(float a, uint32_t ia, float b, uint32_t ib) {
-    return a < b || (a == b && ia < ib);
-}
-
+// Per row m (one CTA): seed entries m*N + n (empty slots: UINT32_MAX).
 __global__ void k_seed_topk(float *__restrict__ lb, int64_t N, int64_t ldLb, int S, uint32_t *__restrict__ seeds) {
+    __shared__ uint32_t picked[kMaxSeeds];
     const int64_t m = blockIdx.x;
-    float *row = lb + (size_t)m * ldLb;
-    float bv[kMaxSeeds];
-    uint32_t bi[kMaxSeeds];
-#pragma unroll
-    for (int k = 0; k < kMaxSeeds; ++k) { bv[k] = TC_INF; bi[k] = 0xffffffffu; }
-    for (int64_t n = threadIdx.x; n < N; n += blockDim.x) {
-        float v = row[n];
-        uint32_t iv = (uint32_t)n;
-        if (!(v < TC_INF)) continue;
-#pragma unroll
-        for (int k = 0; k < kMaxSeeds; ++k) {  // insertion into the sorted local list
-            if (k < S && lex_less(v, iv, bv[k], bi[k])) {
-                float tv = bv[k]; uint32_t ti = bi[k];
-                bv[k] = v; bi[k] = iv;
-                v = tv; iv = ti;
-            }
-        }
-    }
-    __shared__ float cv[256 / 32][kMaxSeeds];
-    __shared__ uint32_t ci[256 / 32][kMaxSeeds];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int head = 0;
-    // warp level: S rounds of arg-min over the lanes' list heads
-    for (int r = 0; r < S; ++r) {
-        float v = head < S ? bv[0] : TC_INF;
-        uint32_t iv = head < S ? bi[0] : 0xffffffffu;
-        float wv = v; uint32_t wi = iv;
-        for (int o = 16; o > 0; o >>= 1) {
-            float ov = __shfl_xor_sync(0xffffffffu, wv, o);
-            uint32_t oi = __shfl_xor_sync(0xffffffffu, wi, o);
-            if (lex_less(ov, oi, wv, wi)) { wv = ov; wi = oi; }
-        }
-        if (lane == 0) { cv[warp][r] = wv; ci[warp][r] = wi; }
-        if (wi == iv && wi != 0xffffffffu) {  // this lane's head won: pop it
-#pragma unroll
-            for (int k = 0; k + 1 < kMaxSeeds; ++k) { bv[k] = bv[k + 1]; bi[k] = bi[k + 1]; }
-            bv[kMaxSeeds - 1] = TC_INF; bi[kMaxSeeds - 1] = 0xffffffffu;
-            ++head;
-        }
-    }
-    __syncthreads();
-    if (warp == 0) {
-        // merge the per-warp lists (each sorted): lane l < 8 walks warp l's list
-        int pos = 0;
-        const int nw = blockDim.x >> 5;
-        for (int r = 0; r < S; ++r) {
-            float v = (lane < nw && pos < S) ? cv[lane][pos] : TC_INF;
-            uint32_t iv = (lane < nw && pos < S) ? ci[lane][pos] : 0xffffffffu;
-            float wv = v; uint32_t wi = iv;
-            for (int o = 16; o > 0; o >>= 1) {
-                float ov = __shfl_xor_sync(0xffffffffu, wv, o);
-                uint32_t oi = __shfl_xor_sync(0xffffffffu, wi, o);
-                if (lex_less(ov, oi, wv, wi)) { wv = ov; wi = oi; }
-            }
-            if (wi == iv && wi != 0xffffffffu) ++pos;
-            if (lane == 0) {
-                seeds[m * S + r] = (wi == 0xffffffffu) ? 0xffffffffu : (uint32_t)(m * N + wi);
-                if (wi != 0xffffffffu) row[wi] = TC_INF;
-            }
-        }
+    seed_topk_row(lb + (size_t)m * ldLb, N, S, picked);
+    if (threadIdx.x < (unsigned)S) {
+        const uint32_t n = picked[threadIdx.x];
+        seeds[m * S + threadIdx.x] = (n == 0xffffffffu) ? 0xffffffffu : (uint32_t)(m * N + n);
     }
 }
 
@@ -422,12 +208,7 @@ cudaError_t launch_seed_topk(float *lb, int64_t M, int64_t N, int64_t ldLb, int 
 // One warp per entry.  Entry e (e < *count): pair id pairs[e] = m*N + n and its
 // current bound lbv[e] (+inf: already dropped).  The gate of selective deployment
 // (Section 6): the tight bound runs only if e_gate * bsf < lbv[e] <= threshold.
-// A pair whose bound exceeds the threshold gets lbv[e] = +inf.
-__device__ __forceinline__ float warp_sum_rd(float v) {
-    for (int o = 16; o > 0; o >>= 1) v = __fadd_rd(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
+// A pair whose tight bound exceeds the threshold gets lbv[e] = +inf.
 template <int DMAX>
 __global__ void __launch_bounds__(128) k_lb_pc_list(PairListArgs a, const float *__restrict__ boxes,
                                                     const int32_t *__restrict__ counts, int K, int w,
@@ -437,8 +218,7 @@ __global__ void __launch_bounds__(128) k_lb_pc_list(PairListArgs a, const float 
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t n_entries = a.count ? (int64_t)*a.count : a.n_static;
-    const int L = a.L, D = a.D;
-    const int G = (L + w - 1) / w;
+    const int G = (a.L + w - 1) / w;
     unsigned long long pruned = 0;
     for (int64_t e = warp; e < n_entries; e += nwarps) {
         const uint32_t pid = a.pairs[e];
@@ -447,68 +227,17 @@ __global__ void __launch_bounds__(128) k_lb_pc_list(PairListArgs a, const float 
         if (!(cur < TC_INF)) continue;
         const int64_t m = pid / (uint64_t)a.N, n = pid - m * a.N;
         const unsigned long long key = ld_volatile_u64(bsf + m);
-        const float thr = prune_threshold(key, rho);
-        if (cur > thr) continue;  // dropped (and counted) when the DTW stage fetches it
+        if (cur > prune_threshold(key, rho)) continue;  // dropped (and counted) by the DTW stage
         if (!(cur > e_gate * best_dist(key))) continue;
-        const float *c = a.C + (size_t)n * L * D;
-        const float *bx_m = boxes + (size_t)m * G * K * 2 * D;
-        const int32_t *cnt_m = counts + (size_t)m * G;
-        float acc = 0.f;
-        bool dropped = false;
-        for (int j0 = 0; j0 < L; j0 += 32) {
-            const int j = j0 + lane;
-            if (j < L) {
-                float x[DMAX];
-#pragma unroll
-                for (int p = 0; p < DMAX; ++p) x[p] = p < D ? __ldg(c + (size_t)j * D + p) : 0.f;
-                const int g = j / w;
-                const int nb = cnt_m[g];
-                const float *bx = bx_m + (size_t)g * K * 2 * D;
-                float best = TC_INF;
-                for (int k = 0; k < nb; ++k) {
-                    float s = 0.f;
-#pragma unroll
-                    for (int p = 0; p < DMAX; ++p)
-                        if (p < D) s = acc_box(x[p], __ldg(bx + k * 2 * D + p), __ldg(bx + k * 2 * D + D + p), s);
-                    best = fminf(best, s);
-                }
-                acc = __fadd_rd(acc, best);
-            }
-            const float tot = warp_sum_rd(acc);
-            if (tot > prune_threshold(ld_volatile_u64(bsf + m), rho)) { dropped = true; break; }
-        }
-        const float tot = warp_sum_rd(acc);
+        float bound;
+        const bool dropped = lb_pc_pair<DMAX>(a.C + (size_t)n * a.L * a.D, boxes + (size_t)m * G * K * 2 * a.D,
+                                              counts + (size_t)m * G, a.L, a.D, K, w, bsf + m, rho, &bound);
         if (lane == 0) {
             if (dropped) { a.lb[e] = TC_INF; ++pruned; }
-            else a.lb[e] = fmaxf(cur, tot);
+            else a.lb[e] = fmaxf(cur, bound);
         }
     }
     if (lane == 0 && pruned && stat_pruned) atomicAdd(stat_pruned, pruned);
-}
-
-// LB_TI (TIP_TOP).  Lane = candidate point j (column of the cost matrix).  The
-// rows of its window are i in [i0, i1] = [max(0, j-W), min(L-1, j+W)].  Row i0 is
-// exact (it is either the top of the window of row i0 = j-W, or row 0, and
-// 0 mod P == 0); rows with i mod P == 0 are exact; the others follow
-//   Lb = max(Lb_prev - dq_i, dq_i - Ub_prev, 0),  Ub = Ub_prev + dq_i
-// with dq_i taken rounded up where it is subtracted from Lb / added to Ub and
-// rounded down where Ub is subtracted from it.  m_j = min Lb; bound = sum m_j^2.
-template <int DMAX>
-__device__ __forceinline__ void exact_interval(const float *__restrict__ qi, const float (&x)[DMAX], int D, float *lo,
-                                               float *hi) {
-    float sl = 0.f, sh = 0.f;
-#pragma unroll
-    for (int p = 0; p < DMAX; ++p) {
-        if (p < D) {
-            const float y = __ldg(qi + p);
-            const float dl = fmaxf(__fsub_rd(x[p], y), __fsub_rd(y, x[p]));
-            const float dh = fmaxf(__fsub_ru(x[p], y), __fsub_ru(y, x[p]));
-            sl = __fmaf_rd(dl, dl, sl);
-            sh = __fmaf_ru(dh, dh, sh);
-        }
-    }
-    *lo = __fsqrt_rd(sl);
-    *hi = __fsqrt_ru(sh);
 }
 
 template <int DMAX>
@@ -520,7 +249,6 @@ __global__ void __launch_bounds__(128) k_lb_ti_list(PairListArgs a, const float 
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t n_entries = a.count ? (int64_t)*a.count : a.n_static;
-    const int L = a.L, D = a.D, W = a.W;
     unsigned long long pruned = 0;
     for (int64_t e = warp; e < n_entries; e += nwarps) {
         const uint32_t pid = a.pairs[e];
@@ -529,46 +257,15 @@ __global__ void __launch_bounds__(128) k_lb_ti_list(PairListArgs a, const float 
         if (!(cur < TC_INF)) continue;
         const int64_t m = pid / (uint64_t)a.N, n = pid - m * a.N;
         const unsigned long long key = ld_volatile_u64(bsf + m);
-        const float thr = prune_threshold(key, rho);
-        if (cur > thr) continue;  // dropped (and counted) when the DTW stage fetches it
+        if (cur > prune_threshold(key, rho)) continue;  // dropped (and counted) by the DTW stage
         if (!(cur > e_gate * best_dist(key))) continue;
-        const float *c = a.C + (size_t)n * L * D;
-        const float *q = a.Q + (size_t)m * L * D;
-        const float *dql = dq_lo + (size_t)m * L, *dqh = dq_hi + (size_t)m * L;
-        float acc = 0.f;
-        bool dropped = false;
-        for (int j0 = 0; j0 < L; j0 += 32) {
-            const int j = j0 + lane;
-            if (j < L) {
-                float x[DMAX];
-#pragma unroll
-                for (int p = 0; p < DMAX; ++p) x[p] = p < D ? __ldg(c + (size_t)j * D + p) : 0.f;
-                const int i0 = max(0, j - W), i1 = min(L - 1, j + W);
-                float lbv, ubv;
-                exact_interval<DMAX>(q + (size_t)i0 * D, x, D, &lbv, &ubv);
-                float mj = lbv;
-                int next_exact = (i0 / P + 1) * P;
-                for (int i = i0 + 1; i <= i1; ++i) {
-                    if (i == next_exact) {
-                        exact_interval<DMAX>(q + (size_t)i * D, x, D, &lbv, &ubv);
-                        next_exact += P;
-                    } else {
-                        const float dl = __ldg(dql + i), dh = __ldg(dqh + i);
-                        const float nl = fmaxf(fmaxf(__fsub_rd(lbv, dh), __fsub_rd(dl, ubv)), 0.f);
-                        ubv = __fadd_ru(ubv, dh);
-                        lbv = nl;
-                    }
-                    mj = fminf(mj, lbv);
-                }
-                acc = __fmaf_rd(mj, mj, acc);
-            }
-            const float tot = warp_sum_rd(acc);
-            if (tot > prune_threshold(ld_volatile_u64(bsf + m), rho)) { dropped = true; break; }
-        }
-        const float tot = warp_sum_rd(acc);
+        float bound;
+        const bool dropped = lb_ti_pair<DMAX>(a.C + (size_t)n * a.L * a.D, a.Q + (size_t)m * a.L * a.D,
+                                              dq_lo + (size_t)m * a.L, dq_hi + (size_t)m * a.L, a.L, a.D, a.W, P,
+                                              bsf + m, rho, &bound);
         if (lane == 0) {
             if (dropped) { a.lb[e] = TC_INF; ++pruned; }
-            else a.lb[e] = fmaxf(cur, tot);
+            else a.lb[e] = fmaxf(cur, bound);
         }
     }
     if (lane == 0 && pruned && stat_pruned) atomicAdd(stat_pruned, pruned);

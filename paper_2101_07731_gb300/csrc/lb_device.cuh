@@ -1,0 +1,353 @@
+// lb_device.cuh -- device building blocks of the lower-bound stage, shared by the
+// per-stage kernels (lb.cu) and the batched persistent kernel (batch.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace tc {
+
+constexpr int kMvRows = 128;
+constexpr int kMvChunk = 32;
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, int src_bytes) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem, int src_bytes) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__device__ __forceinline__ f2 sub2_rd(f2 a, f2 b) {
+    f2 r;
+    asm("sub.rm.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 fma2_rd(f2 a, f2 b, f2 c) {
+    f2 r;
+    asm("fma.rm.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ f2 add2_rd(f2 a, f2 b) {
+    f2 r;
+    asm("add.rm.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// squared distance of x to [lo, hi], rounded down, accumulated into acc
+__device__ __forceinline__ float acc_box(float x, float lo, float hi, float acc) {
+    const float m = max3f(__fsub_rd(x, hi), __fsub_rd(lo, x), 0.f);
+    return __fmaf_rd(m, m, acc);
+}
+
+// one packed step: element value c2 = {x, x} against two queries' (U, Lo)
+__device__ __forceinline__ f2 mv_step(f2 c2, float u0, float u1, float l0, float l1, f2 part) {
+    float a0, a1, b0, b1;
+    upk(sub2_rd(c2, pk(u0, u1)), a0, a1);
+    upk(sub2_rd(pk(l0, l1), c2), b0, b1);
+    const float m0 = max3f(a0, b0, 0.f), m1 = max3f(a1, b1, 0.f);
+    const f2 m2 = pk(m0, m1);
+    return fma2_rd(m2, m2, part);
+}
+
+template <int QB>
+__device__ __forceinline__ void mv_issue(const float *__restrict__ cand, int64_t N, int E, bool vec4,
+                                         const float *UI, const float *LI, int64_t ldE, int n_qp, int64_t n0, int q0,
+                                         int e0, float *sc, float *su, float *sl) {
+    const int tid = threadIdx.x;
+    if (vec4) {
+#pragma unroll
+        for (int k = 0; k < (kMvRows * 8) / 128; ++k) {
+            const int idx = tid + 128 * k;
+            const int row = idx >> 3, seg = idx & 7;
+            const int64_t n = n0 + row;
+            const int e = e0 + seg * 4;
+            const bool ok = n < N && e < E;
+            const float *src = ok ? cand + (size_t)n * E + e : cand;
+            cp_async16(sc + row * kMvChunk + ((seg ^ (row & 7)) << 2), src, ok ? 16 : 0);
+        }
+    } else {
+        for (int k = 0; k < kMvRows * kMvChunk / 128; ++k) {
+            const int idx = tid + 128 * k;
+            const int row = idx >> 5, el = idx & 31;
+            const int64_t n = n0 + row;
+            const int e = e0 + el;
+            const bool ok = n < N && e < E;
+            const float *src = ok ? cand + (size_t)n * E + e : cand;
+            const int seg = el >> 2;
+            cp_async4(sc + row * kMvChunk + ((seg ^ (row & 7)) << 2) + (el & 3), src, ok ? 4 : 0);
+        }
+    }
+    // envelope chunk: QB/2 query pairs x 32 elements x 2 floats (256 bytes), U and Lo
+    for (int idx = tid; idx < (QB / 2) * 16 * 2; idx += 128) {
+        const int which = idx / ((QB / 2) * 16);
+        const int r = idx % ((QB / 2) * 16);
+        const int qp = r >> 4, seg = r & 15;
+        const int qpg = min(q0 / 2 + qp, n_qp - 1);
+        const float *src = (which ? LI : UI) + ((size_t)qpg * ldE + e0) * 2 + seg * 4;
+        cp_async16((which ? sl : su) + qp * 2 * kMvChunk + seg * 4, src, 16);
+    }
+}
+
+// One LB_MV tile: candidates [n0, n0+128) x queries [q0, q0+QB) of the stream, using
+// the caller's shared buffers sc[2][128*32], su[2][QB*32], sl[2][QB*32] (16-byte aligned).
+template <int QB>
+__device__ __forceinline__ void lb_mv_tile(const float *__restrict__ cand, int64_t N, int E, bool vec4,
+                                           const float *__restrict__ UI, const float *__restrict__ LI, int64_t ldE,
+                                           int Mb, float *__restrict__ lb, int64_t ldLb, int64_t n0, int q0,
+                                           float (*sc)[kMvRows * kMvChunk], float (*su)[QB * kMvChunk],
+                                           float (*sl)[QB * kMvChunk]) {
+    const int tid = threadIdx.x;
+    const int nchunks = (E + kMvChunk - 1) / kMvChunk;
+    const int n_qp = (Mb + 1) / 2;
+    f2 acc[QB / 2];
+#pragma unroll
+    for (int k = 0; k < QB / 2; ++k) acc[k] = 0ull;
+    mv_issue<QB>(cand, N, E, vec4, UI, LI, ldE, n_qp, n0, q0, 0, sc[0], su[0], sl[0]);
+    cp_async_commit();
+    for (int c = 0; c < nchunks; ++c) {
+        const int buf = c & 1;
+        if (c + 1 < nchunks) {
+            mv_issue<QB>(cand, N, E, vec4, UI, LI, ldE, n_qp, n0, q0, (c + 1) * kMvChunk, sc[buf ^ 1], su[buf ^ 1],
+                         sl[buf ^ 1]);
+            cp_async_commit();
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        f2 c2[kMvChunk];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const float4 v = *reinterpret_cast<const float4 *>(&sc[buf][tid * kMvChunk + ((s ^ (tid & 7)) << 2)]);
+            c2[4 * s] = pk(v.x, v.x);
+            c2[4 * s + 1] = pk(v.y, v.y);
+            c2[4 * s + 2] = pk(v.z, v.z);
+            c2[4 * s + 3] = pk(v.w, v.w);
+        }
+#pragma unroll
+        for (int qp = 0; qp < QB / 2; ++qp) {
+            f2 part = 0ull;
+            const float *u = &su[buf][qp * 2 * kMvChunk];
+            const float *l = &sl[buf][qp * 2 * kMvChunk];
+#pragma unroll
+            for (int e = 0; e < kMvChunk; e += 2) {
+                const float4 u4 = *reinterpret_cast<const float4 *>(u + 2 * e);
+                const float4 l4 = *reinterpret_cast<const float4 *>(l + 2 * e);
+                part = mv_step(c2[e], u4.x, u4.y, l4.x, l4.y, part);
+                part = mv_step(c2[e + 1], u4.z, u4.w, l4.z, l4.w, part);
+            }
+            acc[qp] = add2_rd(acc[qp], part);
+        }
+        __syncthreads();
+    }
+    const int64_t n = n0 + tid;
+    if (n < N) {
+#pragma unroll
+        for (int qp = 0; qp < QB / 2; ++qp) {
+            float a0, a1;
+            upk(acc[qp], a0, a1);
+            if (q0 + 2 * qp < Mb) lb[(size_t)(q0 + 2 * qp) * ldLb + n] = a0;
+            if (q0 + 2 * qp + 1 < Mb) lb[(size_t)(q0 + 2 * qp + 1) * ldLb + n] = a1;
+        }
+    }
+}
+
+constexpr int kMaxSeeds = 8;
+
+__device__ __forceinline__ bool lex_less(float a, uint32_t ia, float b, uint32_t ib) {
+    return a < b || (a == b && ia < ib);
+}
+
+// The S smallest bounds of one row (ties: smaller n), computed by the whole CTA
+// (blockDim.x a multiple of 32, at most 1024).  out[r] = n of the r-th smallest
+// (UINT32_MAX when the row has fewer than r+1 finite bounds); the chosen entries of
+// the row are set to +inf so that they do not survive compaction.  Must be called by
+// every thread of the CTA; ends with a __syncthreads().
+__device__ inline void seed_topk_row(float *__restrict__ row, int64_t N, int S, uint32_t *out) {
+    __shared__ float cv[32][kMaxSeeds];
+    __shared__ uint32_t ci[32][kMaxSeeds];
+    float bv[kMaxSeeds];
+    uint32_t bi[kMaxSeeds];
+#pragma unroll
+    for (int k = 0; k < kMaxSeeds; ++k) { bv[k] = TC_INF; bi[k] = 0xffffffffu; }
+    for (int64_t n = threadIdx.x; n < N; n += blockDim.x) {
+        float v = row[n];
+        uint32_t iv = (uint32_t)n;
+        if (!(v < TC_INF)) continue;
+#pragma unroll
+        for (int k = 0; k < kMaxSeeds; ++k) {  // insertion into the sorted local list
+            if (k < S && lex_less(v, iv, bv[k], bi[k])) {
+                float tv = bv[k]; uint32_t ti = bi[k];
+                bv[k] = v; bi[k] = iv;
+                v = tv; iv = ti;
+            }
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // warp level: S rounds of arg-min over the lanes' list heads
+    for (int r = 0; r < S; ++r) {
+        float v = bv[0];
+        uint32_t iv = bi[0];
+        float wv = v; uint32_t wi = iv;
+        for (int o = 16; o > 0; o >>= 1) {
+            float ov = __shfl_xor_sync(0xffffffffu, wv, o);
+            uint32_t oi = __shfl_xor_sync(0xffffffffu, wi, o);
+            if (lex_less(ov, oi, wv, wi)) { wv = ov; wi = oi; }
+        }
+        if (lane == 0) { cv[warp][r] = wv; ci[warp][r] = wi; }
+        if (wi == iv && wi != 0xffffffffu) {  // this lane's head won: pop it
+#pragma unroll
+            for (int k = 0; k + 1 < kMaxSeeds; ++k) { bv[k] = bv[k + 1]; bi[k] = bi[k + 1]; }
+            bv[kMaxSeeds - 1] = TC_INF; bi[kMaxSeeds - 1] = 0xffffffffu;
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        // merge the per-warp sorted lists: lane l < nw walks warp l's list
+        int pos = 0;
+        const int nw = blockDim.x >> 5;
+        for (int r = 0; r < S; ++r) {
+            float v = (lane < nw && pos < S) ? cv[lane][pos] : TC_INF;
+            uint32_t iv = (lane < nw && pos < S) ? ci[lane][pos] : 0xffffffffu;
+            float wv = v; uint32_t wi = iv;
+            for (int o = 16; o > 0; o >>= 1) {
+                float ov = __shfl_xor_sync(0xffffffffu, wv, o);
+                uint32_t oi = __shfl_xor_sync(0xffffffffu, wi, o);
+                if (lex_less(ov, oi, wv, wi)) { wv = ov; wi = oi; }
+            }
+            if (wi == iv && wi != 0xffffffffu) ++pos;
+            if (lane == 0) {
+                out[r] = wi;
+                if (wi != 0xffffffffu) row[wi] = TC_INF;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// ============================================================== LB_PC / LB_TI of one pair
+// Warp-level: every lane of the warp calls with the same pair.  The live threshold is
+// re-read from the query's packed best-so-far after every 32 candidate points; the
+// function returns true (dropped) as soon as the partial bound exceeds it, else
+// false with the bound (rounded down) in *bound on every lane.
+// Loads of per-query data (boxes, neighbour distances): through the read-only path,
+// or, for data written earlier in the same launch (kCoherent), through L2 only.
+template <bool kCoherent>
+__device__ __forceinline__ float ld_q(const float *p) {
+    return kCoherent ? __ldcg(p) : __ldg(p);
+}
+
+__device__ __forceinline__ float warp_sum_rd(float v) {
+    for (int o = 16; o > 0; o >>= 1) v = __fadd_rd(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// LB_PC (Section 5): candidate point j is bounded by its nearest box among the boxes
+// of group j / w (boxes of this query: bx_m [G][K][2][D], counts cnt_m [G]).
+template <int DMAX, bool kCoherent = false>
+__device__ __forceinline__ bool lb_pc_pair(const float *__restrict__ c, const float *__restrict__ bx_m,
+                                           const int32_t *__restrict__ cnt_m, int L, int D, int K, int w,
+                                           const unsigned long long *bsf_m, float rho, float *bound) {
+    const int lane = threadIdx.x & 31;
+    float acc = 0.f;
+    for (int j0 = 0; j0 < L; j0 += 32) {
+        const int j = j0 + lane;
+        if (j < L) {
+            float x[DMAX];
+#pragma unroll
+            for (int p = 0; p < DMAX; ++p) x[p] = p < D ? __ldg(c + (size_t)j * D + p) : 0.f;
+            const int g = j / w;
+            const int nb = kCoherent ? __ldcg(cnt_m + g) : cnt_m[g];
+            const float *bx = bx_m + (size_t)g * K * 2 * D;
+            float best = TC_INF;
+            for (int k = 0; k < nb; ++k) {
+                float s = 0.f;
+#pragma unroll
+                for (int p = 0; p < DMAX; ++p)
+                    if (p < D) s = acc_box(x[p], ld_q<kCoherent>(bx + k * 2 * D + p), ld_q<kCoherent>(bx + k * 2 * D + D + p), s);
+                best = fminf(best, s);
+            }
+            acc = __fadd_rd(acc, best);
+        }
+        const float tot = warp_sum_rd(acc);
+        if (tot > prune_threshold(ld_volatile_u64(bsf_m), rho)) return true;
+    }
+    *bound = warp_sum_rd(acc);
+    return false;
+}
+
+// |q_i - c| as an interval: rounded-down / rounded-up Euclidean distance.
+template <int DMAX>
+__device__ __forceinline__ void exact_interval(const float *__restrict__ qi, const float (&x)[DMAX], int D, float *lo,
+                                               float *hi) {
+    float sl = 0.f, sh = 0.f;
+#pragma unroll
+    for (int p = 0; p < DMAX; ++p) {
+        if (p < D) {
+            const float y = __ldg(qi + p);
+            const float dl = fmaxf(__fsub_rd(x[p], y), __fsub_rd(y, x[p]));
+            const float dh = fmaxf(__fsub_ru(x[p], y), __fsub_ru(y, x[p]));
+            sl = __fmaf_rd(dl, dl, sl);
+            sh = __fmaf_ru(dh, dh, sh);
+        }
+    }
+    *lo = __fsqrt_rd(sl);
+    *hi = __fsqrt_ru(sh);
+}
+
+// LB_TI, TIP_TOP (Section 4).  Lane = candidate point j (column of the cost matrix);
+// the rows of its window are i in [i0, i1] = [max(0, j-W), min(L-1, j+W)].  Row i0 is
+// exact (the top of the window of row j-W, or row 0, and 0 mod P == 0); rows with
+// i mod P == 0 are exact; the others follow Lb = max(Lb - dq_i, dq_i - Ub, 0),
+// Ub = Ub + dq_i with dq_i rounded up where it is subtracted from Lb / added to Ub
+// and rounded down where Ub is subtracted from it.  bound = sum_j (min_i Lb)^2.
+template <int DMAX, bool kCoherent = false>
+__device__ __forceinline__ bool lb_ti_pair(const float *__restrict__ c, const float *__restrict__ q,
+                                           const float *__restrict__ dql, const float *__restrict__ dqh, int L, int D,
+                                           int W, int P, const unsigned long long *bsf_m, float rho, float *bound) {
+    const int lane = threadIdx.x & 31;
+    float acc = 0.f;
+    for (int j0 = 0; j0 < L; j0 += 32) {
+        const int j = j0 + lane;
+        if (j < L) {
+            float x[DMAX];
+#pragma unroll
+            for (int p = 0; p < DMAX; ++p) x[p] = p < D ? __ldg(c + (size_t)j * D + p) : 0.f;
+            const int i0 = max(0, j - W), i1 = min(L - 1, j + W);
+            float lbv, ubv;
+            exact_interval<DMAX>(q + (size_t)i0 * D, x, D, &lbv, &ubv);
+            float mj = lbv;
+            int next_exact = (i0 / P + 1) * P;
+            for (int i = i0 + 1; i <= i1; ++i) {
+                if (i == next_exact) {
+                    exact_interval<DMAX>(q + (size_t)i * D, x, D, &lbv, &ubv);
+                    next_exact += P;
+                } else {
+                    const float dl = ld_q<kCoherent>(dql + i), dh = ld_q<kCoherent>(dqh + i);
+                    const float nl = fmaxf(fmaxf(__fsub_rd(lbv, dh), __fsub_rd(dl, ubv)), 0.f);
+                    ubv = __fadd_ru(ubv, dh);
+                    lbv = nl;
+                }
+                mj = fminf(mj, lbv);
+            }
+            acc = __fmaf_rd(mj, mj, acc);
+        }
+        const float tot = warp_sum_rd(acc);
+        if (tot > prune_threshold(ld_volatile_u64(bsf_m), rho)) return true;
+    }
+    *bound = warp_sum_rd(acc);
+    return false;
+}
+
+}  // namespace tc

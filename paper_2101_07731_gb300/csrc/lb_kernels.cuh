@@ -35,6 +35,8 @@ struct LbMvArgs {
     int sms;
 };
 cudaError_t launch_lb_mv(const LbMvArgs &a, cudaStream_t s);
+// whether the LB_MV stream may copy candidate rows 16 bytes at a time
+bool lb_mv_vec4(const float *cand, int E);
 
 // compaction of rows of a bound matrix against per-row thresholds
 struct CompactArgs {

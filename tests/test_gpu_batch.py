@@ -1,0 +1,181 @@
+"""GPU parity of the batched persistent search (many uneven sets in one launch)
+against the FP64 oracle, and the device-side wait limit of its work queue.
+
+Bar: per set, NN indices bit-exact (ties to the smallest index) and distances
+within 1e-5 relative of FP64 (the FP64 refine makes them the FP64 values)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+tc = pytest.importorskip("paper_2101_07731_gb300")
+DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
+RTOL = 1e-5
+
+
+def _gpu(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+
+
+def _make(shapes, seed0=0, kind="proto_warp"):
+    """shapes: (M, N, L, D, W, K) per set; returns host arrays and device sets."""
+    host, sets = [], []
+    for k, (M, N, L, D, W, K) in enumerate(shapes):
+        spec = synth.SeriesSpec(kind, L, D, seed0 + k, n_proto=4, sigma=0.1)
+        Q = synth.generate(spec, synth.ROLE_QUERY, M)
+        Cn = synth.generate(spec, synth.ROLE_CAND, N)
+        host.append((Q, Cn, W))
+        sets.append({"cand": _gpu(Cn), "q": _gpu(Q), "W": W, "K": K})
+    return host, sets
+
+
+def _check(host, outs, exact_dist=True):
+    for k, ((Q, Cn, W), (idx, dist)) in enumerate(zip(host, outs)):
+        if len(Q) == 0:
+            assert idx.numel() == 0
+            continue
+        ridx, rdist = O.nn_brute(Q, Cn, W)
+        gi, gd = idx.cpu().numpy(), dist.cpu().numpy()
+        assert np.array_equal(gi, ridx), (k, np.nonzero(gi != ridx))
+        if exact_dist:
+            assert np.array_equal(gd, rdist), k
+        else:
+            np.testing.assert_allclose(gd, rdist, rtol=RTOL, atol=0)
+
+
+# uneven shapes: every D of the single-launch family (1..12), windows from 0 to
+# beyond L, tiny and ragged N (one LB_MV tile, several, a ragged tail), odd M
+UNEVEN = [(5, 300, 64, 3, 6, 8), (3, 1, 40, 2, 4, 4), (7, 129, 97, 12, 9, 16), (1, 700, 33, 1, 0, 4),
+          (9, 260, 120, 5, 12, 8), (2, 64, 200, 8, 20, 16), (4, 511, 50, 7, 60, 4), (6, 90, 75, 10, 7, 6),
+          (33, 140, 48, 4, 5, 8), (2, 257, 160, 9, 16, 16), (3, 40, 30, 6, 3, 2), (5, 333, 81, 11, 8, 8)]
+
+
+def _check_stats(st, shapes):
+    pairs = sum(M * N for (M, N, *_r) in shapes)
+    assert st["pairs"] == pairs
+    assert st["pruned_mv"] + st["pruned_pc"] + st["pruned_ti"] + st["dtw_started"] == pairs, st
+    assert st["refined"] >= sum(M for (M, *_r) in shapes)
+
+
+def test_batch_uneven_sets_exact():
+    host, sets = _make(UNEVEN, 100)
+    outs, st = tc.batch_nn(sets, stats=True)
+    _check(host, outs)
+    _check_stats(st, UNEVEN)
+
+
+def test_batch_mixed_with_sequential_shapes():
+    # D = 16, and W = 200 (beyond the single launch's widest lane group), run through the per-set path
+    shapes = [(4, 120, 60, 16, 6, 8), (3, 200, 70, 3, 7, 8), (2, 50, 400, 2, 200, 4), (0, 30, 20, 2, 2, 4),
+              (5, 80, 44, 6, 4, 4)]
+    host, sets = _make(shapes, 200)
+    outs, st = tc.batch_nn(sets, stats=True)
+    _check(host, outs)
+    _check_stats(st, shapes)
+
+
+@pytest.mark.parametrize("use_pc,use_ti,no_prune", [(0, 0, 0), (1, 0, 0), (0, 1, 0), (1, 1, 1)])
+def test_batch_cascade_settings(use_pc, use_ti, no_prune):
+    shapes = UNEVEN[:6]
+    host, sets = _make(shapes, 300)
+    outs, st = tc.batch_nn(sets, stats=True, use_pc=use_pc, use_ti=use_ti, e_pc=0.0, e_ti=0.0,
+                           no_prune=no_prune)
+    _check(host, outs)
+    _check_stats(st, shapes)
+    if no_prune:
+        assert st["dtw_started"] == st["pairs"]
+
+
+def test_batch_many_sets_queue():
+    # more sets and items than resident CTAs: items of one set wait on one another
+    rng = np.random.default_rng(5)
+    shapes = []
+    for _ in range(40):
+        L = int(rng.integers(8, 90))
+        shapes.append((int(rng.integers(1, 6)), int(rng.integers(1, 300)), L, int(rng.integers(1, 13)),
+                       int(rng.integers(0, L)), int(rng.integers(1, 9))))
+    host, sets = _make(shapes, 400, kind="random_walk")
+    outs, st = tc.batch_nn(sets, stats=True)
+    _check(host, outs)
+    _check_stats(st, shapes)
+
+
+def test_batch_ties_and_duplicates():
+    spec = synth.SeriesSpec("random_walk", 50, 3, 9)
+    Cn = synth.generate(spec, synth.ROLE_CAND, 40)
+    Cn[25] = Cn[3]
+    Cn[31] = Cn[3]
+    Q = np.stack([Cn[3], Cn[7], Cn[25] + 0.0])
+    host = [(Q, Cn, 5)]
+    outs = tc.batch_nn([{"cand": _gpu(Cn), "q": _gpu(Q), "W": 5, "K": 4}])
+    _check(host, outs)
+    assert outs[0][0].cpu().tolist() == [3, 7, 3]
+
+
+def test_batch_workload_generator_sample():
+    # the uneven-batch generator's shapes at a small scale, 4 queries per set
+    wls = synth.batched_sets(n_sets=6, M=3, seed=0, scale=0.01)
+    host, sets = [], []
+    for wl in wls:
+        Q, Cn = wl.queries(), wl.candidates()
+        host.append((Q, Cn, wl.W))
+        sets.append({"cand": _gpu(Cn), "q": _gpu(Q), "W": wl.W, "K": wl.K})
+    outs = tc.batch_nn(sets)
+    _check(host, outs)
+
+
+def test_batch_graph_replay_follows_buffer_contents():
+    shapes = UNEVEN[:5]
+    host, sets = _make(shapes, 500)
+    out = [(torch.empty(M, dtype=torch.int64, device=DEV), torch.empty(M, dtype=torch.float64, device=DEV))
+           for (M, *_r) in shapes]
+    before = tc.kernel_launches()
+    for it in range(4):
+        # new query contents in the same buffers every call (eager, capture, replays)
+        for k, (M, N, L, D, W, K) in enumerate(shapes):
+            spec = synth.SeriesSpec("proto_warp", L, D, 900 + 10 * it + k, n_proto=4, sigma=0.1)
+            Qn = synth.generate(spec, synth.ROLE_QUERY, M)
+            sets[k]["q"].copy_(_gpu(Qn))
+            host[k] = (Qn, host[k][1], W)
+        outs = tc.batch_nn(sets, out=out)
+        assert all(o[0].data_ptr() == b[0].data_ptr() for o, b in zip(outs, out))
+        _check(host, outs)
+    assert tc.kernel_launches() > before
+
+
+def test_batch_wait_limit_returns_timeout_and_context_survives():
+    # the only work item waits on a counter nothing increments: the wait runs out
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    code = tc.batch_selftest_timeout(100000)
+    t1.record()
+    torch.cuda.synchronize()
+    assert code == tc.ERR_TIMEOUT
+    assert t0.elapsed_time(t1) < 10000.0
+    # the context is still usable
+    host, sets = _make(UNEVEN[:3], 600)
+    _check(host, tc.batch_nn(sets))
+
+
+def test_batch_rejects_non_finite_query():
+    host, sets = _make(UNEVEN[:2], 700)
+    q = sets[1]["q"].clone()
+    q[0, 3, 0] = float("nan")
+    sets[1]["q"] = q
+    with pytest.raises(tc.TcdtwError) as ei:
+        tc.batch_nn(sets)
+    assert ei.value.code == tc.ERR_NONFINITE
+
+
+def test_batch_rejects_bad_descriptors():
+    host, sets = _make(UNEVEN[:1], 800)
+    with pytest.raises(ValueError):
+        tc.batch_nn([{"cand": sets[0]["cand"], "q": sets[0]["q"][:, :10], "W": 3}])
+    with pytest.raises(tc.TcdtwError) as ei:
+        tc.batch_nn(sets, seed_s=9)
+    assert ei.value.code == tc.ERR_INVALID
