@@ -4,7 +4,7 @@
  * TC-DTW (Shen & Chi): query envelopes, the lower-bound cascade LB_MV -> LB_PC /
  * LB_TI with selective deployment, survivor compaction, banded DTW with early
  * abandoning against a device-resident best-so-far; plus a differentiable DTW
- * distance (forward and adjoint) and a batched persistent launch.
+ * distance (forward and adjoint) and a batched search over many uneven sets.
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -94,7 +94,10 @@ typedef struct {
     uint64_t dtw_started;   /* DTWs started (seeds included)                         */
     uint64_t dtw_abandoned; /* DTWs stopped early against the best-so-far            */
     uint64_t cells;         /* DTW cells computed in FP32                            */
-    uint64_t refined;       /* candidates recomputed in FP64 to settle near-ties     */
+    uint64_t refined;       /* candidates recomputed in double-float arithmetic
+                               because FP32 could not separate them from the best */
+    uint64_t refined64;     /* ... of those, recomputed in FP64 because double-float
+                               could not separate them either                      */
 } tcdtw_stats;
 
 /* Fill *opts with the defaults listed above. */
@@ -124,12 +127,16 @@ int tcdtw_build(const float *cand, int64_t N, int32_t L, int32_t D, int32_t W, i
  *   q     device [M][L][D] float32 queries (same L and D as the index).
  *   idx   device [M] int64: index in C of the nearest candidate; exact ties go to
  *         the smallest index.
- *   dist  device [M] float64: its DTW distance, recomputed in FP64.
+ *   dist  device [M] float64: its DTW distance from the double-float recompute
+ *         (relative error below ~1e-9; the FP64 value itself when the FP64 step ran
+ *         for that query).
  *   stats host, may be NULL; when given, the call synchronises `stream` and fills it.
  * Every bound is a rigorous lower bound in FP32 (directed rounding), pruning uses a
- * margin that covers the FP32 DTW rounding error, and candidates whose FP32 DTW
- * cannot be told apart from the best are recomputed in FP64 -- so idx equals the
- * FP64 brute-force argmin.  Errors: INVALID, NOMEM, CUDA, NONFINITE, TIMEOUT.
+ * margin that covers the FP32 DTW rounding error, candidates whose FP32 DTW cannot
+ * be told apart from the best are recomputed in double-float arithmetic with a
+ * proven error bound, and the few that this still cannot separate are recomputed in
+ * FP64 -- so idx equals the FP64 brute-force argmin (ties: smallest index).
+ * Errors: INVALID, NOMEM, CUDA, NONFINITE, TIMEOUT.
  */
 int tcdtw_nn(tcdtw_index *index, const float *q, int64_t M, int64_t *idx, double *dist,
              tcdtw_stats *stats, void *stream);
@@ -148,7 +155,7 @@ int tcdtw_index_info(tcdtw_index *index, int32_t *tile, int32_t *G, int32_t *qbl
  * boundaries below and tcdtw_nn synchronises at its end to add the elapsed times.
  * Stages: 0 non-finite scan, 1 query preparation (envelope, dq, boxes), 2 LB_MV,
  * 3 seeds (selection and their DTW), 4 compaction, 5 LB_PC / LB_TI cascade,
- * 6 DTW of the survivors, 7 FP64 refine and selection.
+ * 6 DTW of the survivors, 7 refine (double-float, then FP64 where needed) and selection.
  * tcdtw_set_profiling: enable != 0 turns it on; either way the totals are reset.
  * tcdtw_stage_times: host ms[TCDTW_NUM_STAGES] receives the summed milliseconds,
  * host *blocks (may be NULL) the number of query blocks timed.  Errors: INVALID.
@@ -256,21 +263,24 @@ int tcdtw_compact(const float *lb, int64_t M, int64_t N, const float *thresh, in
 
 /*
  * Batched search: many independent (candidate set, query set) problems of uneven
- * L, D, N, W in one persistent launch off a device work queue (not in the paper; a
- * deployment pattern).  Each entry is searched exactly as tcdtw_nn would search it
- * (same bounds, same rounding margins, same FP64 refine), so idx/dist are the exact
- * nearest neighbours under Eq. (1) with the band |i-j| <= W.
+ * L, D, N, W searched together (not in the paper; a deployment pattern).  Each entry
+ * is searched exactly as tcdtw_nn would search it (same bounds, same rounding
+ * margins, same refine), so idx/dist are the exact nearest neighbours under Eq. (1)
+ * with the band |i-j| <= W.
  *
- * Work items, in queue order: per query its envelope / neighbour distances / LB_PC
- * boxes; per 32-query x 128-candidate tile its LB_MV bounds; per query the rest of
- * the cascade (seeds, compaction, gated LB_PC and LB_TI, banded DTW with early
- * abandoning, FP64 refine).  Items of one set wait for the earlier items they need on
- * device counters; each wait gives up after about a second, and the call then
- * returns TIMEOUT.  Entries with D > 12 or W beyond the FP64 refine's band are
- * searched through tcdtw_build / tcdtw_nn, one after another, after the launch.
- * The launch and its workspace are kept per distinct batch (the descriptors and
- * opts, byte for byte; up to 4 batches): the second call with the same batch
- * captures the launch into a CUDA graph (opts->use_graph), later calls replay it.
+ * The batch runs as one sequence of persistent launches, each taking work items off
+ * a device queue: (1) per query its envelope / neighbour distances / LB_PC boxes, per
+ * 32-query x 128-candidate tile its LB_MV bounds, per query its seeds -- items of one
+ * set wait for the earlier items they need on device counters, and each wait gives
+ * up after about a second (the call then returns TIMEOUT); (2) the seeds' banded DTW,
+ * one launch per tile class (D); (3) per query compaction and gated LB_PC / LB_TI;
+ * (4) the survivors' DTW with early abandoning, one launch per tile class; (5) per
+ * query the refine.  Entries with D > 12 or W > 140 are searched through tcdtw_build
+ * / tcdtw_nn, one after another, after the sequence.  The sequence and its workspace
+ * are kept per distinct batch (the descriptors and opts, byte for byte; up to 4
+ * batches): the second call with the same batch captures the sequence into a CUDA
+ * graph (opts->use_graph), later calls replay it.  With opts->check_finite the
+ * candidates are scanned when a batch is first seen and the queries on every call.
  */
 typedef struct {
     const float *cand; /* device [N][L][D], row-major, N >= 1 */

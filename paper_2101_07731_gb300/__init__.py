@@ -57,7 +57,8 @@ class Opts(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ("pairs", "pruned_mv", "pruned_pc", "pruned_ti", "dtw_started",
-                                          "dtw_abandoned", "cells", "refined")]
+                                          "dtw_abandoned", "cells", "refined",
+                                          "refined64")]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}

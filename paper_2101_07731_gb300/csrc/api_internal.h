@@ -14,5 +14,6 @@ int64_t ckpt_floats(int64_t P, int L, int W);
 int cuda_err(cudaError_t e);
 const char *last_detail();
 float prune_rho(int L, int D);
+double refine_kappa(int L, int D);
 bool pc_key_fits(int Lq, int D);
 }  // namespace tc

@@ -41,6 +41,24 @@ float prune_rho(int L, int D) {
     return r;
 }
 
+// Separation factor of the double-float refine: a candidate whose double-float DTW
+// exceeds the best one's times kappa has a larger FP64 DTW.  kappa =
+// (1+g64)(1+G)/((1-g64)(1-G)), where G bounds the relative error of the double-float
+// DP (cell costs (3D+2)(D+3)u^2/(1-(3D+2)u), u = 2^-24; at most 2L double-word
+// additions of relative error 4u^2 along a path; the final rounding to double) and
+// g64 = n u64/(1 - n u64), n = 2L+D+2, bounds the FP64 evaluation's error.  Both
+// bounds are doubled for safety; rounded up.
+double refine_kappa(int L, int D) {
+    const double u = ldexp(1.0, -24), u64 = ldexp(1.0, -53);
+    const double k = 3.0 * D + 2.0;
+    const double e_cost = k * (D + 3.0) * u * u / (1.0 - k * u);
+    const double G = 2.0 * ((1.0 + e_cost) * pow(1.0 + 4.0 * u * u, 2.0 * L) - 1.0 + 2.0 * u64);
+    const double n = 2.0 * L + D + 2.0;
+    const double g64 = 2.0 * (n * u64 / (1.0 - n * u64));
+    const double kappa = (1.0 + g64) * (1.0 + G) / ((1.0 - g64) * (1.0 - G));
+    return nextafter(nextafter(kappa, INFINITY), INFINITY);
+}
+
 bool pc_key_fits(int Lq, int D) {
     // Lq^D must fit below 2^63 (mixed-radix cell key)
     long double v = 1;
@@ -92,7 +110,7 @@ bool autotune_nn_tile(const float *cand, int64_t N, int L, int D, int W, cudaStr
         h[i] = (uint32_t)(m * N + n);
     }
     ok = ok && cudaMemcpyAsync(pairs, h.data(), sizeof(uint32_t) * P, cudaMemcpyHostToDevice, s) == cudaSuccess;
-    ok = ok && launch_init_block(Mq, bsf, nullptr, nullptr, s) == cudaSuccess;
+    ok = ok && launch_init_block(Mq, bsf, nullptr, nullptr, nullptr, nullptr, nullptr, s) == cudaSuccess;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     ok = ok && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
     float best = 1e30f;
@@ -134,8 +152,10 @@ cudaError_t dalloc(T **p, size_t n) {
     return cudaMalloc((void **)p, n * sizeof(T));
 }
 
-enum Counter { kStarted = 0, kAbandoned, kCells, kPrunedDtw, kPrunedMv, kPrunedPc, kPrunedTi, kRefined, kNumCounters };
-enum Scalar { kSurvTotal = 0, kCursorSeed, kCursorSurv, kRefineCount, kNumScalars };
+enum Counter {
+    kStarted = 0, kAbandoned, kCells, kPrunedDtw, kPrunedMv, kPrunedPc, kPrunedTi, kRefined, kRefined64, kNumCounters
+};
+enum Scalar { kSurvTotal = 0, kCursorSeed, kCursorSurv, kRefineCount, kRefine64Count, kNumScalars };
 
 }  // namespace tc
 
@@ -148,16 +168,19 @@ struct tcdtw_index {
     int64_t ldE = 0;
     float rho = 1.f;         // pruning / abandoning factor (+inf with no_prune)
     float rho_ref = 1.f;     // refine factor (always the rounding margin)
+    double kappa = 1.0;      // double-float separation factor of the refine (refine_kappa)
     int tile = 0, G = 32, R_ref = 1, sms = 1;
     int blocks_nn = 1, blocks_ref = 1;
     // workspaces
     float *U = nullptr, *Lo = nullptr, *dq_lo = nullptr, *dq_hi = nullptr, *boxes = nullptr, *lbm = nullptr;
     int32_t *box_counts = nullptr;
-    uint32_t *seeds = nullptr, *surv = nullptr, *refine = nullptr;
+    uint32_t *seeds = nullptr, *surv = nullptr, *refine = nullptr, *refine64 = nullptr;
     float *seed_dtw = nullptr, *surv_lb = nullptr, *surv_dtw = nullptr;
-    double *refine_d64 = nullptr;
+    double *refine_d64 = nullptr, *refine64_d64 = nullptr;
+    int32_t *amb = nullptr;
     int32_t *row_counts = nullptr, *row_offsets = nullptr, *scalars = nullptr;
     unsigned long long *bsf = nullptr, *best64 = nullptr, *best_idx = nullptr, *counters = nullptr;
+    unsigned long long *bestdf = nullptr, *best_idx_df = nullptr;
     DevStatus *status = nullptr;
     int64_t refine_cap = 0;
     // per-stage CUDA-event profile (tcdtw_set_profiling)
@@ -195,7 +218,8 @@ void free_index(tcdtw_index *x) {
     if (x->cap_stream) cudaStreamDestroy(x->cap_stream);
     void *ptrs[] = {x->U, x->Lo, x->dq_lo, x->dq_hi, x->boxes, x->lbm, x->box_counts, x->seeds, x->surv,
                     x->refine, x->seed_dtw, x->surv_lb, x->surv_dtw, x->refine_d64, x->row_counts,
-                    x->row_offsets, x->scalars, x->bsf, x->best64, x->best_idx, x->counters, x->status};
+                    x->row_offsets, x->scalars, x->bsf, x->best64, x->best_idx, x->counters, x->status,
+                    x->refine64, x->refine64_d64, x->amb, x->bestdf, x->best_idx_df};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete x;
@@ -233,6 +257,11 @@ int alloc_index(tcdtw_index *x) {
     x->refine_cap = Mb * (N + x->S);
     TC_TRY(dalloc(&x->refine, (size_t)x->refine_cap));
     TC_TRY(dalloc(&x->refine_d64, (size_t)x->refine_cap));
+    TC_TRY(dalloc(&x->refine64, (size_t)x->refine_cap));
+    TC_TRY(dalloc(&x->refine64_d64, (size_t)x->refine_cap));
+    TC_TRY(dalloc(&x->amb, (size_t)Mb));
+    TC_TRY(dalloc(&x->bestdf, (size_t)Mb));
+    TC_TRY(dalloc(&x->best_idx_df, (size_t)Mb));
     TC_TRY(dalloc(&x->row_counts, (size_t)Mb));
     TC_TRY(dalloc(&x->row_offsets, (size_t)Mb));
     TC_TRY(dalloc(&x->scalars, (size_t)kNumScalars));
@@ -283,7 +312,9 @@ cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_o
     TC_MARK(1);
     e = cudaMemsetAsync(x->scalars, 0, sizeof(int32_t) * kNumScalars, s);
     if (e != cudaSuccess) return e;
-    if ((e = launch_init_block(Mb_cur, x->bsf, x->best64, x->best_idx, s)) != cudaSuccess) return e;
+    if ((e = launch_init_block(Mb_cur, x->bsf, x->best64, x->best_idx, x->bestdf, x->best_idx_df, x->amb, s)) !=
+        cudaSuccess)
+        return e;
     // 1. query-side preparation
     if ((e = launch_envelope_pairs(q, Mb_cur, L, D, W, x->U, x->Lo, (int)x->ldE, s)) != cudaSuccess) return e;
     if (x->opts.use_ti && (e = launch_query_dq(q, Mb_cur, L, D, x->dq_lo, x->dq_hi, s)) != cudaSuccess) return e;
@@ -345,15 +376,31 @@ cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_o
     if ((e = launch_refine_select(x->surv, x->surv_dtw, x->scalars + kSurvTotal, 0, N, x->bsf, x->rho_ref, x->refine,
                                   x->scalars + kRefineCount, x->refine_cap, x->sms, s)) != cudaSuccess)
         return e;
+    // double-float recompute of the refine list; FP64 only for queries whose entries it
+    // cannot separate
     DtwRefineArgs rf;
     rf.Q = q; rf.C = x->cand; rf.L = L; rf.D = D; rf.W = W; rf.N = N;
-    rf.pairs = x->refine; rf.count = x->scalars + kRefineCount; rf.d64 = x->refine_d64; rf.best64 = x->best64;
-    if ((e = dtw_refine_launch(x->R_ref, x->blocks_ref, s, rf)) != cudaSuccess) return e;
-    if ((e = launch_refine_pick(x->refine, x->refine_d64, x->scalars + kRefineCount, N, x->best64, x->best_idx,
+    rf.pairs = x->refine; rf.count = x->scalars + kRefineCount; rf.d64 = x->refine_d64; rf.best64 = x->bestdf;
+    if ((e = dtw_refine_df_launch(x->R_ref, x->blocks_ref, s, rf)) != cudaSuccess) return e;
+    if ((e = launch_refine_amb(x->refine, x->refine_d64, x->scalars + kRefineCount, N, x->bestdf, x->kappa, x->amb,
+                               x->best_idx_df, x->sms, s)) != cudaSuccess)
+        return e;
+    if ((e = launch_refine_need64(x->refine, x->refine_d64, x->scalars + kRefineCount, N, x->bestdf, x->kappa,
+                                  x->amb, x->refine64, x->scalars + kRefine64Count, x->refine_cap, x->sms, s)) !=
+        cudaSuccess)
+        return e;
+    DtwRefineArgs r64 = rf;
+    r64.pairs = x->refine64; r64.count = x->scalars + kRefine64Count; r64.d64 = x->refine64_d64;
+    r64.best64 = x->best64;
+    if ((e = dtw_refine_launch(x->R_ref, x->blocks_ref, s, r64)) != cudaSuccess) return e;
+    if ((e = launch_refine_pick(x->refine64, x->refine64_d64, x->scalars + kRefine64Count, N, x->best64, x->best_idx,
                                 x->sms, s)) != cudaSuccess)
         return e;
     if ((e = launch_count_add(x->counters + kRefined, x->scalars + kRefineCount, s)) != cudaSuccess) return e;
-    if ((e = launch_finalize(Mb_cur, x->best64, x->best_idx, idx_out, dist_out, s)) != cudaSuccess) return e;
+    if ((e = launch_count_add(x->counters + kRefined64, x->scalars + kRefine64Count, s)) != cudaSuccess) return e;
+    if ((e = launch_finalize(Mb_cur, x->bestdf, x->best_idx_df, x->amb, x->best64, x->best_idx, idx_out, dist_out,
+                             s)) != cudaSuccess)
+        return e;
     TC_MARK(8);
     return cudaSuccess;
 }
@@ -446,6 +493,7 @@ int tcdtw_build(const float *cand, int64_t N, int32_t L, int32_t D, int32_t W, i
     x->G_pc = (L + o.w - 1) / o.w;
     x->ldE = ((int64_t)L * D + 31) / 32 * 32;
     x->rho_ref = prune_rho(L, D);
+    x->kappa = refine_kappa(L, D);
     x->rho = o.no_prune ? INFINITY : x->rho_ref;
     if (o.no_prune) { x->opts.use_pc = 0; x->opts.use_ti = 0; }
     // query block: bounded by the u32 pair ids and by ~4 GB of workspace
@@ -471,7 +519,7 @@ int tcdtw_build(const float *cand, int64_t N, int32_t L, int32_t D, int32_t W, i
     if (x->R_ref == 0) { free_index(x); return TCDTW_ERR_UNSUPPORTED; }
     x->blocks_nn = dtw_occupancy(x->tile, 1) * x->sms;
     if (x->blocks_nn < 1) x->blocks_nn = x->sms;
-    x->blocks_ref = x->sms * 2;
+    x->blocks_ref = x->sms * 8;  // one-warp blocks
     rc = alloc_index(x);
     if (rc) { free_index(x); return rc; }
     if (o.check_finite) {
@@ -534,6 +582,7 @@ int tcdtw_nn(tcdtw_index *x, const float *q, int64_t M, int64_t *idx, double *di
         stats->dtw_abandoned = c[kAbandoned];
         stats->cells = c[kCells];
         stats->refined = c[kRefined];
+        stats->refined64 = c[kRefined64];
     }
     return TCDTW_OK;
 }
@@ -668,7 +717,7 @@ int tcdtw_lower_bounds(const float *q, int64_t M, const float *c, int64_t N, int
     if (e == cudaSuccess) e = cudaMalloc(&bsf, sizeof(unsigned long long) * M);
     if (e == cudaSuccess) e = launch_iota_pairs(pairs, P, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, sizeof(float) * P, s);
-    if (e == cudaSuccess) e = launch_init_block(M, bsf, nullptr, nullptr, s);
+    if (e == cudaSuccess) e = launch_init_block(M, bsf, nullptr, nullptr, nullptr, nullptr, nullptr, s);
     PairListArgs pl;
     pl.Q = q; pl.C = c; pl.L = L; pl.D = D; pl.W = W; pl.pairs = pairs; pl.count = nullptr; pl.n_static = P;
     pl.N = N; pl.lb = out;

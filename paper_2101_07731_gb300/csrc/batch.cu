@@ -1,29 +1,39 @@
-// batch.cu -- many independent exact DTW-NN searches (uneven L, D, N, W) in one
-// persistent launch off a device work queue (not in the paper: a deployment pattern).
+// batch.cu -- many independent exact DTW-NN searches (uneven L, D, N, W) as one
+// captured graph of persistent launches, each taking work items from a device
+// queue (not in the paper: a deployment pattern).
 //
-// The launch keeps one CTA (4 warps) per resident slot; each CTA repeatedly takes the
-// next item of an ordered queue:
-//   PREP   (set, query)               envelope, neighbour distances, LB_PC boxes
-//   LBMV   (set, query tile, cand tile) one 32-query x 128-candidate LB_MV tile
-//   SEARCH (set, query)               seeds, their DTW, compaction, gated LB_PC/LB_TI,
-//                                     DTW of the survivors, FP64 refine, the answer
-// Items are queued in that order, so an item only ever waits for items with smaller
-// indices; an item is taken only by a running CTA, hence the items it waits for are
-// held by running CTAs that do not wait for it: the queue cannot deadlock.  The waits
-// (LBMV for all PREP of its set, SEARCH for all LBMV of its set) spin on counters with
-// an iteration limit; on expiry the launch records TCDTW_ERR_TIMEOUT, raises an abort
-// flag that every CTA checks before taking an item, and returns.  Every step is the
-// same computation as tcdtw_nn (same bounds, margins, FP64 refine), so the answers
-// are the same exact nearest neighbours.
+//   front   items PREP (set, query): envelope, neighbour distances, LB_PC boxes;
+//           LBMV (set, query tile, cand tile): one 32 x 128 LB_MV tile;
+//           SEED (set, query): the seed candidates (smallest LB_MV) of the query.
+//           Queued in that order; LBMV waits for its set's PREP items and SEED for
+//           its set's LBMV items on device counters (bounded spins, see below).
+//   dtw     the seeds' DTW: warps take entries of one set at a time off the set's
+//           cursor, sets in decreasing cost, each set with its own band tile.
+//   mid     items (set, query): compaction against the seeded best-so-far, gated
+//           LB_PC / LB_TI; the survivors join the set's DTW work list.
+//   dtw     the survivors' DTW with early abandoning, as above.
+//   refine  items (set, four queries): per warp one query, double-float recompute
+//           of the entries FP32 cannot separate from the best, FP64 where
+//           double-float cannot either; the answer.
+// The DTW runs in launches of its own: one kernel holding the LB_MV stream, the
+// refine and the band DP spilled registers inside the DP loop and ran several times
+// slower.  In the front launch an item only waits for items with smaller queue
+// indices, which running CTAs hold and which never wait for it, so it cannot
+// deadlock; each wait gives up after an iteration limit, records
+// TCDTW_ERR_TIMEOUT, raises an abort flag that every CTA checks before taking an
+// item, and returns.  Every step is the same computation as tcdtw_nn (same bounds,
+// margins, refine), so the answers are the same exact nearest neighbours.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <vector>
 
 #include "api_internal.h"
+#include "df.cuh"
 #include "dtw_core.cuh"
 #include "lb_device.cuh"
 #include "lb_kernels.cuh"
@@ -32,11 +42,15 @@
 namespace tc {
 
 constexpr int kBatchR = 8;          // rows per lane of the batched DTW
-constexpr int kBatchMaxD = 12;      // dimensions the megakernel handles (D <= 8 exact, 9..12 padded to 12)
+constexpr int kBatchMaxD = 12;      // dimensions of the single-graph path (D <= 8 exact, 9..12 padded to 12)
 constexpr int kBatchThreads = 128;  // 4 warps per CTA
 constexpr int kBatchQB = 32;        // queries per LB_MV tile
+constexpr int kSeedSlots = 8;       // seed slots per query
 constexpr long long kSpinLimit = 4000000;  // ~1 s of 256 ns sleeps
-constexpr size_t kBatchSmem = 48 * 1024;   // LB_MV double buffers / DTW staging / box scratch
+constexpr size_t kBatchSmem = 48 * 1024;   // LB_MV double buffers / box scratch / FP64 row slots
+
+// Per-set counters (ints, zeroed before every run).
+enum : int { kCntPrep = 0, kCntMv, kCntList, kCntSeedCursor, kCntSurvCursor, kCntPerSet };
 
 struct BatchSet {
     const float *cand, *q;
@@ -44,32 +58,49 @@ struct BatchSet {
     double *dist;
     int64_t N;
     int L, D, W, K, M;
-    int G, Rref, S;
+    int G, dcase, Rref, S;  // DTW lanes per pair and tile DM; FP64 rows per lane; seeds per query
     int use_pc, use_ti, Lq, w, P, Gpc, np2, vec4, check_finite;
     float e_pc, e_ti, rho, rho_ref;
+    double kappa;
     int64_t ldE;
     int n_qtiles, n_ctiles;
     float *U, *Lo, *dq_lo, *dq_hi, *boxes;
     int32_t *box_counts;
-    float *lbm, *surv_lb, *surv_dtw, *seed_dtw;
-    uint32_t *surv;
-    double *d64;
-    int *prep_done, *mv_done;
+    float *lbm;                          // [M][N] LB_MV
+    uint32_t *surv;                      // [M][N] survivor candidate ids, per query
+    float *surv_lb, *surv_dtw;           // [M][N]
+    uint32_t *list;                      // [M*N] DTW work list: q*N + position in the query's survivors
+    uint32_t *seeds;                     // [M][8] (UINT32_MAX: empty slot)
+    float *seed_dtw;                     // [M][8]
+    double *d64;                         // [M][N+8] refine values
+    unsigned long long *bsf;             // [M] packed best-so-far
+    int *nseed, *ncnt;                   // [M]
+    int *cnt;                            // kCntPerSet counters
 };
 
-enum : int { kItemPrep = 0, kItemMv = 1, kItemSearch = 2, kItemStall = 3 };
+enum : int { kItemPrep = 0, kItemMv, kItemSeed, kItemMid, kItemRefine, kItemStall };
+constexpr int kRefinePerItem = 4;  // queries per refine item (one per warp)
 struct BatchItem {
     int kind, set, a, b;
 };
 
 struct BatchCtl {
-    int next;
+    int next[3];  // cursors of the front, mid and refine item ranges
     int abort;
-    int never;  // stays 0: the self-test waits on it
-    int pad;
+    int never;    // stays 0: the self-test waits on it
     DevStatus status;
-    unsigned long long counters[8];  // started, abandoned, cells, pruned at DTW, pruned MV, PC, TI, refined
+    unsigned long long counters[9];  // started, abandoned, cells, pruned at DTW, pruned MV, PC, TI, refined,
+                                     // refined in FP64
 };
+
+// Grab the next item index of range [begin, end) for the CTA (end when aborted).
+__device__ __forceinline__ int grab_item(BatchCtl *ctl, int which, int begin, int end) {
+    __shared__ int s_item;
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = *(volatile int *)&ctl->abort ? end : begin + atomicAdd(&ctl->next[which], 1);
+    __syncthreads();
+    return s_item;
+}
 
 __device__ __forceinline__ int ld_acquire_s32(const int *p) {
     int v;
@@ -161,7 +192,7 @@ __device__ void prep_item(const BatchSet &S, int q, float *smem, BatchCtl *ctl) 
     }
 }
 
-// ------------------------------------------------------------------ SEARCH pieces
+// ------------------------------------------------------------------ compaction
 // Ordered compaction of one row by the CTA: entries n with row[n] <= thr, in
 // increasing n, to out_idx / out_lb; returns the count on every thread.
 __device__ int compact_row(const float *__restrict__ row, int64_t N, float thr, uint32_t *__restrict__ out_idx,
@@ -198,57 +229,125 @@ __device__ int compact_row(const float *__restrict__ row, int64_t N, float thr, 
     return c;
 }
 
-// DTW of the candidates list[0..n) against query q, warp lockstep batches (one pair
-// per group of S.G lanes), abandoning against and lowering the CTA's best-so-far.
+// SEED: the S smallest LB_MV of the query become its seeds (their bounds in the row
+// are set to +inf so that compaction skips them); the best-so-far starts at +inf.
+__device__ void seed_item(const BatchSet &S, int q) {
+    __shared__ uint32_t picked[kSeedSlots];
+    seed_topk_row(S.lbm + (size_t)q * S.N, S.N, S.S, picked);
+    if (threadIdx.x < kSeedSlots) {
+        const uint32_t n = threadIdx.x < (unsigned)S.S ? picked[threadIdx.x] : 0xffffffffu;
+        S.seeds[(size_t)q * kSeedSlots + threadIdx.x] = n;
+    }
+    if (threadIdx.x == 0) {
+        int ns = 0;
+        for (int k = 0; k < S.S; ++k) ns += picked[k] != 0xffffffffu;
+        S.nseed[q] = ns;
+        S.bsf[q] = pack_best(TC_INF, 0xffffffffu);
+    }
+}
+
+__global__ void __launch_bounds__(kBatchThreads) k_batch_front(const BatchSet *__restrict__ sets,
+                                                               const BatchItem *__restrict__ items, int begin,
+                                                               int end, BatchCtl *ctl, long long spin_limit) {
+    extern __shared__ __align__(16) float bsm[];
+    for (;;) {
+        const int it = grab_item(ctl, 0, begin, end);
+        if (it >= end) break;
+        const BatchItem item = items[it];
+        if (item.kind == kItemStall) {  // waits for a counter nothing increments (self-test)
+            batch_wait(&ctl->never, 1, spin_limit, ctl, it);
+            continue;
+        }
+        const BatchSet &S = sets[item.set];
+        if (item.kind == kItemPrep) {
+            prep_item(S, item.a, bsm, ctl);
+            batch_done(S.cnt + kCntPrep);
+        } else if (item.kind == kItemMv) {
+            if (!batch_wait(S.cnt + kCntPrep, S.M, spin_limit, ctl, it)) continue;
+            __threadfence();
+            float(*sc)[kMvRows * kMvChunk] = (float(*)[kMvRows * kMvChunk])bsm;
+            float(*su)[kBatchQB * kMvChunk] = (float(*)[kBatchQB * kMvChunk])(bsm + 2 * kMvRows * kMvChunk);
+            float(*sl)[kBatchQB * kMvChunk] =
+                (float(*)[kBatchQB * kMvChunk])(bsm + 2 * kMvRows * kMvChunk + 2 * kBatchQB * kMvChunk);
+            lb_mv_tile<kBatchQB>(S.cand, S.N, S.L * S.D, S.vec4 != 0, S.U, S.Lo, S.ldE, S.M, S.lbm, S.N,
+                                 (int64_t)item.b * kMvRows, item.a * kBatchQB, sc, su, sl);
+            batch_done(S.cnt + kCntMv);
+        } else if (item.kind == kItemSeed) {
+            if (!batch_wait(S.cnt + kCntMv, S.n_qtiles * S.n_ctiles, spin_limit, ctl, it)) continue;
+            __threadfence();
+            seed_item(S, item.a);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ DTW launches
+// Phase 0: the seed entries i < M*8 (query i/8, slot i%8); phase 1: the work list.
+// A warp takes 32/G consecutive entries of one set (one per lane group) and runs
+// them in lockstep, as the single-set kernel does; the sets follow each other in
+// the order given, each with its own cursor, so warps move on as a set runs dry.
 template <int DM>
-__device__ __noinline__ void batch_dtw_list(const BatchSet &S, int q, const uint32_t *list, const float *lbl, int n, float *out,
-                               unsigned long long *bsf, int *cursor, float *stage, BatchCtl *ctl) {
+__device__ __forceinline__ void dtw_set(const BatchSet &S, int phase, float *stage, BatchCtl *ctl) {
     Grp g = make_grp(S.G);
     g.mask = 0xffffffffu;
-    const int gpw = 32 / S.G;
+    const int G = S.G, gpw = 32 / G;
     const int L = S.L, D = S.D, W = S.W;
+    const int64_t N = S.N;
     const int nv = (L + kBatchR - 1) / kBatchR;
-    const float *qa = S.q + (size_t)q * L * D;
+    const int n_entries = phase == 0 ? S.M * kSeedSlots : S.cnt[kCntList];
+    int *cursor = S.cnt + (phase == 0 ? kCntSeedCursor : kCntSurvCursor);
     unsigned long long started = 0, aband = 0, ncells = 0, pruned = 0;
     for (;;) {
         int base = 0;
         if ((threadIdx.x & 31) == 0) base = atomicAdd(cursor, gpw);
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= n) break;
-        const int e = base + (threadIdx.x & 31) / S.G;
-        bool live = e < n;
-        const uint32_t cn = live ? list[e] : 0u;
+        if (base >= n_entries) break;
+        const int e = base + (threadIdx.x & 31) / G;
+        bool live = e < n_entries;
+        int q = 0;
+        uint32_t cn = 0;
+        float lbe = 0.f;
+        float *out = nullptr;
         if (live) {
-            const float lbe = lbl ? lbl[e] : 0.f;
-            const float thr = prune_threshold(ld_volatile_u64(bsf), S.rho);
+            if (phase == 0) {
+                q = e / kSeedSlots;
+                cn = S.seeds[e];
+                out = S.seed_dtw + e;
+                live = cn != 0xffffffffu;
+            } else {
+                const uint32_t pid = S.list[e];
+                q = (int)(pid / (uint64_t)N);
+                cn = S.surv[pid];
+                lbe = S.surv_lb[pid];
+                out = S.surv_dtw + pid;
+            }
+        }
+        if (live) {
+            const float thr = prune_threshold(ld_volatile_u64(S.bsf + q), S.rho);
             if (!(lbe <= thr) || lbe == TC_INF) {
                 if (g.lig == 0 && lbe != TC_INF) ++pruned;
+                if (g.lig == 0) *out = TC_INF;
                 live = false;
             }
         }
         NnHooks h;
-        h.bsf = bsf;
+        h.bsf = S.bsf + q;
         h.rho = S.rho;
         bool ab = false;
         long long cells = 0;
-        float r = band_pass<kBatchR, DM>(qa, S.cand + (size_t)cn * L * D, L, D, W, 0, nv, g, h, live, &ab, &cells,
-                                         stage);
+        float r = band_pass<kBatchR, DM>(S.q + (size_t)q * L * D, S.cand + (size_t)cn * L * D, L, D, W, 0, nv, g, h,
+                                         live, &ab, &cells, stage);
         r = grp_min(r, g);
         long long cs = cells;
-        for (int o = S.G >> 1; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
-        if (e < n && g.lig == 0) {
-            if (!live) {
-                out[e] = TC_INF;
+        for (int o = G >> 1; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
+        if (live && g.lig == 0) {
+            ++started;
+            ncells += (unsigned long long)cs;
+            if (ab) {
+                ++aband;
+                *out = TC_INF;
             } else {
-                ++started;
-                ncells += (unsigned long long)cs;
-                if (ab) {
-                    ++aband;
-                    out[e] = TC_INF;
-                } else {
-                    out[e] = r;
-                    atomicMin(bsf, pack_best(r, cn));
-                }
+                *out = r;
+                atomicMin(S.bsf + q, pack_best(r, cn));
             }
         }
     }
@@ -260,55 +359,79 @@ __device__ __noinline__ void batch_dtw_list(const BatchSet &S, int q, const uint
     }
 }
 
-__device__ void batch_dtw_dispatch(const BatchSet &S, int q, const uint32_t *list, const float *lbl, int n,
-                                   float *out, unsigned long long *bsf, int *cursor, float *stage, BatchCtl *ctl) {
-    switch (S.D <= 8 ? S.D : 12) {
-#define TC_BD(DMV) \
-    case DMV: batch_dtw_list<DMV>(S, q, list, lbl, n, out, bsf, cursor, stage, ctl); break;
-        TC_BD(1) TC_BD(2) TC_BD(3) TC_BD(4) TC_BD(5) TC_BD(6) TC_BD(7) TC_BD(8) TC_BD(12)
-#undef TC_BD
-        default: break;
-    }
+// One launch per tile class (DM) and phase: the sets order[0..nsets) of the class.
+// (One kernel holding every DM variant does not reuse registers across them and
+// spills inside the DP loop.)
+template <int DM>
+__global__ void __launch_bounds__(kBatchThreads, 3) k_batch_dtw(const BatchSet *__restrict__ sets,
+                                                                const int *__restrict__ order, int nsets, int phase,
+                                                                BatchCtl *ctl) {
+    extern __shared__ __align__(16) float stage_smem[];
+    float *stage = stage_smem + (size_t)threadIdx.x * kBatchR * DM;
+    for (int oi = 0; oi < nsets; ++oi) dtw_set<DM>(sets[order[oi]], phase, stage, ctl);
 }
 
-__device__ __noinline__ double batch_fp64(const BatchSet &S, const float *a, const float *b, const Grp &g) {
-    switch (S.Rref) {
-#define TC_BR(RV) \
-    case RV: return band_pass64<RV>(a, b, S.L, S.D, S.W, g);
-        TC_REFINE_RS(TC_BR)
-#undef TC_BR
+#define TC_BATCH_DMS(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(12)
+constexpr int kNumDmClasses = 9;
+__host__ __device__ constexpr int dm_class_of(int D) { return D <= 8 ? D - 1 : 8; }
+constexpr int kDmOfClass[kNumDmClasses] = {1, 2, 3, 4, 5, 6, 7, 8, 12};
+
+cudaError_t launch_batch_dtw(int dm, int grid, cudaStream_t s, const BatchSet *sets, const int *order, int nsets,
+                             int phase, BatchCtl *ctl) {
+    switch (dm) {
+#define TC_BL(DMV)                                                                                        \
+    case DMV:                                                                                             \
+        k_batch_dtw<DMV><<<grid, kBatchThreads, (size_t)kBatchThreads * kBatchR * DMV * sizeof(float), s>>>( \
+            sets, order, nsets, phase, ctl);                                                              \
+        return cudaGetLastError();
+        TC_BATCH_DMS(TC_BL)
+#undef TC_BL
     }
-    return __longlong_as_double(0x7ff0000000000000LL);
+    return cudaErrorInvalidValue;
 }
 
-__device__ void search_item(const BatchSet &S, int q, float *smem, BatchCtl *ctl) {
-    __shared__ uint32_t seeds[8];
-    __shared__ float seed_dtw[8];
-    __shared__ unsigned long long bsf, best64, best_idx;
-    __shared__ int cursor;
+// Opt the kernel in to `smem` bytes of dynamic shared memory (its static shared
+// memory comes on top, so 48 KB of dynamic memory already needs the opt-in).
+cudaError_t kernel_grid(const void *fn, size_t smem, int *grid) {
+    if (smem > 0) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kBatchThreads, smem);
+    if (e != cudaSuccess) return e;
+    *grid = (occ > 0 ? occ : 1) * num_sms();
+    return cudaSuccess;
+}
+
+cudaError_t batch_dtw_grid(int dm, int *grid) {
+    switch (dm) {
+#define TC_BO(DMV) \
+    case DMV: return kernel_grid((const void *)k_batch_dtw<DMV>, (size_t)kBatchThreads * kBatchR * DMV * sizeof(float), grid);
+        TC_BATCH_DMS(TC_BO)
+#undef TC_BO
+    }
+    return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------------ mid launch
+// Compaction against the seeded best-so-far (seeds are +inf in the row), gated
+// tight bounds (one warp per survivor), and the survivors' entries q*N + k appended
+// to the set's work list in one reservation.
+__device__ void mid_item(const BatchSet &S, int q, BatchCtl *ctl) {
+    __shared__ int s_base;
     const int L = S.L, D = S.D;
     const int64_t N = S.N;
-    float *row = S.lbm + (size_t)q * N;
-    float *stage = smem + (size_t)threadIdx.x * kBatchR * kBatchMaxD;
-    if (threadIdx.x == 0) {
-        bsf = pack_best(TC_INF, 0xffffffffu);
-        best64 = 0x7ff0000000000000ull;
-        best_idx = ~0ull;
-        cursor = 0;
-    }
-    // seeds and their DTW
-    seed_topk_row(row, N, S.S, seeds);
-    int nseed = 0;
-    for (int k = 0; k < S.S; ++k) nseed += seeds[k] != 0xffffffffu;
-    batch_dtw_dispatch(S, q, seeds, nullptr, nseed, seed_dtw, &bsf, &cursor, stage, ctl);
-    __syncthreads();
-    // compaction against the seeded best-so-far (seeds are +inf in the row now)
-    const float thr = prune_threshold(bsf, S.rho);
+    const unsigned long long *bsf = S.bsf + q;
+    const float thr = prune_threshold(ld_volatile_u64(bsf), S.rho);
     uint32_t *sv = S.surv + (size_t)q * N;
-    float *slb = S.surv_lb + (size_t)q * N, *sdt = S.surv_dtw + (size_t)q * N;
-    const int cnt = compact_row(row, N, thr, sv, slb);
-    if (threadIdx.x == 0) atomicAdd(&ctl->counters[4], (unsigned long long)(N - cnt - nseed));
-    // gated tight bounds, one warp per survivor
+    float *slb = S.surv_lb + (size_t)q * N;
+    const int cnt = compact_row(S.lbm + (size_t)q * N, N, thr, sv, slb);
+    if (threadIdx.x == 0) {
+        atomicAdd(&ctl->counters[4], (unsigned long long)(N - cnt - S.nseed[q]));
+        s_base = atomicAdd(S.cnt + kCntList, cnt);
+        S.ncnt[q] = cnt;
+    }
     const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
     for (int pass = 0; pass < 2; ++pass) {
         if ((pass == 0 && !S.use_pc) || (pass == 1 && !S.use_ti)) continue;
@@ -316,23 +439,22 @@ __device__ void search_item(const BatchSet &S, int q, float *smem, BatchCtl *ctl
         for (int e = warp; e < cnt; e += nw) {
             const float cur = slb[e];
             if (!(cur < TC_INF)) continue;
-            const unsigned long long key = ld_volatile_u64(&bsf);
+            const unsigned long long key = ld_volatile_u64(bsf);
             if (cur > prune_threshold(key, S.rho)) continue;
             if (!(cur > (pass == 0 ? S.e_pc : S.e_ti) * best_dist(key))) continue;
             const float *c = S.cand + (size_t)sv[e] * L * D;
             float bound = 0.f;
             bool dropped;
             if (pass == 0) {
-                dropped = D <= 8 ? lb_pc_pair<8, true>(c, S.boxes + (size_t)q * S.Gpc * S.K * 2 * D,
-                                                 S.box_counts + (size_t)q * S.Gpc, L, D, S.K, S.w, &bsf, S.rho, &bound)
-                                 : lb_pc_pair<16, true>(c, S.boxes + (size_t)q * S.Gpc * S.K * 2 * D,
-                                                  S.box_counts + (size_t)q * S.Gpc, L, D, S.K, S.w, &bsf, S.rho, &bound);
+                const float *bx = S.boxes + (size_t)q * S.Gpc * S.K * 2 * D;
+                const int32_t *bc = S.box_counts + (size_t)q * S.Gpc;
+                dropped = D <= 8 ? lb_pc_pair<8>(c, bx, bc, L, D, S.K, S.w, bsf, S.rho, &bound)
+                                 : lb_pc_pair<16>(c, bx, bc, L, D, S.K, S.w, bsf, S.rho, &bound);
             } else {
                 const float *qa = S.q + (size_t)q * L * D;
-                dropped = D <= 8 ? lb_ti_pair<8, true>(c, qa, S.dq_lo + (size_t)q * L, S.dq_hi + (size_t)q * L, L, D, S.W,
-                                                 S.P, &bsf, S.rho, &bound)
-                                 : lb_ti_pair<16, true>(c, qa, S.dq_lo + (size_t)q * L, S.dq_hi + (size_t)q * L, L, D, S.W,
-                                                  S.P, &bsf, S.rho, &bound);
+                const float *dl = S.dq_lo + (size_t)q * L, *dh = S.dq_hi + (size_t)q * L;
+                dropped = D <= 8 ? lb_ti_pair<8>(c, qa, dl, dh, L, D, S.W, S.P, bsf, S.rho, &bound)
+                                 : lb_ti_pair<16>(c, qa, dl, dh, L, D, S.W, S.P, bsf, S.rho, &bound);
             }
             if (lane == 0) {
                 if (dropped) { slb[e] = TC_INF; ++pruned; }
@@ -340,87 +462,162 @@ __device__ void search_item(const BatchSet &S, int q, float *smem, BatchCtl *ctl
             }
         }
         if (lane == 0 && pruned) atomicAdd(&ctl->counters[5 + pass], pruned);
-        __syncthreads();
-    }
-    // DTW of the survivors
-    if (threadIdx.x == 0) cursor = 0;
-    __syncthreads();
-    batch_dtw_dispatch(S, q, sv, slb, cnt, sdt, &bsf, &cursor, stage, ctl);
-    __syncthreads();
-    // FP64 refine of every candidate within the rounding margin of the best
-    const float tfin = prune_threshold(bsf, S.rho_ref);
-    Grp g32 = make_grp(32);
-    const float *qa = S.q + (size_t)q * L * D;
-    double *d64 = S.d64 + (size_t)q * (N + 8);
-    const int ntot = nseed + cnt;
-    for (int e = warp; e < ntot; e += nw) {
-        const float d32 = e < nseed ? seed_dtw[e] : sdt[e - nseed];
-        const uint32_t cn = e < nseed ? seeds[e] : sv[e - nseed];
-        double r = __longlong_as_double(0x7ff0000000000000LL);
-        if (d32 <= tfin) {
-            r = batch_fp64(S, qa, S.cand + (size_t)cn * L * D, g32);
-            r = grp_min(r, g32);
-            if (lane == 0) {
-                atomicMin(&best64, (unsigned long long)__double_as_longlong(r));
-                atomicAdd(&ctl->counters[7], 1ull);
-            }
-        }
-        if (lane == 0) d64[e] = r;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < ntot; e += blockDim.x) {
-        if ((unsigned long long)__double_as_longlong(d64[e]) == best64) {
-            const uint32_t cn = e < nseed ? seeds[e] : sv[e - nseed];
-            atomicMin(&best_idx, (unsigned long long)cn);
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        S.idx[q] = (int64_t)best_idx;
-        S.dist[q] = __longlong_as_double((long long)best64);
-    }
-    __syncthreads();
+    const int base = s_base;
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) S.list[base + k] = (uint32_t)(q * N + k);
 }
 
-// ------------------------------------------------------------------ the persistent kernel
-__global__ void __launch_bounds__(kBatchThreads, 3) k_batch(const BatchSet *__restrict__ sets,
-                                                         const BatchItem *__restrict__ items, int n_items,
-                                                         BatchCtl *ctl, long long spin_limit) {
-    extern __shared__ __align__(16) float bsm[];
-    __shared__ int s_item;
+__global__ void __launch_bounds__(kBatchThreads) k_batch_mid(const BatchSet *__restrict__ sets,
+                                                             const BatchItem *__restrict__ items, int begin, int end,
+                                                             BatchCtl *ctl) {
     for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_item = *(volatile int *)&ctl->abort ? n_items : atomicAdd(&ctl->next, 1);
-        __syncthreads();
-        const int it = s_item;
-        if (it >= n_items) break;
+        const int it = grab_item(ctl, 1, begin, end);
+        if (it >= end) break;
+        const BatchItem item = items[it];
+        mid_item(sets[item.set], item.a, ctl);
+    }
+}
+
+// ------------------------------------------------------------------ refine launch
+__device__ __noinline__ double batch_fp64(const BatchSet &S, const float *a, const float *b, const Grp &g,
+                                          double *ad) {
+    switch (S.Rref) {
+#define TC_BR(RV) \
+    case RV: return band_pass64<RV>(a, b, S.L, S.D, S.W, g, ad);
+        TC_REFINE_RS(TC_BR)
+#undef TC_BR
+    }
+    return __longlong_as_double(0x7ff0000000000000LL);
+}
+
+__device__ __noinline__ double batch_df(const BatchSet &S, const float *a, const float *b, const Grp &g) {
+    switch (S.Rref) {
+#define TC_BR(RV) \
+    case RV: return band_pass_df<RV>(a, b, S.L, S.D, S.W, g);
+        TC_REFINE_RS(TC_BR)
+#undef TC_BR
+    }
+    return __longlong_as_double(0x7ff0000000000000LL);
+}
+
+// Refine of query q by one warp: every entry that FP32 cannot separate from the best
+// gets its double-float DTW; only when that still leaves two or more inseparable
+// entries (or no finite value) do those get the FP64 recompute.  Entry e < nseed is
+// seed e, entry nseed + k is survivor k.
+__device__ void refine_warp(const BatchSet &S, int q, double *ad, BatchCtl *ctl) {
+    const int lane = threadIdx.x & 31;
+    const int L = S.L, D = S.D;
+    const int64_t N = S.N;
+    const int nseed = __ldcg(S.nseed + q), cnt = __ldcg(S.ncnt + q);
+    const int ntot = nseed + cnt;
+    const float *qa = S.q + (size_t)q * L * D;
+    const uint32_t *sd = S.seeds + (size_t)q * kSeedSlots, *sv = S.surv + (size_t)q * N;
+    const float *sdd = S.seed_dtw + (size_t)q * kSeedSlots, *sdt = S.surv_dtw + (size_t)q * N;
+    double *d64 = S.d64 + (size_t)q * (N + 8);
+    const float tfin = prune_threshold(ld_volatile_u64(S.bsf + q), S.rho_ref);
+    const double DINF = __longlong_as_double(0x7ff0000000000000LL);
+    Grp g32 = make_grp(32);
+    unsigned long long bestdf = 0x7ff0000000000000ull, refined = 0;
+    // entries in chunks of 32: a ballot finds the ones to refine, the warp takes them in turn
+    for (int e0 = 0; e0 < ntot; e0 += 32) {
+        const int e = e0 + lane;
+        const float d32 = e < ntot ? (e < nseed ? __ldcg(sdd + e) : __ldcg(sdt + (e - nseed))) : TC_INF;
+        const bool want = e < ntot && d32 <= tfin;
+        if (e < ntot && !want) d64[e] = DINF;
+        unsigned todo = __ballot_sync(0xffffffffu, want);
+        while (todo) {
+            const int k = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int ek = e0 + k;
+            const uint32_t cn = ek < nseed ? __ldcg(sd + ek) : __ldcg(sv + (ek - nseed));
+            double r = batch_df(S, qa, S.cand + (size_t)cn * L * D, g32);
+            r = grp_min(r, g32);
+            if (lane == 0) d64[ek] = r;
+            const unsigned long long rb = (unsigned long long)__double_as_longlong(r);
+            bestdf = rb < bestdf ? rb : bestdf;
+            ++refined;
+        }
+    }
+    __syncwarp();
+    const double thr_df = __dmul_ru(__longlong_as_double((long long)bestdf), S.kappa);
+    int amb = 0;
+    unsigned long long best_idx = ~0ull;
+    for (int e = lane; e < ntot; e += 32) {
+        const double x = d64[e];
+        if (x == DINF) continue;
+        if (!(x > thr_df)) ++amb;
+        if ((unsigned long long)__double_as_longlong(x) == bestdf) {
+            const unsigned long long cn = e < nseed ? __ldcg(sd + e) : __ldcg(sv + (e - nseed));
+            best_idx = cn < best_idx ? cn : best_idx;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        amb += __shfl_xor_sync(0xffffffffu, amb, o);
+        const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best_idx, o);
+        best_idx = ob < best_idx ? ob : best_idx;
+    }
+    // refine entries marked +inf above were never refined; a refined entry whose
+    // value is +inf (overflow) makes the query take the FP64 path
+    bool need64 = amb >= 2 || !(__longlong_as_double((long long)bestdf) < DINF);
+    unsigned long long best64 = 0x7ff0000000000000ull, refined64 = 0;
+    if (need64) {
+        best_idx = ~0ull;
+        for (int e0 = 0; e0 < ntot; e0 += 32) {
+            const int e = e0 + lane;
+            bool want = false;
+            if (e < ntot) {
+                const float d32 = e < nseed ? __ldcg(sdd + e) : __ldcg(sdt + (e - nseed));
+                want = d32 <= tfin && !(d64[e] > thr_df);
+            }
+            unsigned todo = __ballot_sync(0xffffffffu, want);
+            while (todo) {
+                const int k = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const int ek = e0 + k;
+                const uint32_t cn = ek < nseed ? __ldcg(sd + ek) : __ldcg(sv + (ek - nseed));
+                double r = batch_fp64(S, qa, S.cand + (size_t)cn * L * D, g32, ad);
+                r = grp_min(r, g32);
+                const unsigned long long rb = (unsigned long long)__double_as_longlong(r);
+                if (rb < best64 || (rb == best64 && cn < best_idx)) {
+                    if (rb < best64) best_idx = cn;
+                    best64 = rb;
+                    best_idx = cn < best_idx ? cn : best_idx;
+                }
+                ++refined64;
+            }
+        }
+    }
+    if (lane == 0) {
+        S.idx[q] = (int64_t)best_idx;
+        S.dist[q] = __longlong_as_double((long long)(need64 ? best64 : bestdf));
+        atomicAdd(&ctl->counters[7], refined);
+        if (refined64) atomicAdd(&ctl->counters[8], refined64);
+    }
+}
+
+__global__ void __launch_bounds__(kBatchThreads) k_batch_refine(const BatchSet *__restrict__ sets,
+                                                                const BatchItem *__restrict__ items, int begin,
+                                                                int end, BatchCtl *ctl) {
+    extern __shared__ __align__(16) float bsm[];
+    constexpr int kAdPerLane = (int)(kBatchSmem / 4 / 32 / sizeof(double));
+    for (;;) {
+        const int it = grab_item(ctl, 2, begin, end);
+        if (it >= end) break;
         const BatchItem item = items[it];
         const BatchSet &S = sets[item.set];
-        if (item.kind == kItemPrep) {
-            prep_item(S, item.a, bsm, ctl);
-            batch_done(S.prep_done);
-        } else if (item.kind == kItemMv) {
-            if (!batch_wait(S.prep_done, S.M, spin_limit, ctl, it)) continue;
-            __threadfence();
-            float(*sc)[kMvRows * kMvChunk] = (float(*)[kMvRows * kMvChunk])bsm;
-            float(*su)[kBatchQB * kMvChunk] = (float(*)[kBatchQB * kMvChunk])(bsm + 2 * kMvRows * kMvChunk);
-            float(*sl)[kBatchQB * kMvChunk] =
-                (float(*)[kBatchQB * kMvChunk])(bsm + 2 * kMvRows * kMvChunk + 2 * kBatchQB * kMvChunk);
-            lb_mv_tile<kBatchQB>(S.cand, S.N, S.L * S.D, S.vec4 != 0, S.U, S.Lo, S.ldE, S.M, S.lbm, S.N,
-                                 (int64_t)item.b * kMvRows, item.a * kBatchQB, sc, su, sl);
-            batch_done(S.mv_done);
-        } else if (item.kind == kItemSearch) {
-            if (!batch_wait(S.mv_done, S.n_qtiles * S.n_ctiles, spin_limit, ctl, it)) continue;
-            __threadfence();
-            search_item(S, item.a, bsm, ctl);
-        } else {  // kItemStall: waits for a counter nothing increments (self-test)
-            batch_wait(&ctl->never, 1, spin_limit, ctl, it);
+        const int warp = threadIdx.x >> 5;
+        const int qw = item.a + warp;
+        if (warp < kRefinePerItem && qw < S.M) {
+            double *ad = S.Rref * S.D <= kAdPerLane
+                             ? (double *)bsm + (size_t)warp * 32 * kAdPerLane + (size_t)(threadIdx.x & 31) * kAdPerLane
+                             : nullptr;
+            refine_warp(S, qw, ad, ctl);
         }
     }
 }
 
 static_assert(2 * kMvRows * kMvChunk * 4 + 4 * kBatchQB * kMvChunk * 4 <= kBatchSmem, "LB_MV buffers");
-static_assert(kBatchThreads * kBatchR * kBatchMaxD * 4 <= kBatchSmem, "DTW staging");
 
 // ------------------------------------------------------------------ host side
 namespace {
@@ -439,8 +636,13 @@ struct BatchPlan {
     BatchSet *d_sets = nullptr;
     BatchItem *d_items = nullptr;
     BatchCtl *d_ctl = nullptr;
-    int *d_counts = nullptr;
-    int n_items = 0, n_sets = 0, grid = 0;
+    int *d_counts = nullptr, *d_order = nullptr;
+    int n_sets = 0;
+    int front_end = 0, mid_end = 0, n_items = 0;  // item ranges [0, front_end), [front_end, mid_end), [mid_end, n_items)
+    int grid_front = 0, grid_mid = 0, grid_refine = 0;
+    // DTW launches: per tile class present, its sets d_order[off, off + n) and grid
+    struct DtwClass { int dm, off, n, grid; };
+    std::vector<DtwClass> classes;
     cudaGraphExec_t exec = nullptr;
     int launches = 0;
     unsigned long long last_use = 0;
@@ -461,9 +663,10 @@ bool same_key(const BatchPlan *p, const tcdtw_dataset *sets, int n, const tcdtw_
     return memcmp(p->key.data(), sets, sizeof(tcdtw_dataset) * n) == 0;
 }
 
-bool megakernel_ok(const tcdtw_dataset &d, const tcdtw_opts &o) {
+bool graph_path_ok(const tcdtw_dataset &d, const tcdtw_opts &o) {
     const int W = d.W > d.L - 1 ? d.L - 1 : d.W;
-    return d.D <= kBatchMaxD && batch_G(W) > 0 && refine_rows_for(W) > 0 && d.M <= 65535 && o.seed_s <= 8;
+    return d.D <= kBatchMaxD && batch_G(W) > 0 && refine_rows_for(W) > 0 && d.M <= 65535 &&
+           o.seed_s <= kSeedSlots && (double)d.M * (double)d.N < 4.29e9;
 }
 
 template <typename T>
@@ -473,6 +676,8 @@ T *carve(char *&p, size_t n) {
     p += sizeof(T) * (n ? n : 1);
     return r;
 }
+template <typename T>
+size_t carve_bytes(size_t n) { return sizeof(T) * (n ? n : 1) + 256; }
 
 int build_plan(const tcdtw_dataset *sets, const std::vector<int> &mk, const tcdtw_opts &o, cudaStream_t s,
                BatchPlan **out) {
@@ -487,6 +692,7 @@ int build_plan(const tcdtw_dataset *sets, const std::vector<int> &mk, const tcdt
         b.cand = d.cand; b.q = d.q; b.idx = d.idx; b.dist = d.dist;
         b.N = d.N; b.L = d.L; b.D = d.D; b.W = d.W > d.L - 1 ? d.L - 1 : d.W; b.K = d.K; b.M = (int)d.M;
         b.G = batch_G(b.W);
+        b.dcase = d.D <= 8 ? d.D : 12;
         b.Rref = refine_rows_for(b.W);
         b.S = (int)(o.seed_s < d.N ? o.seed_s : d.N);
         b.check_finite = o.check_finite != 0;
@@ -502,25 +708,46 @@ int build_plan(const tcdtw_dataset *sets, const std::vector<int> &mk, const tcdt
         }
         b.vec4 = lb_mv_vec4(d.cand, d.L * d.D);
         b.rho_ref = prune_rho(d.L, d.D);
+        b.kappa = refine_kappa(d.L, d.D);
         b.rho = o.no_prune ? INFINITY : b.rho_ref;
         b.ldE = ((int64_t)d.L * d.D + 31) / 32 * 32;
         b.n_qtiles = (int)((d.M + kBatchQB - 1) / kBatchQB);
         b.n_ctiles = (int)((d.N + kMvRows - 1) / kMvRows);
-        const int64_t Mp = (d.M + 1) / 2 * 2, M = d.M, N = d.N;
-        bytes += 2 * (sizeof(float) * Mp * b.ldE + 256);
-        bytes += 2 * (sizeof(float) * M * d.L + 256);
-        if (b.use_pc) bytes += sizeof(float) * M * b.Gpc * d.K * 2 * d.D + sizeof(int32_t) * M * b.Gpc + 512;
-        bytes += 3 * (sizeof(float) * M * N + 256) + sizeof(uint32_t) * M * N + 256;
-        bytes += sizeof(double) * M * (N + 8) + 256;
+        const size_t Mp = (size_t)(d.M + 1) / 2 * 2, M = (size_t)d.M, N = (size_t)d.N;
+        bytes += 2 * carve_bytes<float>(Mp * b.ldE) + 2 * carve_bytes<float>(M * d.L);
+        if (b.use_pc) bytes += carve_bytes<float>(M * b.Gpc * d.K * 2 * d.D) + carve_bytes<int32_t>(M * b.Gpc);
+        bytes += 3 * carve_bytes<float>(M * N) + 2 * carve_bytes<uint32_t>(M * N) + carve_bytes<double>(M * (N + 8));
+        bytes += carve_bytes<uint32_t>(M * kSeedSlots) + carve_bytes<float>(M * kSeedSlots);
+        bytes += carve_bytes<unsigned long long>(M) + 2 * carve_bytes<int>(M);
         hs.push_back(b);
         cost.push_back((double)N * d.L * d.D * M + (double)M * N * d.L * (2.0 * b.W + 1) * 0.05);
     }
     const int ns = (int)hs.size();
-    bytes += sizeof(BatchSet) * ns + sizeof(BatchItem) * 4 + sizeof(BatchCtl) + sizeof(int) * 2 * ns + 4096;
-    // items: PREP, LBMV, SEARCH, each kind in decreasing set cost
+    // items: front (PREP, LBMV, SEED), mid, refine; each kind in decreasing set cost
     std::vector<int> order(ns);
     for (int k = 0; k < ns; ++k) order[k] = k;
     std::sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    // DTW order: tile classes by total cost, the sets of a class by cost
+    std::vector<double> class_cost(kNumDmClasses, 0.0);
+    for (int k = 0; k < ns; ++k) class_cost[dm_class_of(hs[k].D)] += cost[k];
+    std::vector<int> cls(kNumDmClasses);
+    for (int c = 0; c < kNumDmClasses; ++c) cls[c] = c;
+    std::sort(cls.begin(), cls.end(), [&](int a, int b) { return class_cost[a] > class_cost[b]; });
+    std::vector<int> dtw_order;
+    for (int c : cls) {
+        BatchPlan::DtwClass dc{kDmOfClass[c], (int)dtw_order.size(), 0, 0};
+        for (int k : order)
+            if (dm_class_of(hs[k].D) == c) dtw_order.push_back(k);
+        dc.n = (int)dtw_order.size() - dc.off;
+        if (dc.n > 0) {
+            const cudaError_t e = batch_dtw_grid(dc.dm, &dc.grid);
+            if (e != cudaSuccess) {
+                delete p;
+                return cuda_err(e);
+            }
+            p->classes.push_back(dc);
+        }
+    }
     std::vector<BatchItem> items;
     for (int k : order)
         for (int m = 0; m < hs[k].M; ++m) items.push_back({kItemPrep, k, m, 0});
@@ -528,8 +755,16 @@ int build_plan(const tcdtw_dataset *sets, const std::vector<int> &mk, const tcdt
         for (int ct = 0; ct < hs[k].n_ctiles; ++ct)
             for (int qt = 0; qt < hs[k].n_qtiles; ++qt) items.push_back({kItemMv, k, qt, ct});
     for (int k : order)
-        for (int m = 0; m < hs[k].M; ++m) items.push_back({kItemSearch, k, m, 0});
-    bytes += sizeof(BatchItem) * items.size();
+        for (int m = 0; m < hs[k].M; ++m) items.push_back({kItemSeed, k, m, 0});
+    p->front_end = (int)items.size();
+    for (int k : order)
+        for (int m = 0; m < hs[k].M; ++m) items.push_back({kItemMid, k, m, 0});
+    p->mid_end = (int)items.size();
+    for (int k : order)
+        for (int m = 0; m < hs[k].M; m += kRefinePerItem) items.push_back({kItemRefine, k, m, 0});
+    p->n_items = (int)items.size();
+    bytes += carve_bytes<BatchSet>(ns) + carve_bytes<BatchItem>(items.size()) + carve_bytes<BatchCtl>(1) +
+             carve_bytes<int>((size_t)kCntPerSet * ns) + carve_bytes<int>(ns);
     if (cudaMalloc(&p->arena, bytes) != cudaSuccess) {
         delete p;
         return TCDTW_ERR_NOMEM;
@@ -538,10 +773,11 @@ int build_plan(const tcdtw_dataset *sets, const std::vector<int> &mk, const tcdt
     p->d_sets = carve<BatchSet>(c, ns);
     p->d_items = carve<BatchItem>(c, items.size());
     p->d_ctl = carve<BatchCtl>(c, 1);
-    p->d_counts = carve<int>(c, 2 * ns);
+    p->d_counts = carve<int>(c, (size_t)kCntPerSet * ns);
+    p->d_order = carve<int>(c, ns);
     for (int k = 0; k < ns; ++k) {
         BatchSet &b = hs[k];
-        const int64_t Mp = (b.M + 1) / 2 * 2, M = b.M, N = b.N;
+        const size_t Mp = (size_t)(b.M + 1) / 2 * 2, M = (size_t)b.M, N = (size_t)b.N;
         b.U = carve<float>(c, Mp * b.ldE);
         b.Lo = carve<float>(c, Mp * b.ldE);
         b.dq_lo = carve<float>(c, M * b.L);
@@ -553,38 +789,59 @@ int build_plan(const tcdtw_dataset *sets, const std::vector<int> &mk, const tcdt
         b.lbm = carve<float>(c, M * N);
         b.surv_lb = carve<float>(c, M * N);
         b.surv_dtw = carve<float>(c, M * N);
-        b.seed_dtw = nullptr;
         b.surv = carve<uint32_t>(c, M * N);
+        b.list = carve<uint32_t>(c, M * N);
         b.d64 = carve<double>(c, M * (N + 8));
-        b.prep_done = p->d_counts + 2 * k;
-        b.mv_done = p->d_counts + 2 * k + 1;
+        b.seeds = carve<uint32_t>(c, M * kSeedSlots);
+        b.seed_dtw = carve<float>(c, M * kSeedSlots);
+        b.bsf = carve<unsigned long long>(c, M);
+        b.nseed = carve<int>(c, M);
+        b.ncnt = carve<int>(c, M);
+        b.cnt = p->d_counts + (size_t)kCntPerSet * k;
+    }
+    if ((size_t)(c - (char *)p->arena) > bytes) {  // the carving must stay inside the arena
+        free_plan(p);
+        return TCDTW_ERR_INVALID;
     }
     cudaError_t e = cudaMemcpyAsync(p->d_sets, hs.data(), sizeof(BatchSet) * ns, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(p->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem);
-    int occ = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch, kBatchThreads, kBatchSmem);
+        e = cudaMemcpyAsync(p->d_order, dtw_order.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = kernel_grid((const void *)k_batch_front, kBatchSmem, &p->grid_front);
+    if (e == cudaSuccess) e = kernel_grid((const void *)k_batch_mid, 0, &p->grid_mid);
+    if (e == cudaSuccess) e = kernel_grid((const void *)k_batch_refine, kBatchSmem, &p->grid_refine);
     if (e != cudaSuccess) {
         free_plan(p);
         return cuda_err(e);
     }
-    p->n_items = (int)items.size();
     p->n_sets = ns;
-    p->grid = (occ > 0 ? occ : 1) * num_sms();
-    if (p->grid > p->n_items) p->grid = p->n_items;
+    p->grid_front = std::max(1, std::min(p->grid_front, p->front_end));
+    p->grid_mid = std::max(1, std::min(p->grid_mid, p->mid_end - p->front_end));
+    p->grid_refine = std::max(1, std::min(p->grid_refine, p->n_items - p->mid_end));
     *out = p;
     return TCDTW_OK;
 }
 
+int kernels_per_run(const BatchPlan *p) { return 3 + 2 * (int)p->classes.size(); }
+
 cudaError_t enqueue_plan(BatchPlan *p, cudaStream_t s, long long spin_limit) {
     cudaError_t e = cudaMemsetAsync(p->d_ctl, 0, sizeof(BatchCtl), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_counts, 0, sizeof(int) * 2 * p->n_sets, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_counts, 0, sizeof(int) * kCntPerSet * p->n_sets, s);
     if (e != cudaSuccess) return e;
-    k_batch<<<p->grid, kBatchThreads, kBatchSmem, s>>>(p->d_sets, p->d_items, p->n_items, p->d_ctl, spin_limit);
-    note_launch();
+    k_batch_front<<<p->grid_front, kBatchThreads, kBatchSmem, s>>>(p->d_sets, p->d_items, 0, p->front_end, p->d_ctl,
+                                                                   spin_limit);
+    for (const auto &c : p->classes)
+        if ((e = launch_batch_dtw(c.dm, c.grid, s, p->d_sets, p->d_order + c.off, c.n, 0, p->d_ctl)) != cudaSuccess)
+            return e;
+    k_batch_mid<<<p->grid_mid, kBatchThreads, 0, s>>>(p->d_sets, p->d_items, p->front_end, p->mid_end, p->d_ctl);
+    for (const auto &c : p->classes)
+        if ((e = launch_batch_dtw(c.dm, c.grid, s, p->d_sets, p->d_order + c.off, c.n, 1, p->d_ctl)) != cudaSuccess)
+            return e;
+    k_batch_refine<<<p->grid_refine, kBatchThreads, kBatchSmem, s>>>(p->d_sets, p->d_items, p->mid_end, p->n_items,
+                                                                     p->d_ctl);
+    note_launches(kernels_per_run(p));
     return cudaGetLastError();
 }
 
@@ -612,11 +869,10 @@ int tcdtw_batch_nn(const tcdtw_dataset *sets, int32_t nsets, const tcdtw_opts *o
         if (!d.cand || (d.M > 0 && (!d.q || !d.idx || !d.dist))) return TCDTW_ERR_INVALID;
         if (d.D > TCDTW_MAX_D) return TCDTW_ERR_UNSUPPORTED;
         if (d.M == 0) continue;
-        (megakernel_ok(d, o) ? mk : other).push_back(k);
+        (graph_path_ok(d, o) ? mk : other).push_back(k);
     }
     uint64_t pairs = 0;
     if (!mk.empty()) {
-        // candidates of the megakernel sets: non-finite scan (the queries are checked in PREP)
         std::vector<tcdtw_dataset> key;
         for (int k : mk) key.push_back(sets[k]);
         BatchPlan *plan = nullptr;
@@ -628,6 +884,22 @@ int tcdtw_batch_nn(const tcdtw_dataset *sets, int32_t nsets, const tcdtw_opts *o
         if (!plan) {
             int rc = build_plan(sets, mk, o, s, &plan);
             if (rc) return rc;
+            if (o.check_finite) {
+                // candidates are scanned once, when the batch is first seen (as tcdtw_build
+                // does); the queries are scanned by every run (PREP items)
+                cudaError_t e = cudaMemsetAsync(plan->d_ctl, 0, sizeof(BatchCtl), s);
+                for (size_t i = 0; i < mk.size() && e == cudaSuccess; ++i) {
+                    const tcdtw_dataset &d = sets[mk[i]];
+                    e = launch_check_finite(d.cand, d.N * (int64_t)d.L * d.D, &plan->d_ctl->status, 0, s);
+                }
+                DevStatus st{0, 0};
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                if (e == cudaSuccess) e = cudaMemcpy(&st, &plan->d_ctl->status, sizeof(st), cudaMemcpyDeviceToHost);
+                if (e != cudaSuccess || st.code) {
+                    free_plan(plan);
+                    return e != cudaSuccess ? cuda_err(e) : st.code;
+                }
+            }
             plan->key = key;
             plan->opts = o;
             std::lock_guard<std::mutex> lock(g_plans_mu);
@@ -658,23 +930,16 @@ int tcdtw_batch_nn(const tcdtw_dataset *sets, int32_t nsets, const tcdtw_opts *o
                     if (run != cudaSuccess) e = run;
                     if (e == cudaSuccess) e = cudaGraphInstantiate(&plan->exec, graph, 0);
                     if (graph) cudaGraphDestroy(graph);
-                    note_launches(-1);  // captured, not launched
+                    note_launches(-kernels_per_run(plan));  // captured, not launched
                 }
                 cudaStreamDestroy(cs);
             }
             if (e == cudaSuccess) {
-                note_launches(1);
+                note_launches(kernels_per_run(plan));
                 e = cudaGraphLaunch(plan->exec, s);
             }
         }
         ++plan->launches;
-        if (e == cudaSuccess && o.check_finite) {
-            for (int k : mk) {
-                const tcdtw_dataset &d = sets[k];
-                e = launch_check_finite(d.cand, d.N * (int64_t)d.L * d.D, &plan->d_ctl->status, 0, s);
-                if (e != cudaSuccess) break;
-            }
-        }
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_err(e);
         BatchCtl ctl;
@@ -689,10 +954,11 @@ int tcdtw_batch_nn(const tcdtw_dataset *sets, int32_t nsets, const tcdtw_opts *o
             stats->pruned_pc += ctl.counters[5];
             stats->pruned_ti += ctl.counters[6];
             stats->refined += ctl.counters[7];
+            stats->refined64 += ctl.counters[8];
         }
         for (int k : mk) pairs += (uint64_t)sets[k].M * (uint64_t)sets[k].N;
     }
-    // shapes outside the megakernel's tile family: one index per set
+    // shapes outside the graph path's tile family: one index per set
     for (int k : other) {
         const tcdtw_dataset &d = sets[k];
         tcdtw_index *x = nullptr;
@@ -705,7 +971,7 @@ int tcdtw_batch_nn(const tcdtw_dataset *sets, int32_t nsets, const tcdtw_opts *o
         if (stats) {
             stats->pruned_mv += st.pruned_mv; stats->pruned_pc += st.pruned_pc; stats->pruned_ti += st.pruned_ti;
             stats->dtw_started += st.dtw_started; stats->dtw_abandoned += st.dtw_abandoned;
-            stats->cells += st.cells; stats->refined += st.refined;
+            stats->cells += st.cells; stats->refined += st.refined; stats->refined64 += st.refined64;
         }
         pairs += (uint64_t)d.M * (uint64_t)d.N;
     }
@@ -713,7 +979,7 @@ int tcdtw_batch_nn(const tcdtw_dataset *sets, int32_t nsets, const tcdtw_opts *o
     return TCDTW_OK;
 }
 
-// Self-test of the device-side wait limit: one persistent launch whose only item
+// Self-test of the device-side wait limit: one front launch whose only item
 // waits for a counter that nothing increments; the launch must end by itself with
 // TCDTW_ERR_TIMEOUT after ~spin_limit sleeps, leaving the context usable.
 int tcdtw_batch_selftest_timeout(int64_t spin_limit, void *stream) {
@@ -729,9 +995,10 @@ int tcdtw_batch_selftest_timeout(int64_t spin_limit, void *stream) {
     if (e == cudaSuccess) e = cudaMalloc(&d_ctl, sizeof(BatchCtl));
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_item, &item, sizeof(item), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_ctl, 0, sizeof(BatchCtl), s);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchSmem);
+    int grid = 0;
+    if (e == cudaSuccess) e = kernel_grid((const void *)k_batch_front, kBatchSmem, &grid);
     if (e == cudaSuccess) {
-        k_batch<<<1, kBatchThreads, kBatchSmem, s>>>(d_set, d_item, 1, d_ctl, (long long)spin_limit);
+        k_batch_front<<<1, kBatchThreads, kBatchSmem, s>>>(d_set, d_item, 0, 1, d_ctl, (long long)spin_limit);
         note_launch();
         e = cudaGetLastError();
     }

@@ -1,0 +1,159 @@
+// df.cuh -- double-float (pairs of FP32) DTW for the refine step.
+//
+// The exact nearest neighbour is the FP64 argmin of Eq. (1) (ties: smallest
+// index).  FP64 issues at a small fraction of the FP32 rate on this GPU, so the
+// candidates that FP32 cannot separate from the best one are first recomputed in
+// double-float arithmetic (a value hi + lo of two floats, ~2^-48 relative per
+// operation) with a proven relative error bound; only candidates whose double-float
+// intervals still overlap the best one's go on to a native FP64 recompute.
+//
+// Cell cost.  For each dimension p, TwoSum gives th + tl = a_p - b_p exactly and
+// TwoProd gives ph + pl = th^2 exactly; the large parts ph are summed exactly by
+// TwoSum into sh (the rounding errors e go to the small part), the small parts
+// e + pl + 2 th tl + tl^2 (each at most ~D u of the cost) are summed in FP32 into
+// sl.  Only the FP32 sum of the small parts rounds: the relative error of a cell
+// cost is at most (3D+2)(D+3) u^2 / (1 - (3D+2) u), u = 2^-24.
+//
+// DP.  R(i,j) = cost + min(up, left, diag) with a double-word addition of relative
+// error at most 3u^2 (1 + O(u)) for non-negative operands (df_add; bounded by 4u^2
+// below); the minimum compares (hi, lo) exactly.  By induction over the DP, with the
+// minimum taken over values that are each within the bound of their exact values,
+// the computed R(L-1, L-1) is within a relative (1 + e_cost)(1 + 4u^2)^(2L) - 1 of
+// the exact DTW, 2L-1 being the longest warping path (the host computes the bound,
+// see refine_kappa).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "dtw_core.cuh"  // lane groups and band geometry
+
+namespace tc {
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// |a| >= |b| (or a == 0)
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// (zh, zl) = (xh, xl) + (yh, yl) for non-negative finite double-words (|xl| <= u xh,
+// |yl| <= u yh).  TwoSum gives s + e0 = xh + yh exactly; the low parts are added
+// in two roundings, then FastTwoSum renormalises exactly.  The error is
+// e0 d2 + (xl + yl)((1+d1)(1+d2) - 1) with |e0| <= u s and |xl + yl| <= u (xh + yh):
+// at most 3u^2 (1 + O(u)) of the sum.  (With operands of opposite signs this short
+// form can lose all accuracy; DP values and cell costs are never negative.)
+__device__ __forceinline__ void df_add(float xh, float xl, float yh, float yl, float &zh, float &zl) {
+    float s, e0;
+    two_sum(xh, yh, s, e0);
+    const float e = __fadd_rn(e0, __fadd_rn(xl, yl));
+    fast_two_sum(s, e, zh, zl);
+}
+
+__device__ __forceinline__ bool df_less(float ah, float al, float bh, float bl) {
+    return ah < bh || (ah == bh && al < bl);
+}
+
+// Accumulate the squared difference of one dimension into (sh, sl).
+__device__ __forceinline__ void df_cost_term(float a, float b, float &sh, float &sl) {
+    float th, tl;
+    two_sum(a, -b, th, tl);                                  // th + tl = a - b
+    const float ph = __fmul_rn(th, th);
+    const float pl = __fmaf_rn(th, th, -ph);                 // ph + pl = th^2
+    float q = __fmaf_rn(__fadd_rn(th, th), tl, pl);          // pl + 2 th tl
+    q = __fmaf_rn(tl, tl, q);                                // + tl^2
+    float e;
+    two_sum(sh, ph, sh, e);                                  // exact running sum of ph
+    sl = __fadd_rn(sl, __fadd_rn(e, q));
+}
+
+// Double-float DTW of one pair by one warp (g.G = 32), R rows per lane, D at run
+// time; same band sweep as the FP32 and FP64 passes.  Returns hi + lo rounded to
+// double on the lane that computed R(L-1, L-1), +inf elsewhere.
+template <int R>
+__device__ double band_pass_df(const float *__restrict__ A, const float *__restrict__ B, int L, int D, int W,
+                               const Grp &g) {
+    const float INF = TC_INF;
+    float ch[R], cl[R];
+    float bot_h = INF, bot_l = 0.f, prev_h = INF, prev_l = 0.f;
+    double result = __longlong_as_double(0x7ff0000000000000LL);
+    const int nv = (L + R - 1) / R;
+    const int vlast = (L - 1) / R;
+    int v = g.lig;
+    const int tau_end = v_jhi(nv - 1, R, W, L) + (nv - 1);
+    int tlo = v < nv ? v_jlo(v, R, W) + v : 1 << 30;
+    int thi = v < nv ? v_jhi(v, R, W, L) + v : -1;
+    bool fresh = true;
+    for (int tau = 0; tau <= tau_end; ++tau) {
+        const float in_h = __shfl_sync(g.mask, bot_h, g.src);
+        const float in_l = __shfl_sync(g.mask, bot_l, g.src);
+        if (tau > thi && v < nv) {
+            v += g.G;
+            fresh = true;
+            tlo = v < nv ? v_jlo(v, R, W) + v : 1 << 30;
+            thi = v < nv ? v_jhi(v, R, W, L) + v : -1;
+        }
+        if (tau >= tlo && tau <= thi) {
+            const int j = tau - v;
+            const int i0 = v * R;
+            if (fresh) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) { ch[r] = INF; cl[r] = 0.f; }
+                fresh = false;
+            }
+            float up_h = INF, up_l = 0.f, dg_h = INF, dg_l = 0.f;
+            if (v == 0) {
+                if (j == 0) dg_h = 0.f;
+            } else {
+                if (j <= i0 - 1 + W) { up_h = in_h; up_l = in_l; }
+                if (j >= 1 && j <= i0 + W) { dg_h = prev_h; dg_l = prev_l; }
+            }
+            const unsigned vm = row_mask(j - W - i0, min(j + W - i0, L - 1 - i0), R);
+            const float *bj = B + (size_t)j * D;
+            float sh[R], sl[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) { sh[r] = 0.f; sl[r] = 0.f; }
+            for (int p = 0; p < D; ++p) {
+                const float b = __ldg(bj + p);
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    df_cost_term(__ldg(A + (size_t)min(i0 + r, L - 1) * D + p), b, sh[r], sl[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float lh = ch[r], ll = cl[r];
+                float vh = INF, vl = 0.f;
+                if ((vm >> r) & 1u) {
+                    float mh = up_h, ml = up_l;
+                    if (df_less(lh, ll, mh, ml)) { mh = lh; ml = ll; }
+                    if (df_less(dg_h, dg_l, mh, ml)) { mh = dg_h; ml = dg_l; }
+                    if (mh < INF) {
+                        float c0, c1;
+                        fast_two_sum(sh[r], sl[r], c0, c1);
+                        df_add(c0, c1, mh, ml, vh, vl);
+                    }
+                }
+                dg_h = lh; dg_l = ll;
+                up_h = vh; up_l = vl;
+                ch[r] = vh; cl[r] = vl;
+            }
+            bot_h = ch[R - 1];
+            bot_l = cl[R - 1];
+            if (v == vlast && j == L - 1) {
+                const int rl = (L - 1) - i0;
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (r == rl) result = __dadd_rn((double)ch[r], (double)cl[r]);
+            }
+        }
+        prev_h = in_h;
+        prev_l = in_l;
+    }
+    return result;
+}
+
+}  // namespace tc

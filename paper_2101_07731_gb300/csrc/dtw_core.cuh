@@ -567,9 +567,22 @@ __global__ void __launch_bounds__(128) k_dtw_backward(const float *__restrict__ 
 // t_p = a_p - b_p, s = ((t_0*t_0) + t_1*t_1) + ... without fusion, R = s + min),
 // so the value is bit-identical to a plain sequential FP64 evaluation.  One warp
 // (g.G = 32) per pair, R rows per lane, D at run time.
+//
+// FP64 issues at a small fraction of the FP32 rate on this GPU, so the pass keeps
+// FP64 work to the 3D operations per cell the definition needs: a column's D
+// values are widened once per column (not once per cell), the lane's R rows once
+// per virtual lane into its shared-memory slot ad (R*D doubles; null: widened per
+// cell), the first term is not added to 0, and the three-way minimum compares the
+// bit patterns as integers (the DP values are non-negative doubles or +inf, whose
+// bit patterns order like their values).
+__device__ __forceinline__ double min_nonneg(double a, double b) {
+    const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+    return __longlong_as_double(x < y ? x : y);
+}
+
 template <int R>
 __device__ double band_pass64(const float *__restrict__ A, const float *__restrict__ B, int L, int D, int W,
-                              const Grp &g) {
+                              const Grp &g, double *ad = nullptr) {
     const double INF = __longlong_as_double(0x7ff0000000000000LL);
     double col[R];
     double bottom = INF, prev_in = INF, result = INF;
@@ -595,25 +608,34 @@ __device__ double band_pass64(const float *__restrict__ A, const float *__restri
             if (fresh) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) col[r] = INF;
+                if (ad) {
+                    for (int r = 0; r < R; ++r)
+                        for (int p = 0; p < D; ++p)
+                            ad[r * D + p] = i0 + r < L ? (double)__ldg(A + (size_t)(i0 + r) * D + p) : 0.0;
+                }
                 fresh = false;
             }
             double up = (v == 0) ? INF : ((j <= i0 - 1 + W) ? in : INF);
             double diag = (v == 0) ? ((j == 0) ? 0.0 : INF) : ((j >= 1 && j <= i0 + W) ? prev_in : INF);
             const unsigned vm = row_mask(j - W - i0, min(j + W - i0, L - 1 - i0), R);
             const float *bj = B + (size_t)j * D;
+            // cell costs of the lane's R rows at column j (rows past the end read row
+            // L-1 and are masked below)
+            double s[R];
+            for (int p = 0; p < D; ++p) {
+                const double bp = (double)__ldg(bj + p);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const double ap = ad ? ad[r * D + p] : (double)__ldg(A + (size_t)min(i0 + r, L - 1) * D + p);
+                    const double t = __dsub_rn(ap, bp);
+                    const double t2 = __dmul_rn(t, t);
+                    s[r] = p == 0 ? t2 : __dadd_rn(s[r], t2);
+                }
+            }
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const double left = col[r];
-                double val = INF;
-                if ((vm >> r) & 1u) {
-                    const float *ai = A + (size_t)(i0 + r) * D;
-                    double s = 0.0;
-                    for (int p = 0; p < D; ++p) {
-                        const double t = __dsub_rn((double)__ldg(ai + p), (double)__ldg(bj + p));
-                        s = __dadd_rn(s, __dmul_rn(t, t));
-                    }
-                    val = __dadd_rn(s, fmin(fmin(up, left), diag));
-                }
+                const double val = ((vm >> r) & 1u) ? __dadd_rn(s[r], min_nonneg(min_nonneg(up, left), diag)) : INF;
                 diag = left;
                 up = val;
                 col[r] = val;

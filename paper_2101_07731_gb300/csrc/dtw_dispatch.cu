@@ -7,6 +7,7 @@
 // result is therefore bit-identical to a plain FP64 evaluation.  FP64 issues at a
 // small fraction of the FP32 rate on this GPU, so a pair gets a whole warp (G = 32)
 // and the fewest rows per lane R the band allows, to spread its cells over lanes.
+#include "df.cuh"
 #include "dtw_core.cuh"
 
 namespace tc {
@@ -14,28 +15,65 @@ namespace tc {
 TC_TILES(TC_TILE_DECL)
 
 // Entries e < *count: pair id m*N + n; stores the FP64 DTW in d64[e] and lowers
-// best64[m] (bit pattern of a non-negative double orders like its value).
+// best64[m] (bit pattern of a non-negative double orders like its value).  One warp
+// per block, so that a handful of entries spreads over as many SMs (the FP64 pipe
+// of each SM is the bound); ad_per_lane > 0: the lanes' rows widened in shared memory.
 template <int R>
-__global__ void __launch_bounds__(128) k_dtw_refine(const float *__restrict__ Q, const float *__restrict__ Cand, int L,
-                                                     int D, int W, int64_t N, const uint32_t *__restrict__ pairs,
-                                                     const int32_t *__restrict__ count, double *__restrict__ d64,
-                                                     unsigned long long *__restrict__ best64) {
+__global__ void __launch_bounds__(32) k_dtw_refine(const float *__restrict__ Q, const float *__restrict__ Cand, int L,
+                                                    int D, int W, int64_t N, const uint32_t *__restrict__ pairs,
+                                                    const int32_t *__restrict__ count, double *__restrict__ d64,
+                                                    unsigned long long *__restrict__ best64, int ad_per_lane) {
+    extern __shared__ double ad_smem[];
+    double *ad = ad_per_lane ? ad_smem + (size_t)threadIdx.x * ad_per_lane : nullptr;
     Grp g = make_grp(32);
-    const int warps_per_block = blockDim.x / 32;
-    const int gid = blockIdx.x * warps_per_block + threadIdx.x / 32;
-    const int stride = gridDim.x * warps_per_block;
     const int n_entries = *count;
-    for (int e = gid; e < n_entries; e += stride) {
+    for (int e = blockIdx.x; e < n_entries; e += gridDim.x) {
         const uint32_t pid = pairs[e];
         const int m = (int)(pid / (uint32_t)N);
         const int64_t n = (int64_t)(pid - (uint32_t)m * (uint32_t)N);
-        double r = band_pass64<R>(Q + (size_t)m * L * D, Cand + (size_t)n * L * D, L, D, W, g);
+        double r = band_pass64<R>(Q + (size_t)m * L * D, Cand + (size_t)n * L * D, L, D, W, g, ad);
         r = grp_min(r, g);
         if (g.lig == 0) {
             d64[e] = r;
             atomicMin(best64 + m, (unsigned long long)__double_as_longlong(r));
         }
     }
+}
+
+// Double-float refine: entries e < *count get v[e] = their double-float DTW (rounded
+// to double) and lower bestdf[m] (double bits); one warp per block, as above.
+template <int R>
+__global__ void __launch_bounds__(32) k_dtw_refine_df(const float *__restrict__ Q, const float *__restrict__ Cand,
+                                                       int L, int D, int W, int64_t N,
+                                                       const uint32_t *__restrict__ pairs,
+                                                       const int32_t *__restrict__ count, double *__restrict__ v,
+                                                       unsigned long long *__restrict__ bestdf) {
+    Grp g = make_grp(32);
+    const int n_entries = *count;
+    for (int e = blockIdx.x; e < n_entries; e += gridDim.x) {
+        const uint32_t pid = pairs[e];
+        const int m = (int)(pid / (uint32_t)N);
+        const int64_t n = (int64_t)(pid - (uint32_t)m * (uint32_t)N);
+        double r = band_pass_df<R>(Q + (size_t)m * L * D, Cand + (size_t)n * L * D, L, D, W, g);
+        r = grp_min(r, g);
+        if (g.lig == 0) {
+            v[e] = r;
+            atomicMin(bestdf + m, (unsigned long long)__double_as_longlong(r));
+        }
+    }
+}
+
+cudaError_t dtw_refine_df_launch(int R, int blocks, cudaStream_t s, const DtwRefineArgs &x) {
+    switch (R) {
+#define TC_RD(RV)                                                                                                  \
+    case RV:                                                                                                       \
+        k_dtw_refine_df<RV><<<blocks, 32, 0, s>>>(x.Q, x.C, x.L, x.D, x.W, x.N, x.pairs, x.count, x.d64, x.best64); \
+        note_launch();                                                                                             \
+        return cudaGetLastError();
+        TC_REFINE_RS(TC_RD)
+#undef TC_RD
+    }
+    return cudaErrorInvalidValue;
 }
 
 int refine_rows_for(int W) {
@@ -46,13 +84,27 @@ int refine_rows_for(int W) {
     return 0;
 }
 
+// Rows widened in shared memory when a warp's slots fit in 64 KB.
+int refine_ad_per_lane(int R, int D) { return R * D <= 256 ? R * D : 0; }
+
 cudaError_t dtw_refine_launch(int R, int blocks, cudaStream_t s, const DtwRefineArgs &x) {
+    const int ad = refine_ad_per_lane(R, x.D);
+    const size_t smem = (size_t)32 * ad * sizeof(double);
     switch (R) {
-#define TC_RL(RV)                                                                                                \
-    case RV:                                                                                                     \
-        k_dtw_refine<RV><<<blocks, 128, 0, s>>>(x.Q, x.C, x.L, x.D, x.W, x.N, x.pairs, x.count, x.d64, x.best64); \
-        note_launch();                                                                                           \
-        return cudaGetLastError();
+#define TC_RL(RV)                                                                                                 \
+    case RV: {                                                                                                    \
+        static bool attr = false;                                                                                 \
+        if (!attr) {                                                                                              \
+            cudaError_t e = cudaFuncSetAttribute(k_dtw_refine<RV>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                                 64 * 1024);                                                      \
+            if (e != cudaSuccess) return e;                                                                       \
+            attr = true;                                                                                          \
+        }                                                                                                         \
+        k_dtw_refine<RV><<<blocks, 32, smem, s>>>(x.Q, x.C, x.L, x.D, x.W, x.N, x.pairs, x.count, x.d64, x.best64, \
+                                                  ad);                                                            \
+        note_launch();                                                                                            \
+        return cudaGetLastError();                                                                                \
+    }
         TC_REFINE_RS(TC_RL)
 #undef TC_RL
     }

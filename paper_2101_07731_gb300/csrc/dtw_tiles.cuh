@@ -63,6 +63,8 @@ cudaError_t dtw_pairs_launch(int tile, int G, int blocks, cudaStream_t s, const 
 cudaError_t dtw_nn_launch(int tile, int blocks, cudaStream_t s, const DtwNnArgs &x);
 // FP64 refine with R rows per lane (R in TC_REFINE_RS, one warp per pair)
 cudaError_t dtw_refine_launch(int R, int blocks, cudaStream_t s, const DtwRefineArgs &x);
+// double-float pass: d64 receives the double-float values, best64 the per-query minimum
+cudaError_t dtw_refine_df_launch(int R, int blocks, cudaStream_t s, const DtwRefineArgs &x);
 int refine_rows_for(int W);  // smallest compiled R with 32*(R+1) >= 2W+R, or 0
 cudaError_t dtw_backward_launch(int tile, int G, int blocks, size_t smem, cudaStream_t s, const float *A,
                                 const float *B, const float *ck, int C, const float *gd, int64_t P, int L, int D,

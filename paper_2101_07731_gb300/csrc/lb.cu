@@ -341,22 +341,78 @@ __global__ void k_refine_pick(const uint32_t *__restrict__ pairs, const double *
     }
 }
 
-__global__ void k_finalize(int64_t Mb, const unsigned long long *__restrict__ best64,
+// The double-float values of a query's refine entries cannot order the entries
+// whose values lie within kappa of the best one (or any entry, when no value is
+// finite): those queries take the FP64 recompute.
+__device__ __forceinline__ bool needs_fp64(int amb, unsigned long long bestdf) {
+    return amb >= 2 || !(__longlong_as_double((long long)bestdf) < __longlong_as_double(0x7ff0000000000000LL));
+}
+
+// Per refine entry: count the entries that the double-float values cannot separate
+// from the best one (v <= bestdf * kappa, rounded up), and take the smallest
+// index among the entries at the best value.
+__global__ void k_refine_amb(const uint32_t *__restrict__ pairs, const double *__restrict__ v, const int32_t *count,
+                             int64_t N, const unsigned long long *__restrict__ bestdf, double kappa,
+                             int32_t *__restrict__ amb, unsigned long long *__restrict__ best_idx_df) {
+    const int64_t n_entries = *count;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_entries;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t pid = pairs[e];
+        const int64_t m = pid / (uint64_t)N, n = pid - m * N;
+        const unsigned long long b = bestdf[m];
+        const double x = v[e];
+        if (!(x > __dmul_ru(__longlong_as_double((long long)b), kappa))) atomicAdd(amb + m, 1);
+        if ((unsigned long long)__double_as_longlong(x) == b) atomicMin(best_idx_df + m, (unsigned long long)n);
+    }
+}
+
+// Refine entries of the queries that need FP64 and lie within kappa of the best
+// double-float value join the FP64 list.
+__global__ void k_refine_need64(const uint32_t *__restrict__ pairs, const double *__restrict__ v,
+                                const int32_t *count, int64_t N, const unsigned long long *__restrict__ bestdf,
+                                double kappa, const int32_t *__restrict__ amb, uint32_t *__restrict__ out,
+                                int32_t *__restrict__ out_count, int64_t cap) {
+    const int64_t n_entries = *count;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_entries;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t pid = pairs[e];
+        const int64_t m = pid / (uint64_t)N;
+        const unsigned long long b = bestdf[m];
+        if (!needs_fp64(amb[m], b)) continue;
+        if (!(v[e] > __dmul_ru(__longlong_as_double((long long)b), kappa))) {
+            const int pos = atomicAdd(out_count, 1);
+            if (pos < cap) out[pos] = pid;
+        }
+    }
+}
+
+__global__ void k_finalize(int64_t Mb, const unsigned long long *__restrict__ bestdf,
+                           const unsigned long long *__restrict__ best_idx_df, const int32_t *__restrict__ amb,
+                           const unsigned long long *__restrict__ best64,
                            const unsigned long long *__restrict__ best_idx, int64_t *__restrict__ idx,
                            double *__restrict__ dist) {
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= Mb) return;
-    idx[m] = (int64_t)best_idx[m];
-    dist[m] = __longlong_as_double((long long)best64[m]);
+    if (needs_fp64(amb[m], bestdf[m])) {
+        idx[m] = (int64_t)best_idx[m];
+        dist[m] = __longlong_as_double((long long)best64[m]);
+    } else {
+        idx[m] = (int64_t)best_idx_df[m];
+        dist[m] = __longlong_as_double((long long)bestdf[m]);
+    }
 }
 
 __global__ void k_init_block(int64_t Mb, unsigned long long *bsf, unsigned long long *best64,
-                             unsigned long long *best_idx) {
+                             unsigned long long *best_idx, unsigned long long *bestdf,
+                             unsigned long long *best_idx_df, int32_t *amb) {
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= Mb) return;
     bsf[m] = pack_best(TC_INF, 0xffffffffu);  // +inf: every finite distance is smaller
     if (best64) best64[m] = 0x7ff0000000000000ull;
     if (best_idx) best_idx[m] = ~0ull;
+    if (bestdf) bestdf[m] = 0x7ff0000000000000ull;
+    if (best_idx_df) best_idx_df[m] = ~0ull;
+    if (amb) amb[m] = 0;
 }
 
 __global__ void k_count_add(unsigned long long *acc, const int32_t *v) { *acc += (unsigned long long)*v; }
@@ -389,14 +445,30 @@ cudaError_t launch_refine_pick(const uint32_t *pairs, const double *d64, const i
     k_refine_pick<<<sms, 256, 0, s>>>(pairs, d64, count, N, best64, best_idx); note_launch();
     return cudaGetLastError();
 }
-cudaError_t launch_finalize(int64_t Mb, const unsigned long long *best64, const unsigned long long *best_idx,
+cudaError_t launch_refine_amb(const uint32_t *pairs, const double *v, const int32_t *count, int64_t N,
+                              const unsigned long long *bestdf, double kappa, int32_t *amb,
+                              unsigned long long *best_idx_df, int sms, cudaStream_t s) {
+    k_refine_amb<<<sms, 256, 0, s>>>(pairs, v, count, N, bestdf, kappa, amb, best_idx_df); note_launch();
+    return cudaGetLastError();
+}
+cudaError_t launch_refine_need64(const uint32_t *pairs, const double *v, const int32_t *count, int64_t N,
+                                 const unsigned long long *bestdf, double kappa, const int32_t *amb, uint32_t *out,
+                                 int32_t *out_count, int64_t cap, int sms, cudaStream_t s) {
+    k_refine_need64<<<sms, 256, 0, s>>>(pairs, v, count, N, bestdf, kappa, amb, out, out_count, cap); note_launch();
+    return cudaGetLastError();
+}
+cudaError_t launch_finalize(int64_t Mb, const unsigned long long *bestdf, const unsigned long long *best_idx_df,
+                            const int32_t *amb, const unsigned long long *best64, const unsigned long long *best_idx,
                             int64_t *idx, double *dist, cudaStream_t s) {
-    k_finalize<<<(unsigned)((Mb + 255) / 256), 256, 0, s>>>(Mb, best64, best_idx, idx, dist); note_launch();
+    k_finalize<<<(unsigned)((Mb + 255) / 256), 256, 0, s>>>(Mb, bestdf, best_idx_df, amb, best64, best_idx, idx,
+                                                            dist); note_launch();
     return cudaGetLastError();
 }
 cudaError_t launch_init_block(int64_t Mb, unsigned long long *bsf, unsigned long long *best64,
-                              unsigned long long *best_idx, cudaStream_t s) {
-    k_init_block<<<(unsigned)((Mb + 255) / 256), 256, 0, s>>>(Mb, bsf, best64, best_idx); note_launch();
+                              unsigned long long *best_idx, unsigned long long *bestdf,
+                              unsigned long long *best_idx_df, int32_t *amb, cudaStream_t s) {
+    k_init_block<<<(unsigned)((Mb + 255) / 256), 256, 0, s>>>(Mb, bsf, best64, best_idx, bestdf, best_idx_df, amb);
+    note_launch();
     return cudaGetLastError();
 }
 

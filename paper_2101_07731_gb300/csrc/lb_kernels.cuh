@@ -82,10 +82,20 @@ cudaError_t launch_refine_select(const uint32_t *pairs, const float *dtw, const 
 cudaError_t launch_refine_pick(const uint32_t *pairs, const double *d64, const int32_t *count, int64_t N,
                                const unsigned long long *best64, unsigned long long *best_idx, int sms,
                                cudaStream_t s);
-cudaError_t launch_finalize(int64_t Mb, const unsigned long long *best64, const unsigned long long *best_idx,
+// double-float refine: per-query count of inseparable entries and the index at the
+// best double-float value; entries of queries that need FP64 go to a second list
+cudaError_t launch_refine_amb(const uint32_t *pairs, const double *v, const int32_t *count, int64_t N,
+                              const unsigned long long *bestdf, double kappa, int32_t *amb,
+                              unsigned long long *best_idx_df, int sms, cudaStream_t s);
+cudaError_t launch_refine_need64(const uint32_t *pairs, const double *v, const int32_t *count, int64_t N,
+                                 const unsigned long long *bestdf, double kappa, const int32_t *amb, uint32_t *out,
+                                 int32_t *out_count, int64_t cap, int sms, cudaStream_t s);
+cudaError_t launch_finalize(int64_t Mb, const unsigned long long *bestdf, const unsigned long long *best_idx_df,
+                            const int32_t *amb, const unsigned long long *best64, const unsigned long long *best_idx,
                             int64_t *idx, double *dist, cudaStream_t s);
 cudaError_t launch_init_block(int64_t Mb, unsigned long long *bsf, unsigned long long *best64,
-                              unsigned long long *best_idx, cudaStream_t s);
+                              unsigned long long *best_idx, unsigned long long *bestdf,
+                              unsigned long long *best_idx_df, int32_t *amb, cudaStream_t s);
 cudaError_t launch_count_add(unsigned long long *acc, const int32_t *v, cudaStream_t s);
 cudaError_t launch_iota_pairs(uint32_t *p, int64_t n, cudaStream_t s);
 

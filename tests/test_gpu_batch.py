@@ -1,8 +1,10 @@
-"""GPU parity of the batched persistent search (many uneven sets in one launch)
-against the FP64 oracle, and the device-side wait limit of its work queue.
+"""GPU parity of the batched search (many uneven sets as one sequence of
+persistent launches off device work queues) against the FP64 oracle, and the
+device-side wait limit of its work queue.
 
 Bar: per set, NN indices bit-exact (ties to the smallest index) and distances
-within 1e-5 relative of FP64 (the FP64 refine makes them the FP64 values)."""
+within 1e-9 relative of FP64 (the double-float refine's proven bound is ~1e-10 at
+these sizes; the 1e-5 bar of the method is far looser)."""
 import numpy as np
 import pytest
 import torch
@@ -14,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 tc = pytest.importorskip("paper_2101_07731_gb300")
 DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
-RTOL = 1e-5
+DF_RTOL = 1e-9
 
 
 def _gpu(x):
@@ -33,7 +35,7 @@ def _make(shapes, seed0=0, kind="proto_warp"):
     return host, sets
 
 
-def _check(host, outs, exact_dist=True):
+def _check(host, outs):
     for k, ((Q, Cn, W), (idx, dist)) in enumerate(zip(host, outs)):
         if len(Q) == 0:
             assert idx.numel() == 0
@@ -41,10 +43,7 @@ def _check(host, outs, exact_dist=True):
         ridx, rdist = O.nn_brute(Q, Cn, W)
         gi, gd = idx.cpu().numpy(), dist.cpu().numpy()
         assert np.array_equal(gi, ridx), (k, np.nonzero(gi != ridx))
-        if exact_dist:
-            assert np.array_equal(gd, rdist), k
-        else:
-            np.testing.assert_allclose(gd, rdist, rtol=RTOL, atol=0)
+        np.testing.assert_allclose(gd, rdist, rtol=DF_RTOL, atol=0, err_msg=str(k))
 
 
 # uneven shapes: every D of the single-launch family (1..12), windows from 0 to
@@ -59,6 +58,7 @@ def _check_stats(st, shapes):
     assert st["pairs"] == pairs
     assert st["pruned_mv"] + st["pruned_pc"] + st["pruned_ti"] + st["dtw_started"] == pairs, st
     assert st["refined"] >= sum(M for (M, *_r) in shapes)
+    assert st["refined64"] <= st["refined"]
 
 
 def test_batch_uneven_sets_exact():
@@ -111,9 +111,11 @@ def test_batch_ties_and_duplicates():
     Cn[31] = Cn[3]
     Q = np.stack([Cn[3], Cn[7], Cn[25] + 0.0])
     host = [(Q, Cn, 5)]
-    outs = tc.batch_nn([{"cand": _gpu(Cn), "q": _gpu(Q), "W": 5, "K": 4}])
+    outs, st = tc.batch_nn([{"cand": _gpu(Cn), "q": _gpu(Q), "W": 5, "K": 4}], stats=True)
     _check(host, outs)
     assert outs[0][0].cpu().tolist() == [3, 7, 3]
+    # queries 0 and 2 have three identical best candidates: FP64 settles them
+    assert st["refined64"] >= 6, st
 
 
 def test_batch_workload_generator_sample():
@@ -170,6 +172,19 @@ def test_batch_rejects_non_finite_query():
     with pytest.raises(tc.TcdtwError) as ei:
         tc.batch_nn(sets)
     assert ei.value.code == tc.ERR_NONFINITE
+
+
+def test_batch_rejects_non_finite_candidate_on_first_sight():
+    host, sets = _make(UNEVEN[:2], 750)
+    c = sets[0]["cand"].clone()
+    c[5, 2, 1] = float("inf")
+    sets[0]["cand"] = c
+    with pytest.raises(tc.TcdtwError) as ei:
+        tc.batch_nn(sets)
+    assert ei.value.code == tc.ERR_NONFINITE
+    # once repaired (a new batch description), the search runs
+    sets[0]["cand"] = _gpu(host[0][1])
+    _check(host, tc.batch_nn(sets))
 
 
 def test_batch_rejects_bad_descriptors():
