@@ -3,7 +3,7 @@
 A step is one exact nearest-neighbour search of a batch of 256 queries against
 20,000 resident candidates (L=256, D=5, Sakoe-Chiba W=26, LB_PC K=16; seeded
 prototype-warp data): envelopes, LB_MV, seeds, compaction, gated LB_PC / LB_TI,
-abandoning DTW and FP64 refine -- the whole hot path, all in the library's
+abandoning DTW and the refine -- the whole hot path, all in the library's
 kernels.  The value is whole-job queries/s; the L2 is flushed between timed steps
 (the candidate set, 102 MB, would otherwise stay resident in the 129 MB L2).
 
@@ -69,10 +69,79 @@ def _config(extra=None):
 
 # ----------------------------------------------------------------- CPU oracle legs
 
+def _gen_batched_set(args):
+    """One set of the uneven batch (runs in a spawned worker process)."""
+    k, n_sets, M, seed, scale = args
+    wl = synth.batched_sets(n_sets, M, seed, scale)[k]
+    return k, wl.candidates(), wl.queries()
+
+
+def batched_leg(tc, dev, reps=5):
+    """The uneven batch (32 sets, L ~ U[64,1024], D ~ U{2..12}, N ~ U[1k,20k], 64
+    queries each, W = 10% of L, prototype warp): tcdtw_batch_nn (graph replay) against
+    the same sets searched one after another through prebuilt indexes."""
+    import multiprocessing as mp
+    import torch
+    n_sets, M = 32, 64
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        parts = sorted(pool.map(_gen_batched_set, [(k, n_sets, M, 0, 1.0) for k in range(n_sets)]),
+                       key=lambda r: r[0])
+    gen_s = time.perf_counter() - t0
+    wls = synth.batched_sets(n_sets, M, 0, 1.0)
+    sets = [{"cand": torch.from_numpy(c).to(dev), "q": torch.from_numpy(q).to(dev), "W": w.W, "K": w.K}
+            for (_, c, q), w in zip(parts, wls)]
+    del parts
+    out = [(torch.empty(w.M, dtype=torch.int64, device=dev), torch.empty(w.M, dtype=torch.float64, device=dev))
+           for w in wls]
+    n_q = sum(w.M for w in wls)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    _, st = tc.batch_nn(sets, out=out, stats=True)
+    l0 = tc.kernel_launches()
+    b_ms = timed(lambda: tc.batch_nn(sets, out=out))
+    b_launches = (tc.kernel_launches() - l0) // (reps + 2)
+    got = [o[0].clone() for o in out]
+    idxs = [tc.Index(s["cand"], s["W"], s["K"]) for s in sets]
+
+    def seq():
+        for x, s_, o in zip(idxs, sets, out):
+            x.nn(s_["q"], out=o)
+    s_ms = timed(seq)
+    same = all(torch.equal(g, o[0]) for g, o in zip(got, out))
+    for x in idxs:
+        x.close()
+    assert same, "batched and per-set searches disagree"
+    del sets, out
+    torch.cuda.empty_cache()
+    return {"workload": f"uneven batch: {n_sets} sets x {M} queries, L~U[64,1024], D~U{{2..12}}, N~U[1k,20k], "
+                        "W=10% of L, prototype warp",
+            "queries": n_q, "pairs": st["pairs"], "ms_per_call": b_ms, "queries_per_s": n_q / (b_ms / 1e3),
+            "dtw_cells": st["cells"], "cell_updates_per_s": st["cells"] / (b_ms / 1e3),
+            "pruning_rate": 1.0 - st["dtw_started"] / st["pairs"], "kernels_per_call": int(b_launches),
+            "per_set_calls_ms": s_ms, "speedup_vs_per_set_calls": s_ms / b_ms, "same_indices": same,
+            "generation_s": gen_s, "note": "device-resident inputs, L2 not flushed (5.8 GB of candidates >> L2)"}
+
+
 def cpu_oracle_sample(Q, Cn, W, K, target_s):
     """The paper's pruned search (FP64 oracle, OpenMP over queries) on a bounded
-    sample of queries sized for about target_s seconds; returns (queries/s, cores,
-    sample description, seconds)."""
+    sample sized for about target_s seconds: a prefix of the queries, or whole passes
+    over all of them when one pass is shorter; returns (queries/s, cores, sample
+    description, seconds)."""
     import oracle
     cores = oracle.num_threads()
     n = min(len(Q), max(cores, 16))
@@ -85,7 +154,15 @@ def cpu_oracle_sample(Q, Cn, W, K, target_s):
         oracle.nn_pruned(Q[:n2], Cn, W, K=K)
         t = time.perf_counter() - t0
         n = n2
-    return n / t, cores, f"{n} of {len(Q)} queries x all {len(Cn)} candidates (pruned FP64 search)", t
+    passes = 1
+    if t < target_s * 0.5 and n == len(Q):
+        passes = int(min(64, max(2, round(target_s / max(t, 1e-3)))))
+        t0 = time.perf_counter()
+        for _ in range(passes):
+            oracle.nn_pruned(Q, Cn, W, K=K)
+        t = time.perf_counter() - t0
+    what = f"{n} of {len(Q)} queries" if passes == 1 else f"{passes} passes over all {len(Q)} queries"
+    return n * passes / t, cores, f"{what} x all {len(Cn)} candidates (pruned FP64 search)", t
 
 
 def cpu_brute_sample(Q, Cn, W, n):
@@ -354,6 +431,8 @@ def run_ours(a):
         res["small_workload"] = {"workload": sw.name, "ms_per_call": lat * 1e3, "queries_per_s": sw.M / lat,
                                  "note": "host wall time per tcdtw_nn call (graph replay, synchronous)"}
         small.close()
+        if world == 1:
+            res["batched"] = batched_leg(tc, dev)
 
     if rank == 0 and world == 1 and not a.no_cpu:
         qps, cores, sample, secs = cpu_oracle_sample(Qn, Cn, wl.W, wl.K, a.cpu_seconds)

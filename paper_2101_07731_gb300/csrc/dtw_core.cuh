@@ -253,9 +253,12 @@ __device__ __forceinline__ float band_pass(const float *__restrict__ A, const fl
                 }
                 upk(s, c0, c1);
                 // row 2k
+                // cells outside the band get cost +inf (so the value is +inf), which keeps
+                // the masking off the row-to-row dependency chain
+                c0 = ((vm >> (2 * k)) & 1u) ? c0 : INF;
+                c1 = ((vm >> (2 * k + 1)) & 1u) ? c1 : INF;
                 float left = col[2 * k];
                 float val = __fadd_rn(c0, min3f(up, left, diag));
-                val = ((vm >> (2 * k)) & 1u) ? val : INF;
                 diag = left;
                 up = val;
                 col[2 * k] = val;
@@ -263,7 +266,6 @@ __device__ __forceinline__ float band_pass(const float *__restrict__ A, const fl
                 // row 2k+1
                 float left1 = col[2 * k + 1];
                 float val1 = __fadd_rn(c1, min3f(up, left1, diag));
-                val1 = ((vm >> (2 * k + 1)) & 1u) ? val1 : INF;
                 diag = left1;
                 up = val1;
                 col[2 * k + 1] = val1;
