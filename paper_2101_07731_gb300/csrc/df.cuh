@@ -58,10 +58,10 @@ __device__ __forceinline__ bool df_less(float ah, float al, float bh, float bl) 
     return ah < bh || (ah == bh && al < bl);
 }
 
-// Accumulate the squared difference of one dimension into (sh, sl).
-__device__ __forceinline__ void df_cost_term(float a, float b, float &sh, float &sl) {
-    float th, tl;
-    two_sum(a, -b, th, tl);                                  // th + tl = a - b
+// Accumulate t^2 for an exact difference t = th + tl into (sh, sl): TwoProd gives
+// ph + pl = th^2 exactly, ph joins the exact running sum sh by TwoSum, and the small
+// parts (the TwoSum error, pl, 2 th tl and tl^2) go to sl in FP32.
+__device__ __forceinline__ void df_square_term(float th, float tl, float &sh, float &sl) {
     const float ph = __fmul_rn(th, th);
     const float pl = __fmaf_rn(th, th, -ph);                 // ph + pl = th^2
     float q = __fmaf_rn(__fadd_rn(th, th), tl, pl);          // pl + 2 th tl
@@ -80,7 +80,7 @@ __device__ double band_pass_df(const float *__restrict__ A, const float *__restr
     const float INF = TC_INF;
     float ch[R], cl[R];
     float bot_h = INF, bot_l = 0.f, prev_h = INF, prev_l = 0.f;
-    double result = __longlong_as_double(0x7ff0000000000000LL);
+    float res_h = INF, res_l = 0.f;
     const int nv = (L + R - 1) / R;
     const int vlast = (L - 1) / R;
     int v = g.lig;
@@ -120,8 +120,11 @@ __device__ double band_pass_df(const float *__restrict__ A, const float *__restr
             for (int p = 0; p < D; ++p) {
                 const float b = __ldg(bj + p);
 #pragma unroll
-                for (int r = 0; r < R; ++r)
-                    df_cost_term(__ldg(A + (size_t)min(i0 + r, L - 1) * D + p), b, sh[r], sl[r]);
+                for (int r = 0; r < R; ++r) {
+                    float th, tl;
+                    two_sum(__ldg(A + (size_t)min(i0 + r, L - 1) * D + p), -b, th, tl);  // th + tl = a - b
+                    df_square_term(th, tl, sh[r], sl[r]);
+                }
             }
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -147,13 +150,15 @@ __device__ double band_pass_df(const float *__restrict__ A, const float *__restr
                 const int rl = (L - 1) - i0;
 #pragma unroll
                 for (int r = 0; r < R; ++r)
-                    if (r == rl) result = __dadd_rn((double)ch[r], (double)cl[r]);
+                    if (r == rl) { res_h = ch[r]; res_l = cl[r]; }
             }
         }
         prev_h = in_h;
         prev_l = in_l;
     }
-    return result;
+    // the only FP64 operations: after the loop (FP64 issues at a small fraction of
+    // the FP32 rate; nothing FP64 may sit in the loop body)
+    return res_h < INF ? __dadd_rn((double)res_h, (double)res_l) : __longlong_as_double(0x7ff0000000000000LL);
 }
 
 }  // namespace tc
