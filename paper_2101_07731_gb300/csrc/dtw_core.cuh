@@ -275,12 +275,6 @@ __device__ __forceinline__ float band_pass(const float *__restrict__ A, const fl
             bottom = col[R - 1];
             hooks.after_col(i0, j, bottom);
             ncell += __popc(vm);
-            if (v == vlast && j == L - 1) {
-                const int rl = (L - 1) - i0;
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-                    if (r == rl) result = col[r];
-            }
         }
         prev_in = in;
         if (Hooks::kAbandon) {
@@ -300,6 +294,14 @@ __device__ __forceinline__ float band_pass(const float *__restrict__ A, const fl
         }
     }
     *cells = ncell;
+    // R(L-1, L-1): the last cell of the last virtual lane, still in its lane's column
+    // registers (the lane computes nothing after that virtual lane's last column)
+    if (!*abandoned && live && ((vlast - v0) % g.G) == g.lig && vlast >= v0 && vlast < v1) {
+        const int rl = (L - 1) - vlast * R;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (r == rl) result = col[r];
+    }
     return *abandoned ? INF : result;
 }
 
