@@ -171,6 +171,10 @@ struct tcdtw_index {
     double kappa = 1.0;      // double-float separation factor of the refine (refine_kappa)
     int tile = 0, G = 32, R_ref = 1, sms = 1;
     int blocks_nn = 1, blocks_ref = 1;
+    // the seeds' DTW (a few pairs per query, nothing to abandon against at first):
+    // the tile of the same point width with the fewest rows per lane and the
+    // smallest valid lane group, so that its few pairs spread over more warps
+    int tile_seed = 0, G_seed = 32, blocks_seed = 1;
     // workspaces
     float *U = nullptr, *Lo = nullptr, *dq_lo = nullptr, *dq_hi = nullptr, *boxes = nullptr, *lbm = nullptr;
     int32_t *box_counts = nullptr;
@@ -336,11 +340,12 @@ cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_o
     TC_MARK(3);
     if ((e = launch_seed_topk(x->lbm, Mb_cur, N, N, x->S, x->seeds, s)) != cudaSuccess) return e;
     DtwNnArgs dn;
-    dn.Q = q; dn.C = x->cand; dn.L = L; dn.D = D; dn.W = W; dn.G = x->G; dn.N = N;
+    dn.Q = q; dn.C = x->cand; dn.L = L; dn.D = D; dn.W = W; dn.G = x->G_seed; dn.N = N;
     dn.pairs = x->seeds; dn.lb = nullptr; dn.count = nullptr; dn.n_static = Mb_cur * x->S;
     dn.cursor = x->scalars + kCursorSeed; dn.bsf = x->bsf; dn.rho = x->rho; dn.dtw = x->seed_dtw;
     dn.counters = x->counters;
-    if ((e = dtw_nn_launch(x->tile, x->blocks_nn, s, dn)) != cudaSuccess) return e;
+    if ((e = dtw_nn_launch(x->tile_seed, x->blocks_seed, s, dn)) != cudaSuccess) return e;
+    dn.G = x->G;
     // 4. compaction against the seeded best-so-far
     TC_MARK(4);
     CompactArgs ca;
@@ -519,6 +524,19 @@ int tcdtw_build(const float *cand, int64_t N, int32_t L, int32_t D, int32_t W, i
     if (x->R_ref == 0) { free_index(x); return TCDTW_ERR_UNSUPPORTED; }
     x->blocks_nn = dtw_occupancy(x->tile, 1) * x->sms;
     if (x->blocks_nn < 1) x->blocks_nn = x->sms;
+    x->tile_seed = x->tile;
+    x->G_seed = x->G;
+    for (int t = 0; t < kNumTiles; ++t) {
+        if (kTiles[t].DMAX != kTiles[x->tile].DMAX || kTiles[t].R >= kTiles[x->tile_seed].R) continue;
+        for (int g = 4; g <= 32; g *= 2)
+            if (tile_valid(t, g, W)) {
+                x->tile_seed = t;
+                x->G_seed = g;
+                break;
+            }
+    }
+    x->blocks_seed = dtw_occupancy(x->tile_seed, 1) * x->sms;
+    if (x->blocks_seed < 1) x->blocks_seed = x->sms;
     x->blocks_ref = x->sms * 8;  // one-warp blocks
     rc = alloc_index(x);
     if (rc) { free_index(x); return rc; }
