@@ -42,7 +42,7 @@
 namespace tc {
 
 constexpr int kBatchR = 8;          // rows per lane of the batched DTW
-constexpr int kBatchMaxD = 12;      // dimensions of the single-graph path (D <= 8 exact, 9..12 padded to 12)
+constexpr int kBatchMaxD = 12;      // dimensions of the batched path (one exact-width tile per D)
 constexpr int kBatchThreads = 128;  // 4 warps per CTA
 constexpr int kBatchQB = 32;        // queries per LB_MV tile
 constexpr int kSeedSlots = 8;       // seed slots per query
@@ -371,10 +371,10 @@ __global__ void __launch_bounds__(kBatchThreads, 3) k_batch_dtw(const BatchSet *
     for (int oi = 0; oi < nsets; ++oi) dtw_set<DM>(sets[order[oi]], phase, stage, ctl);
 }
 
-#define TC_BATCH_DMS(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(12)
-constexpr int kNumDmClasses = 9;
-__host__ __device__ constexpr int dm_class_of(int D) { return D <= 8 ? D - 1 : 8; }
-constexpr int kDmOfClass[kNumDmClasses] = {1, 2, 3, 4, 5, 6, 7, 8, 12};
+#define TC_BATCH_DMS(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)
+constexpr int kNumDmClasses = 12;
+__host__ __device__ constexpr int dm_class_of(int D) { return D - 1; }
+constexpr int kDmOfClass[kNumDmClasses] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12};
 
 cudaError_t launch_batch_dtw(int dm, int grid, cudaStream_t s, const BatchSet *sets, const int *order, int nsets,
                              int phase, BatchCtl *ctl) {
@@ -692,7 +692,7 @@ int build_plan(const tcdtw_dataset *sets, const std::vector<int> &mk, const tcdt
         b.cand = d.cand; b.q = d.q; b.idx = d.idx; b.dist = d.dist;
         b.N = d.N; b.L = d.L; b.D = d.D; b.W = d.W > d.L - 1 ? d.L - 1 : d.W; b.K = d.K; b.M = (int)d.M;
         b.G = batch_G(b.W);
-        b.dcase = d.D <= 8 ? d.D : 12;
+        b.dcase = d.D;
         b.Rref = refine_rows_for(b.W);
         b.S = (int)(o.seed_s < d.N ? o.seed_s : d.N);
         b.check_finite = o.check_finite != 0;

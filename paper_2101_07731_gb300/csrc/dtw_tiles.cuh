@@ -7,7 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-// X(id, R, DM), split over three translation units compiled in parallel
+// X(id, R, DM), split over four translation units compiled in parallel
 #define TC_TILES_A(X)                                                                                      \
     X(0, 4, 1) X(1, 8, 1) X(2, 16, 1) X(3, 4, 2) X(4, 8, 2) X(5, 16, 2) X(6, 4, 3) X(7, 8, 3) X(8, 16, 3) \
     X(9, 4, 4) X(10, 8, 4) X(11, 16, 4)
@@ -16,7 +16,8 @@
     X(21, 4, 8) X(22, 8, 8) X(23, 16, 8)
 #define TC_TILES_C(X) \
     X(24, 4, 12) X(25, 8, 12) X(26, 4, 16) X(27, 8, 16) X(28, 2, 32) X(29, 4, 32) X(30, 6, 32) X(31, 2, 64)
-#define TC_TILES(X) TC_TILES_A(X) TC_TILES_B(X) TC_TILES_C(X)
+#define TC_TILES_D(X) X(32, 4, 9) X(33, 8, 9) X(34, 4, 10) X(35, 8, 10) X(36, 4, 11) X(37, 8, 11)
+#define TC_TILES(X) TC_TILES_A(X) TC_TILES_B(X) TC_TILES_C(X) TC_TILES_D(X)
 
 // FP64 refine: rows per lane (one warp per pair, G = 32)
 #define TC_REFINE_RS(X) X(1) X(2) X(4) X(6) X(8) X(16)
