@@ -32,6 +32,7 @@ CASES = [
     (37, 70, 3, 7), (64, 128, 3, 13), (33, 256, 5, 26), (19, 100, 8, 10), (8, 64, 12, 6),
     (5, 90, 16, 9), (4, 60, 32, 6), (3, 50, 64, 4), (17, 40, 1, 0), (9, 31, 2, 200),
     (6, 1, 3, 0), (7, 2, 4, 5), (11, 129, 6, 47), (5, 300, 4, 120),
+    (9, 77, 9, 8), (10, 64, 10, 30), (7, 45, 11, 4),   # exact-width tiles of D = 9..11
 ]
 
 
