@@ -68,6 +68,12 @@ typedef struct tcdtw_index tcdtw_index; /* opaque; created by tcdtw_build */
  *          no abandoning; the answer is the same (0).
  *  use_graph  1 = tcdtw_nn replays a captured CUDA graph of its kernel sequence when
  *          called again with the same (q, M, idx, dist) (1).
+ *  select  1 = TC-DTW's data-adaptive choice (Section 6, "TC-DTW"; parameter ranges of
+ *          Section 7.1): the first tcdtw_nn call on an index times, on up to 32 of
+ *          its queries, LB_MV alone, LB_TI with e_ti in {0.05, 0.1, 0.2} and LB_PC with
+ *          e_pc in {0.1, 0.5} and Lq in {2, 3} (within use_ti / use_pc), and keeps the
+ *          fastest for the index (1).  The answers do not depend on the choice;
+ *          tcdtw_index_opts reports it.
  */
 typedef struct {
     int32_t P;
@@ -83,6 +89,7 @@ typedef struct {
     int32_t check_finite;
     int32_t no_prune;
     int32_t use_graph;
+    int32_t select;
 } tcdtw_opts;
 
 /* Counters of one tcdtw_nn call, summed over its queries. */
@@ -140,6 +147,11 @@ int tcdtw_build(const float *cand, int64_t N, int32_t L, int32_t D, int32_t W, i
  */
 int tcdtw_nn(tcdtw_index *index, const float *q, int64_t M, int64_t *idx, double *dist,
              tcdtw_stats *stats, void *stream);
+
+/* The options the index searches with (host output): those given to tcdtw_build,
+ * with the bound choice of the first tcdtw_nn call when opts->select was set.
+ * Errors: INVALID. */
+int tcdtw_index_opts(tcdtw_index *index, tcdtw_opts *out);
 
 /* Release an index and its workspaces (NULL is accepted). */
 void tcdtw_free(tcdtw_index *index);
@@ -281,6 +293,7 @@ int tcdtw_compact(const float *lb, int64_t M, int64_t N, const float *thresh, in
  * batches): the second call with the same batch captures the sequence into a CUDA
  * graph (opts->use_graph), later calls replay it.  With opts->check_finite the
  * candidates are scanned when a batch is first seen and the queries on every call.
+ * opts->select is not used here: every set runs with the bounds opts enables.
  */
 typedef struct {
     const float *cand; /* device [N][L][D], row-major, N >= 1 */

@@ -52,7 +52,8 @@ class Opts(C.Structure):
     _fields_ = [("P", C.c_int32), ("Lq", C.c_int32), ("w", C.c_int32), ("e_pc", C.c_float),
                 ("e_ti", C.c_float), ("use_pc", C.c_int32), ("use_ti", C.c_int32),
                 ("seed_s", C.c_int32), ("qblock", C.c_int32), ("tile", C.c_int32),
-                ("check_finite", C.c_int32), ("no_prune", C.c_int32), ("use_graph", C.c_int32)]
+                ("check_finite", C.c_int32), ("no_prune", C.c_int32), ("use_graph", C.c_int32),
+                ("select", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -95,6 +96,7 @@ _SIGS = {
     "tcdtw_stage_times": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(_I64)]),
     "tcdtw_kernel_launches": (C.c_uint64, []),
     "tcdtw_index_info": (C.c_int, [_P, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32)]),
+    "tcdtw_index_opts": (C.c_int, [_P, C.POINTER(Opts)]),
     "tcdtw_tile_info": (C.c_int, [_I32, C.POINTER(_I32), C.POINTER(_I32), C.POINTER(_I32)]),
 }
 
@@ -259,6 +261,13 @@ class Index:
         r, dm = _I32(), _I32()
         _call("tcdtw_tile_info", t.value, None, C.byref(r), C.byref(dm))
         return {"tile": t.value, "R": r.value, "DM": dm.value, "G": g.value, "qblock": qb.value}
+
+    def options(self):
+        """The options the index searches with (after TC-DTW's bound selection, made by
+        the first nn() call when select=1)."""
+        o = Opts()
+        _call("tcdtw_index_opts", self._h, C.byref(o))
+        return {n: getattr(o, n) for n, _ in o._fields_}
 
     STAGES = ("check", "prep", "lb_mv", "seed", "compact", "cascade", "dtw", "refine")
 

@@ -16,6 +16,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -175,6 +176,7 @@ struct tcdtw_index {
     // the tile of the same point width with the fewest rows per lane and the
     // smallest valid lane group, so that its few pairs spread over more warps
     int tile_seed = 0, G_seed = 32, blocks_seed = 1;
+    bool selected = false;   // TC-DTW bound choice made (opts.select)
     // workspaces
     float *U = nullptr, *Lo = nullptr, *dq_lo = nullptr, *dq_hi = nullptr, *boxes = nullptr, *lbm = nullptr;
     int32_t *box_counts = nullptr;
@@ -410,6 +412,64 @@ cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_o
     return cudaSuccess;
 }
 
+// TC-DTW's data-adaptive choice (Section 6; parameter ranges of Section 7.1): on the
+// first call, time the pipeline on up to 32 of its queries with LB_MV alone, LB_TI
+// (e_ti in {0.05, 0.1, 0.2}) and LB_PC (e_pc in {0.1, 0.5}, Lq in {2, 3}), each within
+// what the caller enabled, and keep the fastest.  Every choice gives the same answer
+// (the bounds only decide which DTWs are skipped); the paper picks between its two
+// bounds on a few sample series the same way, by trying them.
+cudaError_t select_cascade(tcdtw_index *x, const float *q, int64_t M, cudaStream_t s) {
+    x->selected = true;
+    tcdtw_opts &o = x->opts;
+    if (!o.select || o.no_prune || (!o.use_pc && !o.use_ti)) return cudaSuccess;
+    const int n = (int)std::min<int64_t>(M, std::min<int64_t>(x->Mb, 32));
+    struct Cfg { int pc, ti, Lq; float e_pc, e_ti; };
+    std::vector<Cfg> cfgs = {{0, 0, o.Lq, o.e_pc, o.e_ti}};
+    if (o.use_ti)
+        for (float e : {0.05f, 0.1f, 0.2f}) cfgs.push_back({0, 1, o.Lq, o.e_pc, e});
+    if (o.use_pc)
+        for (int lq : {2, 3})
+            if (pc_key_fits(lq, x->D))
+                for (float e : {0.1f, 0.5f}) cfgs.push_back({1, 0, lq, e, o.e_ti});
+    int64_t *sidx = nullptr;
+    double *sdist = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&sidx, sizeof(int64_t) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&sdist, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const bool prof = x->profile;
+    x->profile = false;
+    float best_ms = INFINITY;
+    Cfg best = cfgs[0];
+    for (size_t c = 0; c < cfgs.size() && e == cudaSuccess; ++c) {
+        o.use_pc = cfgs[c].pc;
+        o.use_ti = cfgs[c].ti;
+        o.Lq = cfgs[c].Lq;
+        o.e_pc = cfgs[c].e_pc;
+        o.e_ti = cfgs[c].e_ti;
+        float ms = 0.f;
+        e = run_block(x, q, n, sidx, sdist, s);  // warm (tables, caches)
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) e = run_block(x, q, n, sidx, sdist, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best_ms) { best_ms = ms; best = cfgs[c]; }
+    }
+    x->profile = prof;
+    o.use_pc = best.pc;
+    o.use_ti = best.ti;
+    o.Lq = best.Lq;
+    o.e_pc = best.e_pc;
+    o.e_ti = best.e_ti;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(sidx);
+    cudaFree(sdist);
+    return e;
+}
+
 // All query blocks of one call.  With use_graph, a key (q, M, idx, dist) seen once
 // before is captured into a CUDA graph (on an internal stream) and replayed on s;
 // the first call of a key runs eagerly so that any one-time setup (function
@@ -565,6 +625,7 @@ int tcdtw_nn(tcdtw_index *x, const float *q, int64_t M, int64_t *idx, double *di
     if (!q || !idx || !dist) return TCDTW_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t E = (int64_t)x->L * x->D;
+    if (!x->selected) TC_TRY(select_cascade(x, q, M, s));
     const bool sync = stats != nullptr || x->opts.check_finite || x->profile;
     x->marks_used = 0;
     if (sync) {
@@ -602,6 +663,12 @@ int tcdtw_nn(tcdtw_index *x, const float *q, int64_t M, int64_t *idx, double *di
         stats->refined = c[kRefined];
         stats->refined64 = c[kRefined64];
     }
+    return TCDTW_OK;
+}
+
+int tcdtw_index_opts(tcdtw_index *x, tcdtw_opts *out) {
+    if (!x || !out) return TCDTW_ERR_INVALID;
+    *out = x->opts;
     return TCDTW_OK;
 }
 

@@ -152,6 +152,7 @@ void tcdtw_default_opts(tcdtw_opts *o) {
     o->check_finite = 1;
     o->no_prune = 0;
     o->use_graph = 1;
+    o->select = 1;
 }
 
 const char *tcdtw_strerror(int code) {

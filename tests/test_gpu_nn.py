@@ -173,6 +173,30 @@ def test_nn_edge_shapes(M, N, L, D, W):
     _check_nn(Q, Cn, W, 4)
 
 
+def test_nn_tc_dtw_selection_keeps_answers():
+    # TC-DTW's data-adaptive bound choice changes which DTWs run, never the answer
+    Q, Cn = _set("proto_warp", 40, 2000, 80, 4, 31, n_proto=6)
+    fixed = tc.Index(_gpu(Cn), 8, 8, select=0)
+    i0, d0 = fixed.nn(_gpu(Q))
+    assert fixed.options()["use_pc"] == 1 and fixed.options()["use_ti"] == 1
+    fixed.close()
+    chosen = tc.Index(_gpu(Cn), 8, 8)
+    i1, d1 = chosen.nn(_gpu(Q))
+    opts = chosen.options()
+    assert not (opts["use_pc"] and opts["use_ti"])      # one of the two bounds, or LB_MV alone
+    if opts["use_ti"]:
+        assert opts["e_ti"] in (pytest.approx(0.05), pytest.approx(0.1), pytest.approx(0.2))
+    if opts["use_pc"]:
+        assert opts["Lq"] in (2, 3) and opts["e_pc"] in (pytest.approx(0.1), pytest.approx(0.5))
+    i2, d2 = chosen.nn(_gpu(Q))                            # the choice is kept
+    assert chosen.options() == opts
+    chosen.close()
+    assert torch.equal(i0, i1) and torch.equal(i1, i2)
+    assert torch.equal(d0, d1) and torch.equal(d1, d2)
+    ridx, rdist = O.nn_brute(Q, Cn, 8)
+    assert np.array_equal(i1.cpu().numpy(), ridx)
+
+
 def test_nn_duplicates_tie_to_smallest_index():
     _, Cn = _set("random_walk", 1, 64, 40, 3, 24)
     Cn = np.concatenate([Cn, Cn[[10, 5, 10]]])          # copies at 64, 65, 66
