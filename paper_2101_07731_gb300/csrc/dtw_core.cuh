@@ -154,7 +154,10 @@ __device__ __forceinline__ float band_pass(const float *__restrict__ A, const fl
     static_assert(R % 2 == 0, "rows are processed in pairs");
     constexpr int RP = R / 2;
     const float INF = TC_INF;
-    f2 a2[RP][DM];     // rows (2k, 2k+1) of the virtual lane, dimension p
+    constexpr bool kDimPack = DM >= 16;
+    constexpr int DH = (DM + 1) / 2;
+    f2 a2[kDimPack ? 1 : RP][kDimPack ? 1 : DM];     // rows (2k, 2k+1) of the virtual lane, dimension p
+    f2 ad[kDimPack ? R : 1][kDimPack ? DH : 1];      // wide points: row r, dimensions (2h, 2h+1)
     float col[R];      // R(i0 + r, j-1) -> R(i0 + r, j)
     float b[DM];
     float bottom = INF, prev_in = INF, result = INF, mn_prev = INF;
@@ -182,7 +185,7 @@ __device__ __forceinline__ float band_pass(const float *__restrict__ A, const fl
             const int j = tau - v;
             const int i0 = v * R;
             if (!loaded) {
-                if (staged) {
+                if (staged && !kDimPack) {
                     // rows were copied to this lane's shared slot one virtual lane ago
                     cp_async_wait_all();
 #pragma unroll
@@ -195,7 +198,7 @@ __device__ __forceinline__ float band_pass(const float *__restrict__ A, const fl
                             a2[k][p] = pk(lo, hi);
                         }
                     }
-                } else {
+                } else if (!kDimPack) {
 #pragma unroll
                     for (int k = 0; k < RP; ++k) {
                         const int i = i0 + 2 * k;
@@ -207,6 +210,18 @@ __device__ __forceinline__ float band_pass(const float *__restrict__ A, const fl
                         }
                     }
                 }
+                if (kDimPack) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const int i = i0 + r;
+#pragma unroll
+                        for (int h = 0; h < DH; ++h) {
+                            const float x0 = (i < L && 2 * h < D) ? __ldg(A + (size_t)i * D + 2 * h) : 0.f;
+                            const float x1 = (i < L && 2 * h + 1 < D) ? __ldg(A + (size_t)i * D + 2 * h + 1) : 0.f;
+                            ad[kDimPack ? r : 0][kDimPack ? h : 0] = pk(x0, x1);
+                        }
+                    }
+                }
 #pragma unroll
                 for (int r = 0; r < R; ++r) col[r] = INF;
                 loaded = true;
@@ -214,7 +229,7 @@ __device__ __forceinline__ float band_pass(const float *__restrict__ A, const fl
                 // reads of the slot above have completed: opaque data dependency)
                 const bool had = staged;
                 staged = false;
-                if (stage && v + g.G < v1) {
+                if (!kDimPack && stage && v + g.G < v1) {
                     float last_lo, last_hi;
                     upk(a2[RP - 1][DM - 1], last_lo, last_hi);
                     const unsigned z = had ? opaque_zero(last_hi) : 0u;
@@ -222,8 +237,26 @@ __device__ __forceinline__ float band_pass(const float *__restrict__ A, const fl
                     staged = true;
                 }
             }
+            f2 cs[kDimPack ? R : 1];
+            if (kDimPack) {
+                // the column two dimensions at a time, each pair used by all R rows
 #pragma unroll
-            for (int p = 0; p < DM; ++p) b[p] = (p < D) ? __ldg(B + (size_t)j * D + p) : 0.f;
+                for (int r = 0; r < R; ++r) cs[kDimPack ? r : 0] = 0ull;
+#pragma unroll
+                for (int h = 0; h < DH; ++h) {
+                    const float x0 = (2 * h < D) ? __ldg(B + (size_t)j * D + 2 * h) : 0.f;
+                    const float x1 = (2 * h + 1 < D) ? __ldg(B + (size_t)j * D + 2 * h + 1) : 0.f;
+                    const f2 bh = pk(x0, x1);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const f2 t = sub2(ad[kDimPack ? r : 0][kDimPack ? h : 0], bh);
+                        cs[kDimPack ? r : 0] = fma2(t, t, cs[kDimPack ? r : 0]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int p = 0; p < DM; ++p) b[p] = (p < D) ? __ldg(B + (size_t)j * D + p) : 0.f;
+            }
             float up, diag;
             if (v == v0) {
                 if (v0 == 0) {
@@ -239,19 +272,29 @@ __device__ __forceinline__ float band_pass(const float *__restrict__ A, const fl
             }
             // rows of this column inside the band: r in [j-W-i0, j+W-i0] and i < L
             const unsigned vm = row_mask(j - W - i0, min(j + W - i0, L - 1 - i0), R);
-            f2 bb[DM];
+            f2 bb[kDimPack ? 1 : DM];
+            if (!kDimPack) {
 #pragma unroll
-            for (int p = 0; p < DM; ++p) bb[p] = pk(b[p], b[p]);
+                for (int p = 0; p < DM; ++p) bb[kDimPack ? 0 : p] = pk(b[p], b[p]);
+            }
 #pragma unroll
             for (int k = 0; k < RP; ++k) {
                 float c0, c1;
-                f2 s = 0ull;
+                if (kDimPack) {
+                    float x, y;
+                    upk(cs[kDimPack ? 2 * k : 0], x, y);
+                    c0 = __fadd_rn(x, y);
+                    upk(cs[kDimPack ? 2 * k + 1 : 0], x, y);
+                    c1 = __fadd_rn(x, y);
+                } else {
+                    f2 s = 0ull;
 #pragma unroll
-                for (int p = 0; p < DM; ++p) {
-                    const f2 t = sub2(a2[k][p], bb[p]);
-                    s = fma2(t, t, s);
+                    for (int p = 0; p < DM; ++p) {
+                        const f2 t = sub2(a2[k][p], bb[p]);
+                        s = fma2(t, t, s);
+                    }
+                    upk(s, c0, c1);
                 }
-                upk(s, c0, c1);
                 // row 2k
                 // cells outside the band get cost +inf (so the value is +inf), which keeps
                 // the masking off the row-to-row dependency chain
