@@ -313,6 +313,11 @@ typedef struct {
 int tcdtw_batch_nn(const tcdtw_dataset *sets, int32_t nsets, const tcdtw_opts *opts,
                    tcdtw_stats *stats, void *stream);
 
+/* Release the batch sequences tcdtw_batch_nn keeps (CUDA graphs and workspaces of
+ * up to 4 distinct batches) after waiting for the device; the next call builds its
+ * sequence again.  Errors: CUDA. */
+int tcdtw_batch_release(void);
+
 /* Failure-detection self-test of the batched launch (no counterpart in the paper):
  * one persistent launch whose only work item waits for a device counter that
  * nothing increments, with a limit of spin_limit sleeps of ~256 ns.  The wait runs

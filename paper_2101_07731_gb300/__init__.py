@@ -20,7 +20,7 @@ import os
 
 import torch
 
-__all__ = ["Index", "dtw", "dtw_pairs", "dtw_pairs_backward", "batch_nn", "batch_selftest_timeout", "envelope", "query_dq",
+__all__ = ["Index", "dtw", "dtw_pairs", "dtw_pairs_backward", "batch_nn", "batch_release", "batch_selftest_timeout", "envelope", "query_dq",
            "pc_boxes", "lower_bounds", "compact", "Opts", "Stats", "TcdtwError", "lib_path",
            "LB_MV", "LB_PC", "LB_TI", "default_opts"]
 
@@ -91,6 +91,7 @@ _SIGS = {
     "tcdtw_lb_mv_noalloc": (C.c_int, [_P, _I64, _P, _I64, _I32, _I32, _I32, _P, _P]),
     "tcdtw_batch_nn": (C.c_int, [C.POINTER(Dataset), _I32, C.POINTER(Opts), C.POINTER(Stats), _P]),
     "tcdtw_batch_selftest_timeout": (C.c_int, [_I64, _P]),
+    "tcdtw_batch_release": (C.c_int, []),
     "tcdtw_tile_count": (C.c_int, []),
     "tcdtw_set_profiling": (C.c_int, [_P, _I32]),
     "tcdtw_stage_times": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(_I64)]),
@@ -334,6 +335,11 @@ def batch_nn(sets, stats: bool = False, out=None, **opts):
     st = Stats()
     _call("tcdtw_batch_nn", arr, len(descs), C.byref(o), C.byref(st) if stats else None, _stream())
     return (outs, st.as_dict()) if stats else outs
+
+
+def batch_release():
+    """Free the cached batch sequences (graphs and workspaces)."""
+    _call("tcdtw_batch_release")
 
 
 def batch_selftest_timeout(spin_limit: int = 200000) -> int:

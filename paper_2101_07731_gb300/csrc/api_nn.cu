@@ -17,6 +17,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -82,11 +83,15 @@ struct TuneVal {
     int tile, G;
 };
 static std::vector<std::pair<TuneKey, TuneVal>> g_tune_cache;
+static std::mutex g_tune_mu;  // indexes may be built from several host threads
 
 bool autotune_nn_tile(const float *cand, int64_t N, int L, int D, int W, cudaStream_t s, int *tile, int *G) {
     const TuneKey key{L, D, W};
-    for (auto &kv : g_tune_cache)
-        if (kv.first == key) { *tile = kv.second.tile; *G = kv.second.G; return true; }
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        for (auto &kv : g_tune_cache)
+            if (kv.first == key) { *tile = kv.second.tile; *G = kv.second.G; return true; }
+    }
     const int dm = dmax_for(D);
     if (dm < 0) return false;
     // enough pairs to fill every SM even with 4-lane groups (8 pairs per warp), but
@@ -142,7 +147,10 @@ bool autotune_nn_tile(const float *cand, int64_t N, int L, int D, int W, cudaStr
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFree(pairs); cudaFree(bsf); cudaFree(dtw); cudaFree(cursor);
-    if (found) g_tune_cache.push_back({key, TuneVal{*tile, *G}});
+    if (found) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache.push_back({key, TuneVal{*tile, *G}});
+    }
     return found;
 }
 

@@ -979,6 +979,16 @@ int tcdtw_batch_nn(const tcdtw_dataset *sets, int32_t nsets, const tcdtw_opts *o
     return TCDTW_OK;
 }
 
+// Free every cached batch sequence (graph and workspace); the next tcdtw_batch_nn
+// call builds its sequence again.
+int tcdtw_batch_release(void) {
+    std::lock_guard<std::mutex> lock(g_plans_mu);
+    const cudaError_t e = cudaDeviceSynchronize();  // a cached graph may still be running
+    for (BatchPlan *p : g_plans) free_plan(p);
+    g_plans.clear();
+    return e == cudaSuccess ? TCDTW_OK : cuda_err(e);
+}
+
 // Self-test of the device-side wait limit: one front launch whose only item
 // waits for a counter that nothing increments; the launch must end by itself with
 // TCDTW_ERR_TIMEOUT after ~spin_limit sleeps, leaving the context usable.

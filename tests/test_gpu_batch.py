@@ -149,6 +149,17 @@ def test_batch_graph_replay_follows_buffer_contents():
     assert tc.kernel_launches() > before
 
 
+def test_batch_release_frees_cached_sequences():
+    host, sets = _make(UNEVEN[:3], 650)
+    free0 = torch.cuda.mem_get_info()[0]
+    _check(host, tc.batch_nn(sets))
+    tc.batch_release()
+    # the arena is gone, and the same batch runs again from scratch
+    assert torch.cuda.mem_get_info()[0] >= free0 - (64 << 20)
+    _check(host, tc.batch_nn(sets))
+    tc.batch_release()
+
+
 def test_batch_wait_limit_returns_timeout_and_context_survives():
     # the only work item waits on a counter nothing increments: the wait runs out
     t0 = torch.cuda.Event(enable_timing=True)
