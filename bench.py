@@ -47,6 +47,7 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extra", action="store_true", help="skip the unpruned and end-to-end legs")
+    ap.add_argument("--no-few", action="store_true", help="skip the few-queries leg")
     return ap.parse_args()
 
 
@@ -84,6 +85,44 @@ def _config(extra=None):
 
 
 # ----------------------------------------------------------------- CPU oracle legs
+
+def few_queries_leg(tc, cand, q, wl, flush, stream, Ms=(1, 2, 4, 8, 16), reps=10):
+    """Searches of a few queries against the full candidate set: the LB_MV stream is
+    then one pass over the candidates (HBM-bound; TMA-fed, stream-K split), the rest of
+    the search is latency-bound.  Stage times come from CUDA events inside the replayed
+    graph (no host gaps); L2 is flushed before every call."""
+    import torch
+    hbm = _peaks().get("hbm_gbs")
+    cand_bytes = wl.N * wl.spec.L * wl.spec.D * 4
+    out = {"M": list(Ms), "lb_mv_us": [], "lb_mv_hbm_frac": [], "search_us": []}
+    for M in Ms:
+        x = tc.Index(cand, wl.W, wl.K)
+        qm = q[:M].contiguous()
+        o = (torch.empty(M, dtype=torch.int64, device=q.device), torch.empty(M, dtype=torch.float64, device=q.device))
+        for _ in range(3):
+            x.nn(qm, out=o)
+        torch.cuda.synchronize()
+        x.set_profiling(True)
+        tot = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x.nn(qm, out=o)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        st, _ = x.stage_times()
+        x.set_profiling(False)
+        x.close()
+        t_mv = st["lb_mv"] / reps / 1e3
+        out["lb_mv_us"].append(t_mv * 1e6)
+        out["lb_mv_hbm_frac"].append(cand_bytes / t_mv / 1e9 / hbm if hbm else None)
+        out["search_us"].append(tot / reps * 1e3)
+    out["note"] = ("lb_mv_hbm_frac: candidate bytes / LB_MV stage time / measured HBM copy bandwidth; "
+                   "search_us: whole tcdtw_nn call, profiling events on")
+    return out
+
 
 def _gen_batched_set(args):
     """One set of the uneven batch (runs in a spawned worker process)."""
@@ -486,6 +525,8 @@ def run_ours(a):
         tot = job_time_ms(tot, dist, dev)
         res["e2e"] = {"value": job_value(world, wl.M, a.steps, tot), "unit": "queries/s",
                       "h2d_bytes_per_step": int(qh.numel() * 4), "d2h_bytes_per_step": int(wl.M * 16)}
+    if not a.no_few:
+        res["few_queries"] = few_queries_leg(tc, cand, q, wl, flush, stream)
     index.close()
 
     if not a.no_extra:

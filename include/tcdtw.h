@@ -326,6 +326,14 @@ int tcdtw_batch_release(void);
  * CUDA on a runtime error.  Synchronous on `stream`. */
 int tcdtw_batch_selftest_timeout(int64_t spin_limit, void *stream);
 
+/* Failure-detection self-test of the TMA-fed LB_MV stream (no counterpart in the
+ * paper): one CTA whose producer warp issues no copy, so the consumers' wait for the
+ * first chunk runs out after wait_us microseconds; the launch records TIMEOUT in its
+ * status word and returns, and the context stays usable.  Returns TIMEOUT on success
+ * of the self-test, INVALID for wait_us outside [1, 10^7], NOMEM, CUDA on a runtime
+ * error.  Synchronous on `stream`. */
+int tcdtw_lb_mv_selftest_timeout(int64_t wait_us, void *stream);
+
 /* Number of compiled DTW band tiles, and the shape of tile t: G lanes per pair,
  * R rows per lane (host outputs).  Returns INVALID for an unknown t. */
 int tcdtw_tile_count(void);

@@ -20,7 +20,7 @@ import os
 
 import torch
 
-__all__ = ["Index", "dtw", "dtw_pairs", "dtw_pairs_backward", "batch_nn", "batch_release", "batch_selftest_timeout", "envelope", "query_dq",
+__all__ = ["Index", "dtw", "dtw_pairs", "dtw_pairs_backward", "batch_nn", "batch_release", "batch_selftest_timeout", "lb_mv_selftest_timeout", "envelope", "query_dq",
            "pc_boxes", "lower_bounds", "compact", "Opts", "Stats", "TcdtwError", "lib_path",
            "LB_MV", "LB_PC", "LB_TI", "default_opts"]
 
@@ -91,6 +91,7 @@ _SIGS = {
     "tcdtw_lb_mv_noalloc": (C.c_int, [_P, _I64, _P, _I64, _I32, _I32, _I32, _P, _P]),
     "tcdtw_batch_nn": (C.c_int, [C.POINTER(Dataset), _I32, C.POINTER(Opts), C.POINTER(Stats), _P]),
     "tcdtw_batch_selftest_timeout": (C.c_int, [_I64, _P]),
+    "tcdtw_lb_mv_selftest_timeout": (C.c_int, [_I64, _P]),
     "tcdtw_batch_release": (C.c_int, []),
     "tcdtw_tile_count": (C.c_int, []),
     "tcdtw_set_profiling": (C.c_int, [_P, _I32]),
@@ -346,6 +347,12 @@ def batch_selftest_timeout(spin_limit: int = 200000) -> int:
     """Run the batched launch's wait-limit self-test; returns the status code
     (TIMEOUT when the device-side wait ran out and the launch ended by itself)."""
     return int(_load().tcdtw_batch_selftest_timeout(int(spin_limit), _stream()))
+
+
+def lb_mv_selftest_timeout(wait_us: int = 20000) -> int:
+    """Run the TMA LB_MV stream's wait-limit self-test; returns the status code
+    (TIMEOUT when the device-side wait ran out and the launch ended by itself)."""
+    return int(_load().tcdtw_lb_mv_selftest_timeout(int(wait_us), _stream()))
 
 
 # ----------------------------------------------------------------- pipeline stages

@@ -196,6 +196,9 @@ struct tcdtw_index {
     unsigned long long *bsf = nullptr, *best64 = nullptr, *best_idx = nullptr, *counters = nullptr;
     unsigned long long *bestdf = nullptr, *best_idx_df = nullptr;
     DevStatus *status = nullptr;
+    float *mv_ws = nullptr;      // partial sums of split LB_MV tiles
+    int64_t mv_ws_floats = 0;
+    int32_t *mv_cnt = nullptr;   // their per-tile arrival counters (kept zero)
     int64_t refine_cap = 0;
     // per-stage CUDA-event profile (tcdtw_set_profiling)
     bool profile = false;
@@ -233,7 +236,7 @@ void free_index(tcdtw_index *x) {
     void *ptrs[] = {x->U, x->Lo, x->dq_lo, x->dq_hi, x->boxes, x->lbm, x->box_counts, x->seeds, x->surv,
                     x->refine, x->seed_dtw, x->surv_lb, x->surv_dtw, x->refine_d64, x->row_counts,
                     x->row_offsets, x->scalars, x->bsf, x->best64, x->best_idx, x->counters, x->status,
-                    x->refine64, x->refine64_d64, x->amb, x->bestdf, x->best_idx_df};
+                    x->refine64, x->refine64_d64, x->amb, x->bestdf, x->best_idx_df, x->mv_ws, x->mv_cnt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete x;
@@ -285,6 +288,10 @@ int alloc_index(tcdtw_index *x) {
     TC_TRY(dalloc(&x->counters, (size_t)kNumCounters));
     TC_TRY(dalloc(&x->status, 1));
     TC_TRY(cudaMemset(x->status, 0, sizeof(DevStatus)));
+    x->mv_ws_floats = std::min<int64_t>(kMvWsFloats, 64 * Mb * N);
+    TC_TRY(dalloc(&x->mv_ws, (size_t)x->mv_ws_floats));
+    TC_TRY(dalloc(&x->mv_cnt, (size_t)kMvTileCounters));
+    TC_TRY(cudaMemset(x->mv_cnt, 0, sizeof(int32_t) * kMvTileCounters));
     TC_TRY(cudaMemset(x->counters, 0, sizeof(unsigned long long) * kNumCounters));
     return TCDTW_OK;
 }
@@ -343,7 +350,8 @@ cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_o
     } else {
         LbMvArgs mv;
         mv.cand = x->cand; mv.N = N; mv.E = E; mv.U = x->U; mv.Lo = x->Lo; mv.ldE = x->ldE; mv.Mb = Mb_cur;
-        mv.lb = x->lbm; mv.ldLb = N; mv.sms = x->sms;
+        mv.lb = x->lbm; mv.ldLb = N; mv.sms = x->sms; mv.status = x->status;
+        mv.ws = x->mv_ws; mv.ws_floats = x->mv_ws_floats; mv.tile_cnt = x->mv_cnt; mv.tile_cnt_cap = kMvTileCounters;
         if ((e = launch_lb_mv(mv, s)) != cudaSuccess) return e;
     }
     // 3. seeds and their DTW
@@ -781,9 +789,26 @@ int tcdtw_lower_bounds(const float *q, int64_t M, const float *c, int64_t N, int
         const int64_t ldE = ((int64_t)E + 31) / 32 * 32;
         const int64_t Mp = (M + 31) / 32 * 32;
         float *U = nullptr, *Lo = nullptr;
-        if (cudaMalloc(&U, sizeof(float) * Mp * ldE) != cudaSuccess) return TCDTW_ERR_NOMEM;
-        if (cudaMalloc(&Lo, sizeof(float) * Mp * ldE) != cudaSuccess) { cudaFree(U); return TCDTW_ERR_NOMEM; }
-        cudaError_t e = cudaSuccess;
+        DevStatus *st = nullptr;
+        float *ws = nullptr;
+        int32_t *cnt = nullptr;
+        const int64_t ws_floats = std::min<int64_t>(kMvWsFloats, 64 * M * N);
+        auto release = [&]() {
+            cudaFree(U);
+            cudaFree(Lo);
+            cudaFree(st);
+            cudaFree(ws);
+            cudaFree(cnt);
+        };
+        if (cudaMalloc(&U, sizeof(float) * Mp * ldE) != cudaSuccess ||
+            cudaMalloc(&Lo, sizeof(float) * Mp * ldE) != cudaSuccess ||
+            cudaMalloc(&st, sizeof(DevStatus)) != cudaSuccess || cudaMalloc(&ws, sizeof(float) * ws_floats) != cudaSuccess ||
+            cudaMalloc(&cnt, sizeof(int32_t) * kMvTileCounters) != cudaSuccess) {
+            release();
+            return TCDTW_ERR_NOMEM;
+        }
+        cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * kMvTileCounters, s);
         for (int64_t m0 = 0; m0 < M && e == cudaSuccess; m0 += 65534) {  // even chunks keep the pair layout
             const int64_t mc = (M - m0) < 65534 ? (M - m0) : 65534;
             e = launch_envelope_pairs(q + m0 * E, mc, L, D, W, U + m0 * ldE, Lo + m0 * ldE, (int)ldE, s);
@@ -791,13 +816,18 @@ int tcdtw_lower_bounds(const float *q, int64_t M, const float *c, int64_t N, int
         if (e == cudaSuccess) {
             LbMvArgs mv;
             mv.cand = c; mv.N = N; mv.E = E; mv.U = U; mv.Lo = Lo; mv.ldE = ldE; mv.Mb = (int)M; mv.lb = out;
-            mv.ldLb = N; mv.sms = sms;
+            mv.ldLb = N; mv.sms = sms; mv.status = st;
+            mv.ws = ws; mv.ws_floats = ws_floats; mv.tile_cnt = cnt; mv.tile_cnt_cap = kMvTileCounters;
             e = launch_lb_mv(mv, s);
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         rc = cuda_err(e);
-        cudaFree(U);
-        cudaFree(Lo);
+        if (rc == TCDTW_OK) {
+            DevStatus h;
+            rc = cuda_err(cudaMemcpy(&h, st, sizeof(h), cudaMemcpyDeviceToHost));
+            if (rc == TCDTW_OK && h.code) rc = h.code;
+        }
+        release();
         return rc;
     }
     // LB_PC / LB_TI: every pair listed once, no gate (e = -1), threshold +inf

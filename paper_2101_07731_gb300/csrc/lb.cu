@@ -47,6 +47,10 @@ bool lb_mv_vec4(const float *cand, int E) { return (E % 4) == 0 && (((uintptr_t)
 
 cudaError_t launch_lb_mv(const LbMvArgs &a, cudaStream_t s) {
     if (a.N <= 0 || a.Mb <= 0) return cudaSuccess;
+    if (a.status) {  // the TMA-fed stream where it applies (lb_tma.cu)
+        cudaError_t e = launch_lb_mv_tma(a, s);
+        if (e != cudaErrorNotSupported) return e;
+    }
     const int vec4 = lb_mv_vec4(a.cand, a.E);
     const int n_ctiles = (int)((a.N + kMvRows - 1) / kMvRows);
     int QB = 32;

@@ -33,8 +33,26 @@ struct LbMvArgs {
     float *lb;          // [Mb][ldLb]
     int64_t ldLb;
     int sms;
+    // device status word for the bounded waits of the TMA stream; null selects the
+    // cp.async stream (which has no waits)
+    DevStatus *status = nullptr;
+    // optional: workspace for the partial sums of split tiles (ws_floats floats) and
+    // per-tile arrival counters (tile_cnt_cap ints, zero before the first use; every
+    // launch leaves them zero); without them every tile is one work unit
+    float *ws = nullptr;
+    int64_t ws_floats = 0;
+    int *tile_cnt = nullptr;
+    int64_t tile_cnt_cap = 0;
 };
 cudaError_t launch_lb_mv(const LbMvArgs &a, cudaStream_t s);
+// lb_tma.cu: the same stream fed by bulk-tensor copies (needs E % 4 == 0, 16-byte
+// aligned candidates and envelopes, and a status word); cudaErrorNotSupported when
+// the arguments do not qualify
+bool lb_mv_tma_ok(const LbMvArgs &a);
+// workspace sizes that let the TMA stream split every tile it needs to split
+constexpr int64_t kMvWsFloats = (int64_t)1 << 23;
+constexpr int64_t kMvTileCounters = 4096;
+cudaError_t launch_lb_mv_tma(const LbMvArgs &a, cudaStream_t s);
 // whether the LB_MV stream may copy candidate rows 16 bytes at a time
 bool lb_mv_vec4(const float *cand, int E);
 

@@ -113,6 +113,33 @@ def test_lower_bounds_large_ragged_lb_mv():
             assert out[m, n] <= ref * (1 + 1e-12) and out[m, n] >= ref * (1 - _lb_rtol(67, 3)) - 1e-6
 
 
+@pytest.mark.parametrize("M", [1, 2, 3, 5, 8, 13, 16, 17, 33, 70])
+def test_lower_bounds_lb_mv_tma_stream(M):
+    # E = L*D a multiple of 4 (the bulk-tensor stream) but not of 32 (a ragged last
+    # chunk), several candidate tiles with a ragged last tile, every query-tile width
+    L, D, W, N = 67, 4, 7, 300
+    Q, Cn = _set("proto_warp", M, N, L, D, 16 + M)
+    out = tc.lower_bounds(_gpu(Q), _gpu(Cn), W, which=tc.LB_MV).cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(M)
+    ms = sorted({0, M - 1, *rng.integers(0, M, 3).tolist()})
+    ns = sorted({0, 127, 128, 255, 256, N - 1, *rng.integers(0, N, 4).tolist()})
+    for m in ms:
+        for n in ns:
+            ref = O.lb_mv(Q[m], Cn[n], W)
+            assert out[m, n] <= ref * (1 + 1e-12) + 1e-30, (m, n, out[m, n], ref)
+            assert out[m, n] >= ref * (1 - _lb_rtol(L, D)) - 1e-6, (m, n, out[m, n], ref)
+
+
+def test_lb_mv_tma_wait_limit_selftest():
+    # the consumers' first wait runs out; the launch reports TIMEOUT and the context
+    # stays usable for the next call
+    assert tc.lb_mv_selftest_timeout(20000) == tc.ERR_TIMEOUT
+    Q, Cn = _set("proto_warp", 2, 40, 32, 4, 17)
+    out = tc.lower_bounds(_gpu(Q), _gpu(Cn), 3, which=tc.LB_MV).cpu().numpy().astype(np.float64)
+    ref = O.lb_mv(Q[1], Cn[39], 3)
+    assert out[1, 39] <= ref * (1 + 1e-12) + 1e-30 and out[1, 39] >= ref * (1 - _lb_rtol(32, 4)) - 1e-6
+
+
 def test_compact_bit_exact():
     rng = np.random.default_rng(0)
     lb = rng.random((7, 1000)).astype(np.float32)
