@@ -161,4 +161,95 @@ __device__ double band_pass_df(const float *__restrict__ A, const float *__restr
     return res_h < INF ? __dadd_rn((double)res_h, (double)res_l) : __longlong_as_double(0x7ff0000000000000LL);
 }
 
+// Double-float cost of one cell (rows a and b of D floats, D <= DM), in the operation
+// order of band_pass_df: (c_h, c_l) = FastTwoSum of the exact-part sum and the
+// small-part sum.
+template <int DM>
+__device__ __forceinline__ void df_cell_cost(const float *a, const float *b, int D, float &c_h, float &c_l) {
+    float sh = 0.f, sl = 0.f;
+#pragma unroll
+    for (int p = 0; p < DM; ++p) {
+        if (p < D) {
+            float th, tl;
+            two_sum(a[p], -b[p], th, tl);  // th + tl = a - b
+            df_square_term(th, tl, sh, sl);
+        }
+    }
+    fast_two_sum(sh, sl, c_h, c_l);
+}
+
+// The double-float band DP of one pair by one warp (G = 32, R rows per lane) with the
+// cell costs already in a table: cost[i * (2W+1) + (j - i + W)] = (c_h, c_l) of cell
+// (i, j).  Same sweep and update as band_pass_df, so the result is bit-identical; a
+// step is then only the two shuffles and the double-word minimum and addition, which
+// is what bounds a lone warp (the cost arithmetic is a long serial chain per cell).
+template <int R>
+__device__ double band_pass_df_table(const float2 *cost, int L, int W, const Grp &g) {
+    const float INF = TC_INF;
+    const int BW = 2 * W + 1;
+    float ch[R], cl[R];
+    float bot_h = INF, bot_l = 0.f, prev_h = INF, prev_l = 0.f;
+    float res_h = INF, res_l = 0.f;
+    const int nv = (L + R - 1) / R;
+    const int vlast = (L - 1) / R;
+    int v = g.lig;
+    const int tau_end = v_jhi(nv - 1, R, W, L) + (nv - 1);
+    int tlo = v < nv ? v_jlo(v, R, W) + v : 1 << 30;
+    int thi = v < nv ? v_jhi(v, R, W, L) + v : -1;
+#pragma unroll
+    for (int r = 0; r < R; ++r) { ch[r] = INF; cl[r] = 0.f; }
+    for (int tau = 0; tau <= tau_end; ++tau) {
+        const float in_h = __shfl_sync(g.mask, bot_h, g.src);
+        const float in_l = __shfl_sync(g.mask, bot_l, g.src);
+        if (tau > thi && v < nv) {
+            v += g.G;
+            tlo = v < nv ? v_jlo(v, R, W) + v : 1 << 30;
+            thi = v < nv ? v_jhi(v, R, W, L) + v : -1;
+#pragma unroll
+            for (int r = 0; r < R; ++r) { ch[r] = INF; cl[r] = 0.f; }
+        }
+        if (tau >= tlo && tau <= thi) {
+            const int j = tau - v;
+            const int i0 = v * R;
+            float up_h = INF, up_l = 0.f, dg_h = INF, dg_l = 0.f;
+            if (v == 0) {
+                if (j == 0) dg_h = 0.f;
+            } else {
+                if (j <= i0 - 1 + W) { up_h = in_h; up_l = in_l; }
+                if (j >= 1 && j <= i0 + W) { dg_h = prev_h; dg_l = prev_l; }
+            }
+            const unsigned vm = row_mask(j - W - i0, min(j + W - i0, L - 1 - i0), R);
+            float2 c[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                c[r] = ((vm >> r) & 1u) ? cost[(size_t)(i0 + r) * BW + (j - (i0 + r) + W)] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float lh = ch[r], ll = cl[r];
+                float vh = INF, vl = 0.f;
+                if ((vm >> r) & 1u) {
+                    float mh = up_h, ml = up_l;
+                    if (df_less(lh, ll, mh, ml)) { mh = lh; ml = ll; }
+                    if (df_less(dg_h, dg_l, mh, ml)) { mh = dg_h; ml = dg_l; }
+                    if (mh < INF) df_add(c[r].x, c[r].y, mh, ml, vh, vl);
+                }
+                dg_h = lh; dg_l = ll;
+                up_h = vh; up_l = vl;
+                ch[r] = vh; cl[r] = vl;
+            }
+            bot_h = ch[R - 1];
+            bot_l = cl[R - 1];
+            if (v == vlast && j == L - 1) {
+                const int rl = (L - 1) - i0;
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (r == rl) { res_h = ch[r]; res_l = cl[r]; }
+            }
+        }
+        prev_h = in_h;
+        prev_l = in_l;
+    }
+    return res_h < INF ? __dadd_rn((double)res_h, (double)res_l) : __longlong_as_double(0x7ff0000000000000LL);
+}
+
 }  // namespace tc

@@ -63,7 +63,95 @@ __global__ void __launch_bounds__(32) k_dtw_refine_df(const float *__restrict__ 
     }
 }
 
+// The same with the band's cell costs tabulated first: the block (kDfBandThreads
+// threads) computes every in-band cell's double-float cost into a shared-memory table
+// in parallel (two cells per thread at a time: each cost is a long serial chain), and
+// one warp then runs the band DP from the table (band_pass_df_table).  The series are
+// read through L1 (a pair is a few KB); the table alone fits twice per SM for the
+// benchmark shape (108 KB at L = 256, W = 26).  Bit-identical to k_dtw_refine_df; used
+// when the table fits in shared memory.
+constexpr int kDfBandThreads = 128;
+
+template <int R, int DM>
+__global__ void __launch_bounds__(kDfBandThreads) k_dtw_refine_df_band(const float *__restrict__ Q,
+                                                                       const float *__restrict__ Cand, int L, int D,
+                                                                       int W, int64_t N,
+                                                                       const uint32_t *__restrict__ pairs,
+                                                                       const int32_t *__restrict__ count,
+                                                                       double *__restrict__ v,
+                                                                       unsigned long long *__restrict__ bestdf) {
+    extern __shared__ __align__(16) float2 cost[];
+    const int E = L * D, BW = 2 * W + 1, cells = L * BW;
+    const int n_entries = *count;
+    for (int e = blockIdx.x; e < n_entries; e += gridDim.x) {
+        const uint32_t pid = pairs[e];
+        const int m = (int)(pid / (uint32_t)N);
+        const int64_t n = (int64_t)(pid - (uint32_t)m * (uint32_t)N);
+        const float *qa = Q + (size_t)m * E, *cb = Cand + (size_t)n * E;
+        __syncthreads();  // the previous entry's sweep is done with the table
+        for (int k0 = threadIdx.x; k0 < cells; k0 += 2 * kDfBandThreads) {
+            float ch[2], cl[2];
+            bool in[2];
+            int kk[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                kk[u] = k0 + u * kDfBandThreads;
+                const int k = kk[u] < cells ? kk[u] : cells - 1;
+                const int i = k / BW, j = i + (k - i * BW) - W;
+                in[u] = kk[u] < cells && j >= 0 && j < L;
+                const int jj = in[u] ? j : i;
+                df_cell_cost<DM>(qa + (size_t)i * D, cb + (size_t)jj * D, D, ch[u], cl[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+                if (in[u]) cost[kk[u]] = make_float2(ch[u], cl[u]);
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            Grp g = make_grp(32);
+            double r = band_pass_df_table<R>(cost, L, W, g);
+            r = grp_min(r, g);
+            if (g.lig == 0) {
+                v[e] = r;
+                atomicMin(bestdf + m, (unsigned long long)__double_as_longlong(r));
+            }
+        }
+    }
+}
+
+namespace {
+constexpr size_t kDfBandSmemMax = 200 * 1024;
+
+size_t df_band_smem(int L, int, int W) { return (size_t)L * (2 * W + 1) * sizeof(float2); }
+
+template <int R, int DM>
+cudaError_t launch_refine_df_band(int blocks, cudaStream_t s, const DtwRefineArgs &x, size_t smem) {
+    static bool attr = false;  // idempotent
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_dtw_refine_df_band<R, DM>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDfBandSmemMax);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_dtw_refine_df_band<R, DM><<<blocks, kDfBandThreads, smem, s>>>(x.Q, x.C, x.L, x.D, x.W, x.N, x.pairs, x.count,
+                                                                     x.d64, x.best64);
+    note_launch();
+    return cudaGetLastError();
+}
+}  // namespace
+
 cudaError_t dtw_refine_df_launch(int R, int blocks, cudaStream_t s, const DtwRefineArgs &x) {
+    const size_t smem = df_band_smem(x.L, x.D, x.W);
+    if ((R == 1 || R == 2) && x.D <= 32 && smem <= kDfBandSmemMax) {
+        if (R == 1) {
+            if (x.D <= 8) return launch_refine_df_band<1, 8>(blocks, s, x, smem);
+            if (x.D <= 16) return launch_refine_df_band<1, 16>(blocks, s, x, smem);
+            return launch_refine_df_band<1, 32>(blocks, s, x, smem);
+        }
+        if (x.D <= 8) return launch_refine_df_band<2, 8>(blocks, s, x, smem);
+        if (x.D <= 16) return launch_refine_df_band<2, 16>(blocks, s, x, smem);
+        return launch_refine_df_band<2, 32>(blocks, s, x, smem);
+    }
     switch (R) {
 #define TC_RD(RV)                                                                                                  \
     case RV:                                                                                                       \

@@ -82,22 +82,45 @@ __device__ __forceinline__ float row_thr(const float *thresh, const unsigned lon
     return thresh ? thresh[m] : prune_threshold(bsf[m], rho);
 }
 
-// count pass: one CTA per row
-__global__ void k_count_rows(const float *__restrict__ lb, int64_t N, int64_t ldLb, const float *thresh,
-                             const unsigned long long *bsf, float rho, int32_t *__restrict__ counts,
-                             unsigned long long *pruned) {
-    const int64_t m = blockIdx.x;
-    const float thr = row_thr(thresh, bsf, rho, m);
-    const float *row = lb + (size_t)m * ldLb;
-    int c = 0;
-    for (int64_t n = threadIdx.x; n < N; n += blockDim.x) c += (row[n] <= thr);
-    __shared__ int red[32];
+// The per-row passes run one CTA of kRowThreads threads per row; a row of N bounds
+// was just written by the LB_MV stream and sits in L2, so the passes are bound by load
+// latency: every thread keeps four loads (count, seeds) or kRowEpt loads (write) in
+// flight instead of walking the row one coalesced load at a time.
+constexpr int kRowThreads = 1024;
+constexpr int kRowEpt = 16;  // write pass: contiguous bounds per thread per chunk
+
+__device__ __forceinline__ int block_sum(int c, int *red) {
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
     __syncthreads();
+    int t = 0;
+    if (threadIdx.x < 32) {
+        t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    return t;  // valid in thread 0
+}
+
+// count pass: one CTA per row
+__global__ void __launch_bounds__(kRowThreads) k_count_rows(const float *__restrict__ lb, int64_t N, int64_t ldLb,
+                                                            const float *thresh, const unsigned long long *bsf,
+                                                            float rho, int32_t *__restrict__ counts,
+                                                            unsigned long long *pruned) {
+    __shared__ int red[32];
+    const int64_t m = blockIdx.x;
+    const float thr = row_thr(thresh, bsf, rho, m);
+    const float *row = lb + (size_t)m * ldLb;
+    const int64_t bd = blockDim.x;
+    int c = 0;
+    for (int64_t n0 = threadIdx.x; n0 < N; n0 += 4 * bd) {
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = n0 + u * bd < N ? row[n0 + u * bd] : TC_INF;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) c += (n0 + u * bd < N && v[u] <= thr);
+    }
+    const int t = block_sum(c, red);
     if (threadIdx.x == 0) {
-        int t = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
         counts[m] = t;
         if (pruned) atomicAdd(pruned, (unsigned long long)(N - t));
     }
@@ -129,69 +152,93 @@ __global__ void k_scan_counts(const int32_t *__restrict__ counts, int64_t M, int
     if (threadIdx.x == 0) *total = carry;
 }
 
-// write pass: one CTA (256 threads) per row, survivors in increasing n.  Output
-// position of row m's k-th survivor: base(m) + k with base(m) = offsets[m] (flat
-// list) or m * ldOut (per-row lists).  pairs (flat) receive m*N + n and lbs the
-// bound; idx_out (per-row) receives n.
-__global__ void k_write_rows(const float *__restrict__ lb, int64_t N, int64_t ldLb, const float *thresh,
-                             const unsigned long long *bsf, float rho, const int32_t *__restrict__ offsets,
-                             int64_t ldOut, uint32_t *__restrict__ pairs, float *__restrict__ lbs,
-                             int32_t *__restrict__ idx_out) {
+// write pass: one CTA per row, survivors in increasing n.  The row is taken in chunks
+// of kRowThreads * kRowEpt bounds; thread t owns the kRowEpt consecutive bounds
+// [t*kRowEpt, (t+1)*kRowEpt) of a chunk, so one exclusive scan of the per-thread
+// survivor counts gives every survivor its place.  Output position of row m's k-th
+// survivor: base(m) + k with base(m) = offsets[m] (flat list) or m * ldOut (per-row
+// lists).  pairs (flat) receive m*N + n and lbs the bound; idx_out (per-row) receives n.
+__global__ void __launch_bounds__(kRowThreads) k_write_rows(const float *__restrict__ lb, int64_t N, int64_t ldLb,
+                                                            const float *thresh, const unsigned long long *bsf,
+                                                            float rho, const int32_t *__restrict__ offsets,
+                                                            int64_t ldOut, uint32_t *__restrict__ pairs,
+                                                            float *__restrict__ lbs, int32_t *__restrict__ idx_out) {
+    __shared__ int wsum[32];
+    __shared__ int chunk_total;
     const int64_t m = blockIdx.x;
     const float thr = row_thr(thresh, bsf, rho, m);
     const float *row = lb + (size_t)m * ldLb;
     const int64_t base = offsets ? (int64_t)offsets[m] : m * ldOut;
-    __shared__ int wsum[8];
-    __shared__ int running;
-    if (threadIdx.x == 0) running = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t n0 = 0; n0 < N; n0 += 256) {
-        const int64_t n = n0 + threadIdx.x;
-        const float v = n < N ? row[n] : TC_INF;
-        const bool keep = n < N && v <= thr;
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        if (lane == 0) wsum[warp] = __popc(bal);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t chunk = (int64_t)blockDim.x * kRowEpt;
+    int64_t running = 0;
+    for (int64_t c0 = 0; c0 < N; c0 += chunk) {
+        const int64_t s = c0 + (int64_t)threadIdx.x * kRowEpt;
+        float v[kRowEpt];
+#pragma unroll
+        for (int k = 0; k < kRowEpt; ++k) v[k] = s + k < N ? row[s + k] : TC_INF;
+        unsigned keep = 0;
+#pragma unroll
+        for (int k = 0; k < kRowEpt; ++k) keep |= (unsigned)(s + k < N && v[k] <= thr) << k;
+        const int cnt = __popc(keep);
+        // exclusive scan of cnt over the CTA
+        int incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) wsum[warp] = incl;
         __syncthreads();
-        int before = running;
-        for (int w = 0; w < warp; ++w) before += wsum[w];
-        if (keep) {
-            const int64_t pos = base + before + __popc(bal & ((1u << lane) - 1u));
-            if (pairs) {
-                pairs[pos] = (uint32_t)(m * N + n);
-                lbs[pos] = v;
-            } else {
-                idx_out[pos] = (int32_t)n;
+        if (warp == 0) {
+            int w = lane < nw ? wsum[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += t;
+            }
+            if (lane < nw) wsum[lane] = w;  // inclusive over warps
+            if (lane == 31) chunk_total = w;
+        }
+        __syncthreads();
+        int64_t pos = base + running + (warp > 0 ? wsum[warp - 1] : 0) + incl - cnt;
+#pragma unroll
+        for (int k = 0; k < kRowEpt; ++k) {
+            if ((keep >> k) & 1u) {
+                if (pairs) {
+                    pairs[pos] = (uint32_t)(m * N + s + k);
+                    lbs[pos] = v[k];
+                } else {
+                    idx_out[pos] = (int32_t)(s + k);
+                }
+                ++pos;
             }
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int t = 0;
-            for (int w = 0; w < 8; ++w) t += wsum[w];
-            running += t;
-        }
-        __syncthreads();
+        running += chunk_total;
+        __syncthreads();  // wsum and chunk_total are rewritten by the next chunk
     }
 }
 
 cudaError_t launch_compact(const CompactArgs &a, cudaStream_t s) {
     if (a.M <= 0) return cudaSuccess;
-    k_count_rows<<<(unsigned)a.M, 256, 0, s>>>(a.lb, a.N, a.ldLb, a.thresh, a.bsf, a.rho, a.counts, a.pruned); note_launch();
+    k_count_rows<<<(unsigned)a.M, kRowThreads, 0, s>>>(a.lb, a.N, a.ldLb, a.thresh, a.bsf, a.rho, a.counts,
+                                                        a.pruned);
+    note_launch();
     if (a.offsets) {
         k_scan_counts<<<1, 1024, 0, s>>>(a.counts, a.M, a.offsets, a.total);
         note_launch();
     }
-    k_write_rows<<<(unsigned)a.M, 256, 0, s>>>(a.lb, a.N, a.ldLb, a.thresh, a.bsf, a.rho, a.offsets, a.ldOut, a.pairs,
-                                                a.lbs, a.idx_out); note_launch();
+    k_write_rows<<<(unsigned)a.M, kRowThreads, 0, s>>>(a.lb, a.N, a.ldLb, a.thresh, a.bsf, a.rho, a.offsets, a.ldOut,
+                                                        a.pairs, a.lbs, a.idx_out);
+    note_launch();
     return cudaGetLastError();
 }
 
 // ============================================================== seeds
-// Per row m (one CTA of 256 threads): the S candidates with the smallest bound
+// Per row m (one CTA of kRowThreads threads): the S candidates with the smallest bound
 // (ties: smaller n) become seed entries m*N + n (empty slots: UINT32_MAX), and
 // their bound in the row is replaced by +inf so they do not survive compaction.
 // Per row m (one CTA): seed entries m*N + n (empty slots: UINT32_MAX).
-__global__ void k_seed_topk(float *__restrict__ lb, int64_t N, int64_t ldLb, int S, uint32_t *__restrict__ seeds) {
+__global__ void __launch_bounds__(kRowThreads) k_seed_topk(float *__restrict__ lb, int64_t N, int64_t ldLb, int S,
+                                                          uint32_t *__restrict__ seeds) {
     __shared__ uint32_t picked[kMaxSeeds];
     const int64_t m = blockIdx.x;
     seed_topk_row(lb + (size_t)m * ldLb, N, S, picked);
@@ -204,7 +251,8 @@ __global__ void k_seed_topk(float *__restrict__ lb, int64_t N, int64_t ldLb, int
 cudaError_t launch_seed_topk(float *lb, int64_t M, int64_t N, int64_t ldLb, int S, uint32_t *seeds, cudaStream_t s) {
     if (M <= 0 || S <= 0) return cudaSuccess;
     if (S > kMaxSeeds) S = kMaxSeeds;
-    k_seed_topk<<<(unsigned)M, 256, 0, s>>>(lb, N, ldLb, S, seeds); note_launch();
+    k_seed_topk<<<(unsigned)M, kRowThreads, 0, s>>>(lb, N, ldLb, S, seeds);
+    note_launch();
     return cudaGetLastError();
 }
 

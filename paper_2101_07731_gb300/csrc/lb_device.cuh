@@ -181,16 +181,25 @@ __device__ inline void seed_topk_row(float *__restrict__ row, int64_t N, int S, 
     uint32_t bi[kMaxSeeds];
 #pragma unroll
     for (int k = 0; k < kMaxSeeds; ++k) { bv[k] = TC_INF; bi[k] = 0xffffffffu; }
-    for (int64_t n = threadIdx.x; n < N; n += blockDim.x) {
-        float v = row[n];
-        uint32_t iv = (uint32_t)n;
-        if (!(v < TC_INF)) continue;
+    // four loads in flight per thread (the row is an L2-resident, latency-bound read);
+    // the lexicographic (bound, n) order makes the result independent of visit order
+    const int64_t bd = blockDim.x;
+    for (int64_t n0 = threadIdx.x; n0 < N; n0 += 4 * bd) {
+        float v4[4];
 #pragma unroll
-        for (int k = 0; k < kMaxSeeds; ++k) {  // insertion into the sorted local list
-            if (k < S && lex_less(v, iv, bv[k], bi[k])) {
-                float tv = bv[k]; uint32_t ti = bi[k];
-                bv[k] = v; bi[k] = iv;
-                v = tv; iv = ti;
+        for (int u = 0; u < 4; ++u) v4[u] = n0 + u * bd < N ? row[n0 + u * bd] : TC_INF;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            float v = v4[u];
+            uint32_t iv = (uint32_t)(n0 + u * bd);
+            if (!(v < TC_INF)) continue;
+#pragma unroll
+            for (int k = 0; k < kMaxSeeds; ++k) {  // insertion into the sorted local list
+                if (k < S && lex_less(v, iv, bv[k], bi[k])) {
+                    float tv = bv[k]; uint32_t ti = bi[k];
+                    bv[k] = v; bi[k] = iv;
+                    v = tv; iv = ti;
+                }
             }
         }
     }
