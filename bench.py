@@ -256,6 +256,80 @@ def large_leg(tc, dev):
             "note": "one search after a warm one, device-resident inputs (26 GB >> L2), per-stage CUDA events"}
 
 
+def pairs_leg(tc, dev, flush, reps=10):
+    """The differentiable DTW distance: 1,024 pairs, L=512, D=8, W=51 (random walks).
+    Forward alone (no checkpoints), and forward with band-row checkpoints plus the
+    backward pass (what one autograd step costs); CUDA events, L2 flushed before every
+    repetition."""
+    import torch
+    wl = synth.PAIRS_1024_L512
+    a, b = wl.pairs()
+    A, B = torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)
+    P, L, D, W = wl.P, wl.L, wl.D, wl.W
+    ck = torch.empty(max(1, tc.ckpt_bytes(P, L, D, W) // 4), dtype=torch.float32, device=dev)
+    g = torch.ones(P, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / reps
+
+    fwd_ms = timed(lambda: tc.dtw_pairs(A, B, W))
+    fb_ms = timed(lambda: (tc.dtw_pairs(A, B, W, ck), tc.dtw_pairs_backward(A, B, W, ck, g)))
+    cells = P * synth.band_cells(L, W)
+    instr = cells * (2 * D + 3)
+    peak = SM_COUNT_NOMINAL * FP32_LANES_PER_SM * 2070e6
+    return {"workload": wl.name, "pairs": P, "forward_ms": fwd_ms, "forward_pairs_per_s": P / (fwd_ms / 1e3),
+            "forward_cell_updates_per_s": cells / (fwd_ms / 1e3),
+            "forward_roofline": {"bound": "alu", "achieved": instr / (fwd_ms / 1e3) / 1e12, "peak": peak / 1e12,
+                                 "unit": "Tinstr/s", "frac": instr / (fwd_ms / 1e3) / peak},
+            "forward_backward_ms": fb_ms, "forward_backward_pairs_per_s": P / (fb_ms / 1e3),
+            "note": "forward: tcdtw_dtw_pairs without checkpoints; forward_backward: with band-row "
+                    "checkpoints plus tcdtw_dtw_pairs_backward; algorithmic 2D+3 FP32 operations per band cell"}
+
+
+def reverse_lb_leg(tc, cand, q, wl, flush, stream, ms_default, reps=5):
+    """The candidate-side LB_MV (use_rev=1) on the benchmark search: candidate envelopes
+    built once per index, the reverse bound applied to every LB_MV survivor."""
+    import torch
+    t0 = time.perf_counter()
+    x = tc.Index(cand, wl.W, wl.K, use_rev=1)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    out = (torch.empty(wl.M, dtype=torch.int64, device=q.device),
+           torch.empty(wl.M, dtype=torch.float64, device=q.device))
+    _, _, st = x.nn(q, stats=True)
+    for _ in range(2):
+        x.nn(q, out=out)
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x.nn(q, out=out)
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    x.close()
+    ms = tot / reps
+    return {"ms_per_step": ms, "queries_per_s": wl.M / (ms / 1e3), "vs_default_step": ms / ms_default,
+            "pruned_rev": st["pruned_rev"], "pruned_mv": st["pruned_mv"], "dtw_started": st["dtw_started"],
+            "build_s": build_s,
+            "note": "tcdtw_build with use_rev=1 (candidate envelopes, 2*N*L*D floats) and the same search"}
+
+
 def cpu_oracle_sample(Q, Cn, W, K, target_s):
     """The paper's pruned search (FP64 oracle, OpenMP over queries) on a bounded
     sample sized for about target_s seconds: a prefix of the queries, or whole passes
@@ -525,6 +599,8 @@ def run_ours(a):
         tot = job_time_ms(tot, dist, dev)
         res["e2e"] = {"value": job_value(world, wl.M, a.steps, tot), "unit": "queries/s",
                       "h2d_bytes_per_step": int(qh.numel() * 4), "d2h_bytes_per_step": int(wl.M * 16)}
+    if not a.no_extra:
+        res["reverse_lb"] = reverse_lb_leg(tc, cand, q, wl, flush, stream, ms_per_step)
     if not a.no_few:
         res["few_queries"] = few_queries_leg(tc, cand, q, wl, flush, stream)
     index.close()
@@ -550,6 +626,7 @@ def run_ours(a):
                                  "note": "host wall time per tcdtw_nn call (graph replay, synchronous)"}
         small.close()
         if world == 1:
+            res["pairs"] = pairs_leg(tc, dev, flush)
             res["batched"] = batched_leg(tc, dev)
             res["large"] = large_leg(tc, dev)
 

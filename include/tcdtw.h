@@ -47,6 +47,8 @@ extern "C" {
 #define TCDTW_LB_MV 0 /* LB_MV (Section 3), over candidate points, no sqrt            */
 #define TCDTW_LB_PC 1 /* LB_PC (Section 5) with uniform window grouping              */
 #define TCDTW_LB_TI 2 /* LB_TI in its TIP_TOP form (Section 4.2 (3))                  */
+#define TCDTW_LB_MV_REV 3 /* candidate-side LB_MV: the candidate's envelope, summed over
+                             query points (Section 3 with the roles exchanged)        */
 
 typedef struct tcdtw_index tcdtw_index; /* opaque; created by tcdtw_build */
 
@@ -74,6 +76,10 @@ typedef struct tcdtw_index tcdtw_index; /* opaque; created by tcdtw_build */
  *          e_pc in {0.1, 0.5} and Lq in {2, 3} (within use_ti / use_pc), and keeps the
  *          fastest for the index (1).  The answers do not depend on the choice;
  *          tcdtw_index_opts reports it.
+ *  use_rev  1 = also apply the candidate-side LB_MV (TCDTW_LB_MV_REV) to every pair that
+ *          survives the query-side LB_MV, before LB_PC / LB_TI; a pair's bound becomes
+ *          the larger of the two.  tcdtw_build then computes and keeps the envelopes
+ *          of all candidates (2*N*L*D floats) (0).  Not applied by tcdtw_batch_nn.
  */
 typedef struct {
     int32_t P;
@@ -90,6 +96,7 @@ typedef struct {
     int32_t no_prune;
     int32_t use_graph;
     int32_t select;
+    int32_t use_rev;
 } tcdtw_opts;
 
 /* Counters of one tcdtw_nn call, summed over its queries. */
@@ -105,6 +112,7 @@ typedef struct {
                                because FP32 could not separate them from the best */
     uint64_t refined64;     /* ... of those, recomputed in FP64 because double-float
                                could not separate them either                      */
+    uint64_t pruned_rev;    /* ... pruned by the candidate-side LB_MV (use_rev)      */
 } tcdtw_stats;
 
 /* Fill *opts with the defaults listed above. */

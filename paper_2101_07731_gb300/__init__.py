@@ -22,13 +22,13 @@ import torch
 
 __all__ = ["Index", "dtw", "dtw_pairs", "dtw_pairs_backward", "batch_nn", "batch_release", "batch_selftest_timeout", "lb_mv_selftest_timeout", "envelope", "query_dq",
            "pc_boxes", "lower_bounds", "compact", "Opts", "Stats", "TcdtwError", "lib_path",
-           "LB_MV", "LB_PC", "LB_TI", "default_opts"]
+           "LB_MV", "LB_PC", "LB_TI", "LB_MV_REV", "default_opts"]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_PKG, "libtcdtw.so")
 _lib = None
 
-LB_MV, LB_PC, LB_TI = 0, 1, 2
+LB_MV, LB_PC, LB_TI, LB_MV_REV = 0, 1, 2, 3
 # status codes of the C ABI (tcdtw.h)
 OK, ERR_INVALID, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_NONFINITE, ERR_UNSUPPORTED = range(7)
 
@@ -53,13 +53,13 @@ class Opts(C.Structure):
                 ("e_ti", C.c_float), ("use_pc", C.c_int32), ("use_ti", C.c_int32),
                 ("seed_s", C.c_int32), ("qblock", C.c_int32), ("tile", C.c_int32),
                 ("check_finite", C.c_int32), ("no_prune", C.c_int32), ("use_graph", C.c_int32),
-                ("select", C.c_int32)]
+                ("select", C.c_int32), ("use_rev", C.c_int32)]
 
 
 class Stats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ("pairs", "pruned_mv", "pruned_pc", "pruned_ti", "dtw_started",
                                           "dtw_abandoned", "cells", "refined",
-                                          "refined64")]
+                                          "refined64", "pruned_rev")]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}

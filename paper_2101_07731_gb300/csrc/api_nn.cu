@@ -162,7 +162,8 @@ cudaError_t dalloc(T **p, size_t n) {
 }
 
 enum Counter {
-    kStarted = 0, kAbandoned, kCells, kPrunedDtw, kPrunedMv, kPrunedPc, kPrunedTi, kRefined, kRefined64, kNumCounters
+    kStarted = 0, kAbandoned, kCells, kPrunedDtw, kPrunedMv, kPrunedPc, kPrunedTi, kRefined, kRefined64, kPrunedRev,
+    kNumCounters
 };
 enum Scalar { kSurvTotal = 0, kCursorSeed, kCursorSurv, kRefineCount, kRefine64Count, kNumScalars };
 
@@ -196,6 +197,7 @@ struct tcdtw_index {
     unsigned long long *bsf = nullptr, *best64 = nullptr, *best_idx = nullptr, *counters = nullptr;
     unsigned long long *bestdf = nullptr, *best_idx_df = nullptr;
     DevStatus *status = nullptr;
+    float *Uc = nullptr, *Lc = nullptr;  // candidate envelopes [N][L*D] (use_rev)
     float *mv_ws = nullptr;      // partial sums of split LB_MV tiles
     int64_t mv_ws_floats = 0;
     int32_t *mv_cnt = nullptr;   // their per-tile arrival counters (kept zero)
@@ -236,7 +238,8 @@ void free_index(tcdtw_index *x) {
     void *ptrs[] = {x->U, x->Lo, x->dq_lo, x->dq_hi, x->boxes, x->lbm, x->box_counts, x->seeds, x->surv,
                     x->refine, x->seed_dtw, x->surv_lb, x->surv_dtw, x->refine_d64, x->row_counts,
                     x->row_offsets, x->scalars, x->bsf, x->best64, x->best_idx, x->counters, x->status,
-                    x->refine64, x->refine64_d64, x->amb, x->bestdf, x->best_idx_df, x->mv_ws, x->mv_cnt};
+                    x->refine64, x->refine64_d64, x->amb, x->bestdf, x->best_idx_df, x->mv_ws, x->mv_cnt,
+                    x->Uc, x->Lc};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete x;
@@ -378,6 +381,10 @@ cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_o
     pl.Q = q; pl.C = x->cand; pl.L = L; pl.D = D; pl.W = W; pl.pairs = x->surv;
     pl.count = x->scalars + kSurvTotal; pl.n_static = 0; pl.N = N; pl.lb = x->surv_lb;
     const int64_t hint = (int64_t)Mb_cur * 64;
+    if (x->opts.use_rev &&
+        (e = launch_lb_rev_list(pl, x->Uc, x->Lc, x->bsf, x->rho, x->counters + kPrunedRev, hint, x->sms, s)) !=
+            cudaSuccess)
+        return e;
     if (x->opts.use_pc &&
         (e = launch_lb_pc_list(pl, x->boxes, x->box_counts, x->K, x->opts.w, x->bsf, x->rho, x->opts.e_pc,
                                x->counters + kPrunedPc, hint, x->sms, s)) != cudaSuccess)
@@ -576,7 +583,7 @@ int tcdtw_build(const float *cand, int64_t N, int32_t L, int32_t D, int32_t W, i
     x->rho_ref = prune_rho(L, D);
     x->kappa = refine_kappa(L, D);
     x->rho = o.no_prune ? INFINITY : x->rho_ref;
-    if (o.no_prune) { x->opts.use_pc = 0; x->opts.use_ti = 0; }
+    if (o.no_prune) { x->opts.use_pc = 0; x->opts.use_ti = 0; x->opts.use_rev = 0; }
     // query block: bounded by the u32 pair ids and by ~4 GB of workspace
     int64_t Mb = o.qblock > 0 ? o.qblock : 256;
     const double per_q = (double)N * 20.0 + (double)x->ldE * 8.0 + (o.use_pc ? (double)x->G_pc * K * 2 * D * 4.0 : 0);
@@ -627,6 +634,22 @@ int tcdtw_build(const float *cand, int64_t N, int32_t L, int32_t D, int32_t W, i
         }
         if (st.code) { free_index(x); return st.code; }
     }
+    if (x->opts.use_rev) {
+        // candidate-side envelopes for the reverse LB_MV, once per index
+        const int64_t E = (int64_t)L * D;
+        if (E > INT32_MAX) { free_index(x); return TCDTW_ERR_UNSUPPORTED; }
+        rc = dalloc(&x->Uc, (size_t)N * E) == cudaSuccess && dalloc(&x->Lc, (size_t)N * E) == cudaSuccess
+                 ? TCDTW_OK
+                 : TCDTW_ERR_NOMEM;
+        cudaError_t e = cudaSuccess;
+        for (int64_t n0 = 0; rc == TCDTW_OK && n0 < N && e == cudaSuccess; n0 += 65535) {
+            const int64_t nc = (N - n0) < 65535 ? (N - n0) : 65535;
+            e = launch_envelope(cand + n0 * E, nc, L, D, W, x->Uc + n0 * E, x->Lc + n0 * E, (int)E, s);
+        }
+        if (rc == TCDTW_OK && e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (rc == TCDTW_OK && e != cudaSuccess) rc = cuda_err(e);
+        if (rc) { free_index(x); return rc; }
+    }
     *out = x;
     return TCDTW_OK;
 }
@@ -673,6 +696,7 @@ int tcdtw_nn(tcdtw_index *x, const float *q, int64_t M, int64_t *idx, double *di
         stats->pruned_mv = c[kPrunedMv] - seeds + c[kPrunedDtw];
         stats->pruned_pc = c[kPrunedPc];
         stats->pruned_ti = c[kPrunedTi];
+        stats->pruned_rev = c[kPrunedRev];
         stats->dtw_started = c[kStarted];
         stats->dtw_abandoned = c[kAbandoned];
         stats->cells = c[kCells];
@@ -771,7 +795,7 @@ int tcdtw_compact(const float *lb, int64_t M, int64_t N, const float *thresh, in
 int tcdtw_lower_bounds(const float *q, int64_t M, const float *c, int64_t N, int32_t L, int32_t D, int32_t W,
                        int32_t K, const tcdtw_opts *opts, int32_t which, float *out, void *stream) {
     if (M < 0 || N < 0 || L < 1 || D < 1 || W < 0 || K < 1) return TCDTW_ERR_INVALID;
-    if (which < TCDTW_LB_MV || which > TCDTW_LB_TI) return TCDTW_ERR_INVALID;
+    if (which < TCDTW_LB_MV || which > TCDTW_LB_MV_REV) return TCDTW_ERR_INVALID;
     if (D > TCDTW_MAX_D) return TCDTW_ERR_UNSUPPORTED;
     if (M == 0 || N == 0) return TCDTW_OK;
     if (!q || !c || !out) return TCDTW_ERR_INVALID;
@@ -854,6 +878,15 @@ int tcdtw_lower_bounds(const float *q, int64_t M, const float *c, int64_t N, int
             e = launch_pc_boxes(q + m0 * E, mc, L, D, W, K, o.Lq, o.w, aux1 + m0 * G * K * 2 * D, cnts + m0 * G, s);
         }
         if (e == cudaSuccess) e = launch_lb_pc_list(pl, aux1, cnts, K, o.w, bsf, rho, -1.0f, nullptr, P, sms, s);
+    } else if (which == TCDTW_LB_MV_REV) {
+        // envelopes of the candidates, then every pair's reverse bound
+        if (e == cudaSuccess) e = cudaMalloc(&aux1, sizeof(float) * N * E);
+        if (e == cudaSuccess) e = cudaMalloc(&aux2, sizeof(float) * N * E);
+        for (int64_t n0 = 0; n0 < N && e == cudaSuccess; n0 += 65535) {
+            const int64_t nc = (N - n0) < 65535 ? (N - n0) : 65535;
+            e = launch_envelope(c + n0 * E, nc, L, D, W, aux1 + n0 * E, aux2 + n0 * E, E, s);
+        }
+        if (e == cudaSuccess) e = launch_lb_rev_list(pl, aux1, aux2, nullptr, rho, nullptr, P, sms, s);
     } else {
         if (e == cudaSuccess) e = cudaMalloc(&aux1, sizeof(float) * M * L);
         if (e == cudaSuccess) e = cudaMalloc(&aux2, sizeof(float) * M * L);

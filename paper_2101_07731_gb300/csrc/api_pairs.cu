@@ -153,6 +153,7 @@ void tcdtw_default_opts(tcdtw_opts *o) {
     o->no_prune = 0;
     o->use_graph = 1;
     o->select = 1;
+    o->use_rev = 0;
 }
 
 const char *tcdtw_strerror(int code) {

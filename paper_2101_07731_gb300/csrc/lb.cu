@@ -358,6 +358,60 @@ cudaError_t launch_lb_ti_list(const PairListArgs &a, const float *dq_lo, const f
     return cudaGetLastError();
 }
 
+// ============================================================== reverse LB_MV on listed pairs
+// Candidate-side LB_MV (the bound with the roles of query and candidate exchanged:
+// Section 3's envelope is taken around the candidate and the query's points are
+// measured against it).  One warp per entry; the candidate envelopes Uc, Lc [N][L*D]
+// are computed once per index.  Per element m = max(q -rd Uc, Lc -rd q, 0), m*m added
+// rounded down; every 512 elements the warp's partial sum (rounded down) is compared
+// with the live threshold and the pair is dropped as soon as it exceeds it.  A kept
+// pair's bound becomes max(its bound, reverse bound): both are lower bounds of DTW.
+__global__ void __launch_bounds__(128) k_lb_rev_list(PairListArgs a, const float *__restrict__ Uc,
+                                                     const float *__restrict__ Lc, const unsigned long long *bsf,
+                                                     float rho, unsigned long long *stat_pruned) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t n_entries = a.count ? (int64_t)*a.count : a.n_static;
+    const int64_t E = (int64_t)a.L * a.D;
+    unsigned long long pruned = 0;
+    for (int64_t e = warp; e < n_entries; e += nwarps) {
+        const uint32_t pid = a.pairs[e];
+        if (pid == 0xffffffffu) continue;
+        const float cur = a.lb[e];
+        if (!(cur < TC_INF)) continue;
+        const int64_t m = pid / (uint64_t)a.N, n = pid - m * a.N;
+        const float *q = a.Q + (size_t)m * E;
+        const float *hi = Uc + (size_t)n * E, *lo = Lc + (size_t)n * E;
+        float thr = bsf ? prune_threshold(ld_volatile_u64(bsf + m), rho) : TC_INF;
+        if (cur > thr) continue;  // dropped (and counted) by the DTW stage
+        float acc = 0.f, total = 0.f;
+        bool dropped = false;
+        for (int64_t c0 = 0; c0 < E && !dropped; c0 += 512) {
+            const int64_t c1 = c0 + 512 < E ? c0 + 512 : E;
+            for (int64_t k = c0 + lane; k < c1; k += 32) acc = acc_box(__ldg(q + k), __ldg(lo + k), __ldg(hi + k), acc);
+            float t = acc;
+            for (int o = 16; o > 0; o >>= 1) t = __fadd_rd(t, __shfl_xor_sync(0xffffffffu, t, o));
+            total = t;
+            if (bsf) thr = prune_threshold(ld_volatile_u64(bsf + m), rho);
+            dropped = __shfl_sync(0xffffffffu, total > thr, 0);
+        }
+        if (lane == 0) {
+            if (dropped) { a.lb[e] = TC_INF; ++pruned; }
+            else a.lb[e] = fmaxf(cur, total);
+        }
+    }
+    if (lane == 0 && pruned && stat_pruned) atomicAdd(stat_pruned, pruned);
+}
+
+cudaError_t launch_lb_rev_list(const PairListArgs &a, const float *Uc, const float *Lc, const unsigned long long *bsf,
+                               float rho, unsigned long long *stat_pruned, int64_t n_hint, int sms, cudaStream_t s) {
+    const int blocks = list_blocks(n_hint, sms);
+    k_lb_rev_list<<<blocks, 128, 0, s>>>(a, Uc, Lc, bsf, rho, stat_pruned);
+    note_launch();
+    return cudaGetLastError();
+}
+
 // ============================================================== refine and select
 // Entries of a list whose FP32 DTW is within the final threshold join the refine
 // list (their FP64 DTW decides the winner).

@@ -114,3 +114,16 @@ def test_product_path_has_no_cpu_fallback():
         tc.Index(x, 2)
     src = open(os.path.join(ROOT, "paper_2101_07731_gb300", "__init__.py")).read()
     assert "import oracle" not in src and "from oracle" not in src
+
+
+def test_binding_structs_mirror_the_header():
+    # the ctypes mirrors of tcdtw_opts / tcdtw_stats / tcdtw_dataset must list the
+    # header's fields in the header's order (the C side writes whole structs)
+    import paper_2101_07731_gb300 as tc
+    hdr = open(os.path.join(ROOT, "include", "tcdtw.h")).read()
+    for cname, py in (("tcdtw_opts", tc.Opts), ("tcdtw_stats", tc.Stats), ("tcdtw_dataset", tc.Dataset)):
+        body = re.search(r"typedef struct \{([^{}]*)\}\s*" + cname + ";", hdr).group(1)
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        names = [re.findall(r"(\w+)\s*$", part)[0] for stmt in body.split(";") if stmt.strip()
+                 for part in stmt.split(",")]
+        assert names == [n for n, _ in py._fields_], (cname, names)

@@ -140,6 +140,22 @@ def test_lb_mv_tma_wait_limit_selftest():
     assert out[1, 39] <= ref * (1 + 1e-12) + 1e-30 and out[1, 39] >= ref * (1 - _lb_rtol(32, 4)) - 1e-6
 
 
+@pytest.mark.parametrize("M,N,L,D,W", [(4, 37, 64, 3, 6), (3, 130, 129, 5, 13), (2, 20, 50, 8, 0), (3, 25, 40, 2, 60),
+                                       (2, 9, 70, 33, 7), (2, 600, 96, 1, 9)])
+def test_lower_bounds_candidate_side_lb_mv(M, N, L, D, W):
+    # the reverse bound is LB_MV with the roles exchanged: the candidate's envelope,
+    # summed over the query's points
+    Q, Cn = _set("proto_warp", M, N, L, D, 18)
+    out = tc.lower_bounds(_gpu(Q), _gpu(Cn), W, which=tc.LB_MV_REV).cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(N)
+    for m in range(M):
+        for n in sorted({0, N - 1, *rng.integers(0, N, 6).tolist()}):
+            ref = O.lb_mv(Cn[n], Q[m], W)
+            assert out[m, n] <= ref * (1 + 1e-12) + 1e-30, (m, n, out[m, n], ref)
+            assert out[m, n] >= ref * (1 - _lb_rtol(L, D)) - 1e-6, (m, n, out[m, n], ref)
+            assert out[m, n] <= O.dtw(Q[m], Cn[n], W) * (1 + 1e-12) + 1e-30
+
+
 def test_compact_bit_exact():
     rng = np.random.default_rng(0)
     lb = rng.random((7, 1000)).astype(np.float32)
@@ -165,7 +181,8 @@ def _check_nn(Q, Cn, W, K=16, **opts):
     np.testing.assert_allclose(gd, rdist, rtol=DF_RTOL, atol=0)
     M, N = len(Q), len(Cn)
     assert st["pairs"] == M * N
-    assert st["pruned_mv"] + st["pruned_pc"] + st["pruned_ti"] + st["dtw_started"] == st["pairs"], st
+    assert (st["pruned_mv"] + st["pruned_pc"] + st["pruned_ti"] + st["pruned_rev"] + st["dtw_started"] ==
+            st["pairs"]), st
     assert st["refined"] >= M
     assert st["refined64"] <= st["refined"]
     return gd, rdist, st
@@ -198,6 +215,21 @@ def test_nn_query_blocks_and_seeds(seed_s, qblock):
 def test_nn_edge_shapes(M, N, L, D, W):
     Q, Cn = _set("random_walk", M, N, L, D, 23)
     _check_nn(Q, Cn, W, 4)
+
+
+def test_nn_candidate_side_bound_keeps_answers():
+    # use_rev adds the candidate-side LB_MV to the cascade: different pruning, same NN
+    Q, Cn = _set("proto_warp", 30, 1200, 80, 4, 33, n_proto=6)
+    gd, rd, st = _check_nn(Q, Cn, 8, 8, use_rev=1, select=0)
+    plain = tc.Index(_gpu(Cn), 8, 8, use_rev=0, select=0)
+    i0, d0, st0 = plain.nn(_gpu(Q), stats=True)
+    plain.close()
+    assert st["pruned_rev"] >= 0 and st0["pruned_rev"] == 0
+    np.testing.assert_array_equal(gd, d0.cpu().numpy())
+    # random walks: the two envelopes differ, so the reverse bound prunes some pairs
+    Q2, C2 = _set("random_walk", 12, 800, 64, 2, 34)
+    _, _, st2 = _check_nn(Q2, C2, 6, 4, use_rev=1, select=0, use_pc=0, use_ti=0)
+    assert st2["pruned_rev"] > 0
 
 
 def test_nn_tc_dtw_selection_keeps_answers():
