@@ -76,6 +76,8 @@ def lib():
         L.orc_query_dq.argtypes = [_f32p, I, I, _f64p]
         L.orc_lb_ti.restype = D_
         L.orc_lb_ti.argtypes = [_f32p, _f32p, I, I, I, I]
+        L.orc_lb_ti_var.restype = D_
+        L.orc_lb_ti_var.argtypes = [_f32p, _f32p, I, I, I, I, I]
         L.orc_pc_boxes.restype = None
         L.orc_pc_boxes.argtypes = [_f32p, I, I, I, I, I, I, _f64p, _i32p]
         L.orc_lb_pc.restype = D_
@@ -152,6 +154,15 @@ def lb_ti(q, c, W: int, P: int = 5) -> float:
     q, c = _f32(q), _f32(c)
     L, D = q.shape
     return float(lib().orc_lb_ti(q, c, L, D, W, P))
+
+
+def lb_ti_var(q, c, W: int, P: int, top: int) -> float:
+    """LB_TI variants (Section 4.2): top=1 exact window tops (TIP_TOP, or LB_TI_TOP
+    when P >= L), top=0 window tops from the candidate-side triangle (LB_TIP, or the
+    basic LB_TI when P >= L)."""
+    q, c = _f32(q), _f32(c)
+    L, D = q.shape
+    return float(lib().orc_lb_ti_var(q, c, L, D, W, P, int(top)))
 
 
 def pc_boxes(q, W: int, K: int, Lq: int = 2, w: int = 6):

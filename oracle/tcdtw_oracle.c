@@ -22,7 +22,8 @@
  *     envelopes, triangle bounds and boxes;
  *   - a negative triangle lower bound is stored as 0 (a distance is >= 0);
  *   - LB_TI uses the "TIP_TOP" variant: exact distances on query rows with
- *     i mod P == 0 and at the top of each window;
+ *     i mod P == 0 and at the top of each window (orc_lb_ti_var adds the basic,
+ *     TOP and TIP variants);
  *   - LB_PC boxes are the tight bounding boxes of each cluster's member points;
  *     cells are ordered lexicographically with dimension 0 most significant; when
  *     there are more than K non-empty cells the first K-1 are kept and the rest
@@ -239,6 +240,59 @@ double orc_lb_ti_dq(const float *q, const double *dq, const float *c, int L, int
         if (s >= abandon_at) break;
     }
     free(Lb_prev); free(Ub_prev); free(Lb_cur); free(Ub_cur); free(m);
+    return s;
+}
+
+/*
+ * The other LB_TI variants of Section 4.2 (basic LB_TI, LB_TI_TOP, LB_TIP; `top` and P
+ * select them; top = 1 is orc_lb_ti_dq above):
+ *   - i mod P == 0: exact row (P >= L: only row 0, the basic algorithm's start);
+ *   - j == i+W, top == 1: exact top of the window;
+ *   - j == i+W, top == 0, W >= 1: the candidate-side triangle with c_{j-1} (Eqs.
+ *     (bt_lb_ir), (bt_ub_ir)), dc_j = d(c_{j-1}, c_j), from row i's value at j-1:
+ *       Lb(i,j) = max(Lb(i,j-1) - dc_j, dc_j - Ub(i,j-1)),  stored as max(.,0),
+ *       Ub(i,j) = Ub(i,j-1) + dc_j;
+ *     (with W = 0 the window is the single point j = i, which has no neighbour in
+ *     the window, so it is exact);
+ *   - otherwise the query-side recursion with dq_i, as above.
+ */
+double orc_lb_ti_var(const float *q, const float *c, int L, int D, int W, int P, int top) {
+    if (W > L - 1) W = L - 1;
+    double *dq = (double *)malloc(sizeof(double) * (size_t)L);
+    double *dc = (double *)malloc(sizeof(double) * (size_t)L);
+    orc_query_dq(q, L, D, dq);
+    orc_query_dq(c, L, D, dc);  /* the same neighbour distance, on the candidate */
+    double *Lb_prev = (double *)malloc(sizeof(double) * (size_t)L);
+    double *Ub_prev = (double *)malloc(sizeof(double) * (size_t)L);
+    double *Lb_cur = (double *)malloc(sizeof(double) * (size_t)L);
+    double *Ub_cur = (double *)malloc(sizeof(double) * (size_t)L);
+    double *m = (double *)malloc(sizeof(double) * (size_t)L);
+    for (int j = 0; j < L; ++j) m[j] = ORC_INF;
+    for (int i = 0; i < L; ++i) {
+        for (int j = imax(0, i - W); j <= imin(L - 1, i + W); ++j) {
+            double lb, ub;
+            if (i % P == 0 || (j == i + W && (top || W == 0))) {
+                lb = ub = orc_euclid(q + (size_t)i * D, c + (size_t)j * D, D);
+            } else if (j == i + W) {
+                lb = dmax2(Lb_cur[j - 1] - dc[j], dc[j] - Ub_cur[j - 1]);
+                lb = dmax2(lb, 0.0);
+                ub = Ub_cur[j - 1] + dc[j];
+            } else {
+                lb = dmax2(Lb_prev[j] - dq[i], dq[i] - Ub_prev[j]);
+                lb = dmax2(lb, 0.0);
+                ub = Ub_prev[j] + dq[i];
+            }
+            Lb_cur[j] = lb;
+            Ub_cur[j] = ub;
+            m[j] = dmin2(m[j], lb);
+        }
+        double *t;
+        t = Lb_prev; Lb_prev = Lb_cur; Lb_cur = t;
+        t = Ub_prev; Ub_prev = Ub_cur; Ub_cur = t;
+    }
+    double s = 0.0;
+    for (int j = 0; j < L; ++j) s += m[j] * m[j];
+    free(dq); free(dc); free(Lb_prev); free(Ub_prev); free(Lb_cur); free(Ub_cur); free(m);
     return s;
 }
 

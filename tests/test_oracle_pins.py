@@ -203,6 +203,57 @@ def test_lb_ti_dq_is_neighbour_distance():
     assert np.allclose(dq[1:], np.linalg.norm(q[1:] - q[:-1], axis=1), rtol=1e-13)
 
 
+def _read_golden_ti():
+    q = c = None
+    vals = []
+    with open(os.path.join(HERE, "golden", "ti_variants_hand.txt")) as f:
+        for line in f:
+            t = line.split()
+            if not t or t[0].startswith("#"):
+                continue
+            if t[0] == "query":
+                q = np.array([float(x) for x in t[1:]], np.float32)[:, None]
+            elif t[0] == "cand":
+                c = np.array([float(x) for x in t[1:]], np.float32)[:, None]
+            elif t[0] == "lbti":
+                vals.append((int(t[1]), int(t[2]), float(t[3])))
+    return q, c, vals
+
+
+def test_lb_ti_variants_hand_worked_example():
+    q, c, vals = _read_golden_ti()
+    assert len(vals) == 6
+    for P, top, want in vals:
+        assert O.lb_ti_var(q, c, 1, P, top) == want, (P, top)
+    assert O.lb_ad(q, c, 1) == 36.0
+
+
+def test_lb_ti_variants_order_and_soundness():
+    """Exact window tops and more exact rows only tighten the triangle bounds (the
+    recursions are monotone in (Lb, -Ub)), and every variant stays below LB_AD:
+    basic <= TOP <= TIP_TOP, basic <= TIP <= TIP_TOP <= LB_AD, the top = 1 variant
+    is orc_lb_ti, and P = 1 gives LB_AD for both tops.  A wrong sign or a mis-indexed
+    neighbour in the candidate-side triangle breaks soundness or the order."""
+    Q = rw(3, 36, 3, 41, role=1)
+    Cs = rw(4, 36, 3, 41)
+    for W in (0, 1, 3, 8, 35):
+        for q in Q:
+            for c in Cs:
+                ad = O.lb_ad(q, c, W)
+                basic = O.lb_ti_var(q, c, W, 1000, 0)
+                top = O.lb_ti_var(q, c, W, 1000, 1)
+                tip = O.lb_ti_var(q, c, W, 4, 0)
+                tiptop = O.lb_ti_var(q, c, W, 4, 1)
+                tol = 1e-12 * max(1.0, ad)
+                assert basic <= top + tol and basic <= tip + tol
+                assert top <= tiptop + tol and tip <= tiptop + tol and tiptop <= ad + tol
+                assert tiptop == O.lb_ti(q, c, W, 4)
+                assert O.lb_ti_var(q, c, W, 1, 0) == pytest.approx(ad, rel=1e-13)
+                assert O.lb_ti_var(q, c, W, 1, 1) == pytest.approx(ad, rel=1e-13)
+                if W == 0:  # single-point windows: every top is exact, the variants agree
+                    assert basic == top and tip == tiptop
+
+
 # ---------------------------------------------------------------- LB_PC (Section 5)
 
 def _read_golden_boxes():
