@@ -330,6 +330,37 @@ def reverse_lb_leg(tc, cand, q, wl, flush, stream, ms_default, reps=5):
             "note": "tcdtw_build with use_rev=1 (candidate envelopes, 2*N*L*D floats) and the same search"}
 
 
+def ti_variants_leg(tc, cand, q, wl, flush, stream, reps=3):
+    """Ablation of the LB_TI variants (Section 4.2) on the benchmark search: each one
+    alone behind LB_MV on every survivor (LB_PC off, TI gate e = 0), and LB_MV alone."""
+    import torch
+    L = wl.spec.L
+    cases = [("lb_mv_only", dict(use_ti=0)), ("tip_top_P5", dict(P=5, ti_top=1)), ("tip_P5", dict(P=5, ti_top=0)),
+             ("top", dict(P=L, ti_top=1)), ("basic", dict(P=L, ti_top=0))]
+    out = {}
+    o = (torch.empty(wl.M, dtype=torch.int64, device=q.device), torch.empty(wl.M, dtype=torch.float64, device=q.device))
+    for name, kw in cases:
+        x = tc.Index(cand, wl.W, wl.K, select=0, use_pc=0, use_ti=kw.pop("use_ti", 1), e_ti=0.0, **kw)
+        _, _, st = x.nn(q, stats=True)
+        for _ in range(2):
+            x.nn(q, out=o)
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x.nn(q, out=o)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        x.close()
+        out[name] = {"ms_per_step": tot / reps, "pruned_ti": st["pruned_ti"], "dtw_started": st["dtw_started"],
+                     "cells": st["cells"]}
+    out["note"] = "each variant alone behind LB_MV on every survivor (e_ti = 0, LB_PC off); P = L: no periodic rows"
+    return out
+
+
 def cpu_oracle_sample(Q, Cn, W, K, target_s):
     """The paper's pruned search (FP64 oracle, OpenMP over queries) on a bounded
     sample sized for about target_s seconds: a prefix of the queries, or whole passes
@@ -601,6 +632,7 @@ def run_ours(a):
                       "h2d_bytes_per_step": int(qh.numel() * 4), "d2h_bytes_per_step": int(wl.M * 16)}
     if not a.no_extra:
         res["reverse_lb"] = reverse_lb_leg(tc, cand, q, wl, flush, stream, ms_per_step)
+        res["ti_variants"] = ti_variants_leg(tc, cand, q, wl, flush, stream)
     if not a.no_few:
         res["few_queries"] = few_queries_leg(tc, cand, q, wl, flush, stream)
     index.close()

@@ -80,6 +80,12 @@ typedef struct tcdtw_index tcdtw_index; /* opaque; created by tcdtw_build */
  *          survives the query-side LB_MV, before LB_PC / LB_TI; a pair's bound becomes
  *          the larger of the two.  tcdtw_build then computes and keeps the envelopes
  *          of all candidates (2*N*L*D floats) (0).  Not applied by tcdtw_batch_nn.
+ *  ti_top  LB_TI's window top c_{i+W}: 1 = exact distance (LB_TI_TOP; with P the
+ *          TIP_TOP form, Section 4.2 (3)), 0 = from the candidate-side triangle with
+ *          c_{i+W-1} (Eqs. (bt_lb_ir), (bt_ub_ir); with P < L the LB_TIP form, with
+ *          P >= L the basic LB_TI, whose only exact row is row 0) (1).  ti_top = 0
+ *          needs W <= 127 (else tcdtw_build and tcdtw_lower_bounds return
+ *          UNSUPPORTED); tcdtw_batch_nn always uses 1.
  */
 typedef struct {
     int32_t P;
@@ -97,6 +103,7 @@ typedef struct {
     int32_t use_graph;
     int32_t select;
     int32_t use_rev;
+    int32_t ti_top;
 } tcdtw_opts;
 
 /* Counters of one tcdtw_nn call, summed over its queries. */

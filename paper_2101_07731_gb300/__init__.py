@@ -53,7 +53,7 @@ class Opts(C.Structure):
                 ("e_ti", C.c_float), ("use_pc", C.c_int32), ("use_ti", C.c_int32),
                 ("seed_s", C.c_int32), ("qblock", C.c_int32), ("tile", C.c_int32),
                 ("check_finite", C.c_int32), ("no_prune", C.c_int32), ("use_graph", C.c_int32),
-                ("select", C.c_int32), ("use_rev", C.c_int32)]
+                ("select", C.c_int32), ("use_rev", C.c_int32), ("ti_top", C.c_int32)]
 
 
 class Stats(C.Structure):

@@ -389,10 +389,13 @@ cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_o
         (e = launch_lb_pc_list(pl, x->boxes, x->box_counts, x->K, x->opts.w, x->bsf, x->rho, x->opts.e_pc,
                                x->counters + kPrunedPc, hint, x->sms, s)) != cudaSuccess)
         return e;
-    if (x->opts.use_ti &&
-        (e = launch_lb_ti_list(pl, x->dq_lo, x->dq_hi, x->opts.P, x->bsf, x->rho, x->opts.e_ti,
-                               x->counters + kPrunedTi, hint, x->sms, s)) != cudaSuccess)
-        return e;
+    if (x->opts.use_ti) {
+        e = x->opts.ti_top ? launch_lb_ti_list(pl, x->dq_lo, x->dq_hi, x->opts.P, x->bsf, x->rho, x->opts.e_ti,
+                                               x->counters + kPrunedTi, hint, x->sms, s)
+                           : launch_lb_ti_rows_list(pl, x->dq_lo, x->dq_hi, x->opts.P, x->bsf, x->rho,
+                                                    x->opts.e_ti, x->counters + kPrunedTi, hint, x->sms, s);
+        if (e != cudaSuccess) return e;
+    }
     // 6. DTW of the survivors
     TC_MARK(6);
     dn.pairs = x->surv; dn.lb = x->surv_lb; dn.count = x->scalars + kSurvTotal; dn.n_static = 0;
@@ -572,6 +575,7 @@ int tcdtw_build(const float *cand, int64_t N, int32_t L, int32_t D, int32_t W, i
     // LB_PC only changes speed: skip it when the cell keys (Lq^D) do not fit 63 bits
     if (o.use_pc && !pc_key_fits(o.Lq, D)) o.use_pc = 0;
     if (W > L - 1) W = L - 1;
+    if (o.use_ti && !o.ti_top && !lb_ti_rows_supported(W)) return TCDTW_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     tcdtw_index *x = new (std::nothrow) tcdtw_index();
     if (!x) return TCDTW_ERR_NOMEM;
@@ -802,6 +806,8 @@ int tcdtw_lower_bounds(const float *q, int64_t M, const float *c, int64_t N, int
     tcdtw_opts o;
     if (opts) o = *opts; else tcdtw_default_opts(&o);
     if (which == TCDTW_LB_PC && !pc_key_fits(o.Lq, D)) return TCDTW_ERR_INVALID;
+    if (which == TCDTW_LB_TI && !o.ti_top && !lb_ti_rows_supported(W < L - 1 ? W : L - 1))
+        return TCDTW_ERR_UNSUPPORTED;
     if (o.P < 1 || o.Lq < 1 || o.w < 1) return TCDTW_ERR_INVALID;
     if (W > L - 1) W = L - 1;
     if ((double)M * (double)N >= 4.29e9) return TCDTW_ERR_UNSUPPORTED;
@@ -891,7 +897,9 @@ int tcdtw_lower_bounds(const float *q, int64_t M, const float *c, int64_t N, int
         if (e == cudaSuccess) e = cudaMalloc(&aux1, sizeof(float) * M * L);
         if (e == cudaSuccess) e = cudaMalloc(&aux2, sizeof(float) * M * L);
         if (e == cudaSuccess) e = launch_query_dq(q, M, L, D, aux1, aux2, s);
-        if (e == cudaSuccess) e = launch_lb_ti_list(pl, aux1, aux2, o.P, bsf, rho, -1.0f, nullptr, P, sms, s);
+        if (e == cudaSuccess)
+            e = o.ti_top ? launch_lb_ti_list(pl, aux1, aux2, o.P, bsf, rho, -1.0f, nullptr, P, sms, s)
+                         : launch_lb_ti_rows_list(pl, aux1, aux2, o.P, bsf, rho, -1.0f, nullptr, P, sms, s);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     rc = cuda_err(e);

@@ -154,6 +154,7 @@ void tcdtw_default_opts(tcdtw_opts *o) {
     o->use_graph = 1;
     o->select = 1;
     o->use_rev = 0;
+    o->ti_top = 1;
 }
 
 const char *tcdtw_strerror(int code) {

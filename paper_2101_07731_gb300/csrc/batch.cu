@@ -862,6 +862,7 @@ int tcdtw_batch_nn(const tcdtw_dataset *sets, int32_t nsets, const tcdtw_opts *o
     if (opts) o = *opts; else tcdtw_default_opts(&o);
     if (o.P < 1 || o.Lq < 1 || o.w < 1 || o.seed_s < 1 || o.seed_s > 8) return TCDTW_ERR_INVALID;
     o.use_rev = 0;  // the candidate-side bound needs per-set candidate envelopes: not batched
+    o.ti_top = 1;   // the batched cascade evaluates LB_TI in its TIP_TOP form
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<int> mk, other;
     for (int32_t k = 0; k < nsets; ++k) {

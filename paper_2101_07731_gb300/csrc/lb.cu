@@ -323,6 +323,39 @@ __global__ void __launch_bounds__(128) k_lb_ti_list(PairListArgs a, const float 
     if (lane == 0 && pruned && stat_pruned) atomicAdd(stat_pruned, pruned);
 }
 
+// LB_TI without the exact window top (basic / TIP variants; lb_ti_rows_pair), one warp
+// per listed pair, same gate and bookkeeping as k_lb_ti_list.
+template <int DMAX, int NS>
+__global__ void __launch_bounds__(128) k_lb_ti_rows_list(PairListArgs a, const float *__restrict__ dq_lo,
+                                                         const float *__restrict__ dq_hi, int P,
+                                                         const unsigned long long *bsf, float rho, float e_gate,
+                                                         unsigned long long *stat_pruned) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t n_entries = a.count ? (int64_t)*a.count : a.n_static;
+    unsigned long long pruned = 0;
+    for (int64_t e = warp; e < n_entries; e += nwarps) {
+        const uint32_t pid = a.pairs[e];
+        if (pid == 0xffffffffu) continue;
+        const float cur = a.lb[e];
+        if (!(cur < TC_INF)) continue;
+        const int64_t m = pid / (uint64_t)a.N, n = pid - m * a.N;
+        const unsigned long long key = ld_volatile_u64(bsf + m);
+        if (cur > prune_threshold(key, rho)) continue;  // dropped (and counted) by the DTW stage
+        if (!(cur > e_gate * best_dist(key))) continue;
+        const float bound = lb_ti_rows_pair<DMAX, NS>(a.C + (size_t)n * a.L * a.D, a.Q + (size_t)m * a.L * a.D,
+                                                      dq_lo + (size_t)m * a.L, dq_hi + (size_t)m * a.L, a.L, a.D,
+                                                      a.W, P);
+        const bool dropped = __shfl_sync(0xffffffffu, bound > prune_threshold(ld_volatile_u64(bsf + m), rho), 0);
+        if (lane == 0) {
+            if (dropped) { a.lb[e] = TC_INF; ++pruned; }
+            else a.lb[e] = fmaxf(cur, bound);
+        }
+    }
+    if (lane == 0 && pruned && stat_pruned) atomicAdd(stat_pruned, pruned);
+}
+
 #define TC_DMAX_DISPATCH(D, CALL) \
     do {                          \
         if ((D) <= 8) { CALL(8); }        \
@@ -355,6 +388,30 @@ cudaError_t launch_lb_ti_list(const PairListArgs &a, const float *dq_lo, const f
 #define TC_TI_CALL(DM) k_lb_ti_list<DM><<<blocks, 128, 0, s>>>(a, dq_lo, dq_hi, P, bsf, rho, e_gate, stat_pruned)
     TC_DMAX_DISPATCH(a.D, TC_TI_CALL); note_launch();
 #undef TC_TI_CALL
+    return cudaGetLastError();
+}
+
+bool lb_ti_rows_supported(int W) { return W <= 127; }
+
+cudaError_t launch_lb_ti_rows_list(const PairListArgs &a, const float *dq_lo, const float *dq_hi, int P,
+                                   const unsigned long long *bsf, float rho, float e_gate,
+                                   unsigned long long *stat_pruned, int64_t n_hint, int sms, cudaStream_t s) {
+    if (!lb_ti_rows_supported(a.W)) return cudaErrorInvalidValue;
+    const int blocks = list_blocks(n_hint, sms);
+    const int w2 = 2 * a.W + 1;
+#define TC_TIR_NS(DM, NSV) \
+    k_lb_ti_rows_list<DM, NSV><<<blocks, 128, 0, s>>>(a, dq_lo, dq_hi, P, bsf, rho, e_gate, stat_pruned)
+#define TC_TIR_CALL(DM)                          \
+    do {                                         \
+        if (w2 <= 32) TC_TIR_NS(DM, 1);          \
+        else if (w2 <= 64) TC_TIR_NS(DM, 2);     \
+        else if (w2 <= 128) TC_TIR_NS(DM, 4);    \
+        else TC_TIR_NS(DM, 8);                   \
+    } while (0)
+    TC_DMAX_DISPATCH(a.D, TC_TIR_CALL);
+    note_launch();
+#undef TC_TIR_CALL
+#undef TC_TIR_NS
     return cudaGetLastError();
 }
 

@@ -359,4 +359,117 @@ __device__ __forceinline__ bool lb_ti_pair(const float *__restrict__ c, const fl
     return false;
 }
 
+// |a - b| of two candidate points as an interval (both from global memory).
+template <int DMAX>
+__device__ __forceinline__ void point_interval(const float *__restrict__ a, const float *__restrict__ b, int D, float *lo,
+                                               float *hi) {
+    float sl = 0.f, sh = 0.f;
+#pragma unroll
+    for (int p = 0; p < DMAX; ++p) {
+        if (p < D) {
+            const float x = __ldg(a + p), y = __ldg(b + p);
+            const float dl = fmaxf(__fsub_rd(x, y), __fsub_rd(y, x));
+            const float dh = fmaxf(__fsub_ru(x, y), __fsub_ru(y, x));
+            sl = __fmaf_rd(dl, dl, sl);
+            sh = __fmaf_ru(dh, dh, sh);
+        }
+    }
+    *lo = __fsqrt_rd(sl);
+    *hi = __fsqrt_ru(sh);
+}
+
+// LB_TI without the exact window top (Section 4.2: the basic LB_TI when P >= L, LB_TIP
+// otherwise): the top c_{i+W} of a non-periodic row's window comes from the candidate-
+// side triangle with c_{i+W-1} (Eqs. (bt_lb_ir), (bt_ub_ir)), which chains consecutive
+// columns of the same row, so the pair is swept row by row instead of one lane per
+// column.  The warp holds row i's window by offset k = j - i + W in [0, 2W]: lane l,
+// slot s holds k = l + 32 s (NS slots, 32 NS >= 2W + 1).  Between rows the window
+// shifts down one offset (shuffles); the column leaving at the bottom adds its minimum
+// squared (rounded down).  Per row: i mod P == 0 -> every point exact; otherwise the
+// query-side recursion with [dq_lo, dq_hi] for k < 2W, then the top from offset 2W-1's
+// (Lb, Ub) and [dc_lo, dc_hi] = |c_{j-1} - c_j| (exact when W = 0: no neighbour in the
+// window).  Same rounding directions as lb_ti_pair.  Returns the bound (every lane).
+template <int DMAX, int NS>
+__device__ __forceinline__ float lb_ti_rows_pair(const float *__restrict__ c, const float *__restrict__ q,
+                                                 const float *__restrict__ dql, const float *__restrict__ dqh, int L,
+                                                 int D, int W, int P) {
+    const int lane = threadIdx.x & 31;
+    const float INF = TC_INF;
+    float lb[NS], ub[NS], mn[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) { lb[s] = INF; ub[s] = INF; mn[s] = INF; }
+    float acc = 0.f;
+    const int kt = 2 * W;  // offset of the window top
+    for (int i = 0; i < L; ++i) {
+        if (i > 0) {
+            // the column leaving the window: offset 0 of row i-1, column i-1-W
+            if (lane == 0 && i - 1 - W >= 0) acc = __fmaf_rd(mn[0], mn[0], acc);
+            float nl[NS], nu[NS], nm[NS];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const float dl = __shfl_down_sync(0xffffffffu, lb[s], 1);
+                const float du = __shfl_down_sync(0xffffffffu, ub[s], 1);
+                const float dm = __shfl_down_sync(0xffffffffu, mn[s], 1);
+                const float wl = __shfl_sync(0xffffffffu, s + 1 < NS ? lb[s + 1 < NS ? s + 1 : s] : INF, 0);
+                const float wu = __shfl_sync(0xffffffffu, s + 1 < NS ? ub[s + 1 < NS ? s + 1 : s] : INF, 0);
+                const float wm = __shfl_sync(0xffffffffu, s + 1 < NS ? mn[s + 1 < NS ? s + 1 : s] : INF, 0);
+                nl[s] = lane == 31 ? wl : dl;
+                nu[s] = lane == 31 ? wu : du;
+                nm[s] = lane == 31 ? wm : dm;
+            }
+#pragma unroll
+            for (int s = 0; s < NS; ++s) { lb[s] = nl[s]; ub[s] = nu[s]; mn[s] = nm[s]; }
+        }
+        const bool exact_row = (i % P) == 0;
+        const float dl = i > 0 ? __ldg(dql + i) : 0.f, dh = i > 0 ? __ldg(dqh + i) : 0.f;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const int k = lane + 32 * s, j = i - W + k;
+            if (k > kt || j < 0 || j >= L) continue;
+            if (exact_row || W == 0) {
+                float x[DMAX];
+#pragma unroll
+                for (int p = 0; p < DMAX; ++p) x[p] = p < D ? __ldg(c + (size_t)j * D + p) : 0.f;
+                float lo, hi;
+                exact_interval<DMAX>(q + (size_t)i * D, x, D, &lo, &hi);
+                lb[s] = lo;
+                ub[s] = hi;
+                mn[s] = k == kt ? lo : fminf(mn[s], lo);
+            } else if (k < kt) {
+                const float nl = fmaxf(fmaxf(__fsub_rd(lb[s], dh), __fsub_rd(dl, ub[s])), 0.f);
+                ub[s] = __fadd_ru(ub[s], dh);
+                lb[s] = nl;
+                mn[s] = fminf(mn[s], nl);
+            }
+        }
+        if (!exact_row && W > 0 && i + W < L) {
+            // the top from its left neighbour in this row (offset kt - 1)
+            const int sl = (kt - 1) >> 5, ll = (kt - 1) & 31, st = kt >> 5, lt = kt & 31;
+            float nbl = INF, nbu = INF;
+#pragma unroll
+            for (int s = 0; s < NS; ++s)
+                if (s == sl) { nbl = lb[s]; nbu = ub[s]; }
+            nbl = __shfl_sync(0xffffffffu, nbl, ll);
+            nbu = __shfl_sync(0xffffffffu, nbu, ll);
+            if (lane == lt) {
+                const int j = i + W;
+                float dcl, dch;
+                point_interval<DMAX>(c + (size_t)(j - 1) * D, c + (size_t)j * D, D, &dcl, &dch);
+                const float tl = fmaxf(fmaxf(__fsub_rd(nbl, dch), __fsub_rd(dcl, nbu)), 0.f);
+                const float tu = __fadd_ru(nbu, dch);
+#pragma unroll
+                for (int s = 0; s < NS; ++s)
+                    if (s == st) { lb[s] = tl; ub[s] = tu; mn[s] = tl; }
+            }
+        }
+    }
+    // the columns still in the last row's window
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const int k = lane + 32 * s, j = L - 1 - W + k;
+        if (k <= kt && j >= 0 && j < L) acc = __fmaf_rd(mn[s], mn[s], acc);
+    }
+    return warp_sum_rd(acc);
+}
+
 }  // namespace tc

@@ -89,6 +89,11 @@ struct PairListArgs {
 cudaError_t launch_lb_pc_list(const PairListArgs &a, const float *boxes, const int32_t *counts, int K, int w,
                               const unsigned long long *bsf, float rho, float e_gate, unsigned long long *stat_pruned,
                               int64_t n_hint, int sms, cudaStream_t s);
+// LB_TI without the exact window top (basic when P >= L, TIP otherwise): W <= 127
+bool lb_ti_rows_supported(int W);
+cudaError_t launch_lb_ti_rows_list(const PairListArgs &a, const float *dq_lo, const float *dq_hi, int P,
+                                   const unsigned long long *bsf, float rho, float e_gate,
+                                   unsigned long long *stat_pruned, int64_t n_hint, int sms, cudaStream_t s);
 // candidate-side LB_MV of listed pairs (bsf == null: threshold +inf, every bound kept)
 cudaError_t launch_lb_rev_list(const PairListArgs &a, const float *Uc, const float *Lc, const unsigned long long *bsf,
                                float rho, unsigned long long *stat_pruned, int64_t n_hint, int sms, cudaStream_t s);

@@ -156,6 +156,61 @@ def test_lower_bounds_candidate_side_lb_mv(M, N, L, D, W):
             assert out[m, n] <= O.dtw(Q[m], Cn[n], W) * (1 + 1e-12) + 1e-30
 
 
+def _ti_chain_tol(q, c):
+    """Closeness bar of the FP32 triangle recursions without periodic exact rows: every
+    step rounds Ub up and Lb down (4 roundings of at most 2^-24 relative), a chain is at
+    most L steps long, and Lb = dc - Ub can cancel, so a column minimum may sit up to
+    4 L 2^-24 Umax below its FP64 value, Umax bounding every Ub (the sum of all neighbour
+    distances of both series plus the largest point distance).  Summed over the L
+    squared minima (m <= Umax): 2 L Umax err + L err^2."""
+    q, c = q.astype(np.float64), c.astype(np.float64)
+    L = len(q)
+    umax = (np.linalg.norm(np.diff(q, axis=0), axis=1).sum() + np.linalg.norm(np.diff(c, axis=0), axis=1).sum()
+            + np.linalg.norm(q[:, None, :] - c[None, :, :], axis=2).max())
+    err = 4.0 * L * 2.0 ** -24 * umax
+    return 2.0 * L * umax * err + L * err * err
+
+
+@pytest.mark.parametrize("L,D,W", [(40, 3, 0), (48, 1, 1), (64, 3, 6), (129, 5, 26), (70, 8, 60), (90, 2, 100),
+                                   (35, 33, 7)])
+@pytest.mark.parametrize("P,top", [(1000, 0), (5, 0), (1000, 1)])
+def test_lower_bounds_lb_ti_variants(L, D, W, P, top):
+    # basic LB_TI (P >= L, window tops from the candidate-side triangle), LB_TIP (P = 5)
+    # and LB_TI_TOP (exact tops, P >= L) against the oracle's variants
+    Q, Cn = _set("proto_warp", 3, 9, L, D, 19)
+    out = tc.lower_bounds(_gpu(Q), _gpu(Cn), W, which=tc.LB_TI, P=P, ti_top=top).cpu().numpy().astype(np.float64)
+    for m in range(3):
+        for n in range(9):
+            ref = O.lb_ti_var(Q[m], Cn[n], W, P, top)
+            g = out[m, n]
+            assert g <= ref * (1 + 1e-12) + 1e-30, (m, n, g, ref)
+            assert g >= ref - _ti_chain_tol(Q[m], Cn[n]), (m, n, g, ref)
+            if top == 1:
+                assert g >= ref * (1 - _lb_rtol(L, D)) - 1e-6, (m, n, g, ref)
+
+
+@pytest.mark.parametrize("L,W", [(3, 1), (40, 0), (40, 3), (129, 26), (96, 60), (150, 100)])
+def test_lower_bounds_lb_ti_variants_exact_on_small_integers(L, W):
+    # D = 1 and small integer values: every distance, neighbour distance and recursion
+    # step is an exact integer in FP32 (a square root of a perfect square is exact),
+    # so each variant must equal the oracle exactly, however long its triangle chains
+    rng = np.random.default_rng(L + W)
+    if L == 3:  # the hand-worked example (tests/golden/ti_variants_hand.txt)
+        Q = np.array([[[0.], [1.], [2.]]], np.float32)
+        Cn = np.array([[[0.], [0.], [-5.]]], np.float32)
+    else:
+        Q = np.clip(np.cumsum(rng.integers(-2, 3, (3, L, 1)), axis=1), -60, 60).astype(np.float32)
+        Cn = (np.clip(np.cumsum(rng.integers(-3, 4, (5, L, 1)), axis=1), -40, 40) + 25).astype(np.float32)
+    for P, top in ((1000, 0), (2, 0), (5, 0), (1000, 1), (5, 1)):
+        out = tc.lower_bounds(_gpu(Q), _gpu(Cn), W, which=tc.LB_TI, P=P, ti_top=top).cpu().numpy()
+        for m in range(len(Q)):
+            for n in range(len(Cn)):
+                assert float(out[m, n]) == O.lb_ti_var(Q[m], Cn[n], W, P, top), (P, top, m, n)
+    if L == 3:
+        assert [float(tc.lower_bounds(_gpu(Q), _gpu(Cn), 1, which=tc.LB_TI, P=P, ti_top=t).item())
+                for P, t in ((3, 0), (3, 1), (2, 0), (2, 1))] == [9.0, 25.0, 16.0, 36.0]
+
+
 def test_compact_bit_exact():
     rng = np.random.default_rng(0)
     lb = rng.random((7, 1000)).astype(np.float32)
@@ -230,6 +285,14 @@ def test_nn_candidate_side_bound_keeps_answers():
     Q2, C2 = _set("random_walk", 12, 800, 64, 2, 34)
     _, _, st2 = _check_nn(Q2, C2, 6, 4, use_rev=1, select=0, use_pc=0, use_ti=0)
     assert st2["pruned_rev"] > 0
+
+
+@pytest.mark.parametrize("P", [5, 1000])
+def test_nn_lb_ti_without_exact_tops_keeps_answers(P):
+    # LB_TIP (P = 5) and the basic LB_TI (P >= L) in the cascade, on every survivor
+    Q, Cn = _set("proto_warp", 20, 900, 72, 3, 35, n_proto=6)
+    _, _, st = _check_nn(Q, Cn, 7, 8, use_pc=0, use_ti=1, ti_top=0, P=P, e_ti=0.0, select=0)
+    assert st["pruned_ti"] >= 0
 
 
 def test_nn_tc_dtw_selection_keeps_answers():
