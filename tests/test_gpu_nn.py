@@ -295,6 +295,30 @@ def test_nn_lb_ti_without_exact_tops_keeps_answers(P):
     assert st["pruned_ti"] >= 0
 
 
+def test_sharded_index_single_rank_nccl():
+    # the candidate-sharded search through a real process group (NCCL, one rank: the
+    # shard is the whole set, offset 0) equals the plain index
+    import os
+    import socket
+    import torch.distributed as dist
+    from paper_2101_07731_gb300.sharded import ShardedIndex
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("nccl", rank=0, world_size=1, device_id=torch.device("cuda:0"))
+    try:
+        Q, Cn = _set("proto_warp", 10, 400, 48, 3, 37)
+        sh = ShardedIndex(_gpu(Cn), 0, 5, 8)
+        gi, gd = sh.nn(_gpu(Q))
+        sh.close()
+        ridx, rdist = O.nn_brute(Q, Cn, 5)
+        assert np.array_equal(gi.cpu().numpy(), ridx)
+        np.testing.assert_allclose(gd.cpu().numpy(), rdist, rtol=DF_RTOL, atol=0)
+    finally:
+        dist.destroy_process_group()
+
+
 def test_nn_tc_dtw_selection_keeps_answers():
     # TC-DTW's data-adaptive bound choice changes which DTWs run, never the answer
     Q, Cn = _set("proto_warp", 40, 2000, 80, 4, 31, n_proto=6)
