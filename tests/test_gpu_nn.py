@@ -130,6 +130,20 @@ def test_lower_bounds_lb_mv_tma_stream(M):
             assert out[m, n] >= ref * (1 - _lb_rtol(L, D)) - 1e-6, (m, n, out[m, n], ref)
 
 
+@pytest.mark.parametrize("M,N,L,D", [(1, 40, 67, 4), (5, 130, 67, 4), (2, 7, 8, 4), (16, 129, 300, 8)])
+def test_lower_bounds_lb_mv_tma_shared_tiles(M, N, L, D):
+    # few candidate tiles: the stream-K split gives each tile several CTAs (N = 40,
+    # E = 268: one tile of 9 chunks over 9 CTAs), whose parts the last one adds up
+    W = 5
+    Q, Cn = _set("proto_warp", M, N, L, D, 26 + M)
+    out = tc.lower_bounds(_gpu(Q), _gpu(Cn), W, which=tc.LB_MV).cpu().numpy().astype(np.float64)
+    for m in range(M):
+        for n in range(N):
+            ref = O.lb_mv(Q[m], Cn[n], W)
+            assert out[m, n] <= ref * (1 + 1e-12) + 1e-30, (m, n, out[m, n], ref)
+            assert out[m, n] >= ref * (1 - _lb_rtol(L, D)) - 1e-6, (m, n, out[m, n], ref)
+
+
 def test_lb_mv_tma_wait_limit_selftest():
     # the consumers' first wait runs out; the launch reports TIMEOUT and the context
     # stays usable for the next call
