@@ -389,6 +389,22 @@ def cpu_oracle_sample(Q, Cn, W, K, target_s):
     return n * passes / t, cores, f"{what} x all {len(Cn)} candidates (pruned FP64 search)", t
 
 
+def cpu_brute_large_sample(nq, nc=64):
+    """FP64 brute force of the largest workload (1,024 x 100,000, L=2,048, D=32, W=102)
+    on the host cores: nq queries (one per core) against the first nc candidates, every
+    pair's DTW, extrapolated to all 100,000 candidates."""
+    import oracle
+    wl = synth.PROTO_1024x100000_L2048
+    Q, C = wl.queries(nq), wl.candidates(nc)
+    t0 = time.perf_counter()
+    oracle.nn_brute(Q, C, wl.W)
+    secs = time.perf_counter() - t0
+    return {"value": nq / (secs * wl.N / nc), "unit": "queries/s", "cores": len(os.sched_getaffinity(0)),
+            "seconds": secs,
+            "sample": f"{nq} queries x the first {nc} candidates of {wl.name}, FP64 DTW of every pair, "
+                      f"extrapolated to all {wl.N} candidates"}
+
+
 def cpu_brute_sample(Q, Cn, W, n):
     import oracle
     t0 = time.perf_counter()
@@ -669,6 +685,8 @@ def run_ours(a):
         nb = max(cores, 4)
         res["cpu_bruteforce"] = {"value": cpu_brute_sample(Qn, Cn, wl.W, nb), "unit": "queries/s", "cores": cores,
                                  "sample": f"{nb} queries x all candidates, FP64 DTW of every pair"}
+        if not a.no_extra:
+            res["cpu_bruteforce_large"] = cpu_brute_large_sample(nb)
     if rank == 0:
         print(json.dumps(res), flush=True)
     if dist is not None:
