@@ -646,10 +646,10 @@ def run_ours(a):
         tot = job_time_ms(tot, dist, dev)
         res["e2e"] = {"value": job_value(world, wl.M, a.steps, tot), "unit": "queries/s",
                       "h2d_bytes_per_step": int(qh.numel() * 4), "d2h_bytes_per_step": int(wl.M * 16)}
-    if not a.no_extra:
+    if not a.no_extra and world == 1:
         res["reverse_lb"] = reverse_lb_leg(tc, cand, q, wl, flush, stream, ms_per_step)
         res["ti_variants"] = ti_variants_leg(tc, cand, q, wl, flush, stream)
-    if not a.no_few:
+    if not a.no_few and world == 1:
         res["few_queries"] = few_queries_leg(tc, cand, q, wl, flush, stream)
     index.close()
 
