@@ -253,8 +253,12 @@ int tcdtw_pc_boxes(const float *q, int64_t M, int32_t L, int32_t D, int32_t W, i
 /* All M*N values of one lower bound (which = TCDTW_LB_*), no abandoning, rounded
  * down so that out[m][n] <= the exact bound <= DTW(q[m], c[n]).
  * q device [M][L][D], c device [N][L][D], out device [M][N] float32.
- * opts supplies P, Lq and w (NULL = defaults); K is the LB_PC cluster cap.
- * Errors: INVALID, NOMEM, CUDA. */
+ * opts supplies P, Lq, w and ti_top (NULL = defaults): TCDTW_LB_TI with ti_top = 0 is
+ * LB_TIP (the basic LB_TI when P >= L); K is the LB_PC cluster cap.
+ * TCDTW_LB_MV_REV computes the candidates' envelopes on the fly (2*N*L*D floats).
+ * Synchronous on `stream`.
+ * Errors: INVALID, NOMEM, CUDA, TIMEOUT (a bounded device wait of the LB_MV stream ran
+ * out), UNSUPPORTED (ti_top = 0 with W > 127). */
 int tcdtw_lower_bounds(const float *q, int64_t M, const float *c, int64_t N, int32_t L, int32_t D,
                        int32_t W, int32_t K, const tcdtw_opts *opts, int32_t which, float *out,
                        void *stream);
