@@ -166,6 +166,7 @@ enum Counter {
     kNumCounters
 };
 enum Scalar { kSurvTotal = 0, kCursorSeed, kCursorSurv, kRefineCount, kRefine64Count, kNumScalars };
+constexpr int kFewQueries = 4;  // query blocks at most this big run their survivors on the seed tile
 
 }  // namespace tc
 
@@ -400,7 +401,13 @@ cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_o
     TC_MARK(6);
     dn.pairs = x->surv; dn.lb = x->surv_lb; dn.count = x->scalars + kSurvTotal; dn.n_static = 0;
     dn.cursor = x->scalars + kCursorSurv; dn.dtw = x->surv_dtw;
-    if ((e = dtw_nn_launch(x->tile, x->blocks_nn, s, dn)) != cudaSuccess) return e;
+    // a block of a few queries leaves too few survivors to fill the GPU: each pair's
+    // sweep latency decides, and the seed tile (fewest rows per lane) is shorter per pair
+    // than the autotuned throughput tile
+    const bool few = Mb_cur <= kFewQueries;
+    dn.G = few ? x->G_seed : x->G;
+    if ((e = dtw_nn_launch(few ? x->tile_seed : x->tile, few ? x->blocks_seed : x->blocks_nn, s, dn)) != cudaSuccess)
+        return e;
     // 7. refine near-ties in FP64 and select
     TC_MARK(7);
     if ((e = launch_refine_select(x->seeds, x->seed_dtw, nullptr, (int64_t)Mb_cur * x->S, N, x->bsf, x->rho_ref,
