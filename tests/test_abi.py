@@ -127,3 +127,30 @@ def test_binding_structs_mirror_the_header():
         names = [re.findall(r"(\w+)\s*$", part)[0] for stmt in body.split(";") if stmt.strip()
                  for part in stmt.split(",")]
         assert names == [n for n, _ in py._fields_], (cname, names)
+
+
+def test_argument_errors_of_the_newer_calls(lib):
+    # every check below returns before any CUDA call (no GPU needed; the dummy
+    # addresses are never dereferenced)
+    import paper_2101_07731_gb300 as tc
+    o = tc.default_opts()
+    assert (o.use_rev, o.ti_top, o.select) == (0, 1, 1)
+    dummy = C.c_void_p(256)
+    f = lib.tcdtw_lower_bounds
+    f.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                  C.POINTER(tc.Opts), C.c_int32, C.c_void_p, C.c_void_p]
+    for which in (-1, 4):
+        assert f(dummy, 1, dummy, 1, 30, 2, 3, 4, C.byref(o), which, dummy, None) == tc.ERR_INVALID
+    # the row-sweep LB_TI variants hold the window in up to 8 x 32 lanes: W <= 127
+    o2 = tc.default_opts(ti_top=0)
+    assert f(dummy, 1, dummy, 1, 300, 2, 200, 4, C.byref(o2), tc.LB_TI, dummy, None) == tc.ERR_UNSUPPORTED
+    build = lib.tcdtw_build
+    build.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.POINTER(tc.Opts),
+                      C.c_void_p, C.POINTER(C.c_void_p)]
+    h = C.c_void_p()
+    assert build(dummy, 1, 300, 2, 200, 4, C.byref(o2), None, C.byref(h)) == tc.ERR_UNSUPPORTED
+    lib.tcdtw_lb_mv_selftest_timeout.argtypes = [C.c_int64, C.c_void_p]
+    lib.tcdtw_batch_selftest_timeout.argtypes = [C.c_int64, C.c_void_p]
+    assert lib.tcdtw_lb_mv_selftest_timeout(0, None) == tc.ERR_INVALID
+    assert lib.tcdtw_lb_mv_selftest_timeout(10_000_001, None) == tc.ERR_INVALID
+    assert lib.tcdtw_batch_selftest_timeout(0, None) == tc.ERR_INVALID
