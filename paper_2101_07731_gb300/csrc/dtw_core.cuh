@@ -419,8 +419,9 @@ struct NnHooks {
 // Entries e in [0, count): pair (m = pairs[e] / N, n = pairs[e] % N); lb[e] is the
 // entry's best lower bound (+inf = already dropped; lb == null: 0).  Writes dtw[e]
 // (FP32 DTW, or +inf when pruned / abandoned) and lowers bsf[m].
+// R = 16 with up to 5 dimensions: capped at 128 registers (4 CTAs, 16 warps per SM)
 template <int R, int DM>
-__global__ void __launch_bounds__(128) k_dtw_nn(const float *__restrict__ Q, const float *__restrict__ Cand, int L,
+__global__ void __launch_bounds__(128, (R >= 16 && DM <= 5) ? 4 : 1) k_dtw_nn(const float *__restrict__ Q, const float *__restrict__ Cand, int L,
                                                  int D, int W, int G, int64_t N, const uint32_t *__restrict__ pairs,
                                                  const float *__restrict__ lb, const int32_t *__restrict__ count,
                                                  int n_static, int *__restrict__ cursor, unsigned long long *bsf,
