@@ -17,6 +17,8 @@
 #include <string.h>
 
 #include <algorithm>
+
+#include <nvtx3/nvToolsExt.h>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -301,8 +303,16 @@ int alloc_index(tcdtw_index *x) {
 }
 
 // Stage boundary k of the current block (profiling only).
+// With profiling on, every stage is also an NVTX range on the calling thread (seen by
+// Nsight Systems when it is attached; the calls do nothing otherwise).
+const char *const kStageRange[TCDTW_NUM_STAGES] = {"tcdtw check",   "tcdtw prep",    "tcdtw lb_mv",
+                                                   "tcdtw seed",    "tcdtw compact", "tcdtw cascade",
+                                                   "tcdtw dtw",     "tcdtw refine"};
+
 cudaError_t mark(tcdtw_index *x, int k, cudaStream_t s) {
     if (!x->profile) return cudaSuccess;
+    if (k > 0) nvtxRangePop();
+    if (k < TCDTW_NUM_STAGES) nvtxRangePushA(kStageRange[k]);
     const size_t slot = (size_t)x->marks_used;
     if (slot >= x->events.size()) {
         cudaEvent_t ev;
