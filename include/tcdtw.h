@@ -68,8 +68,12 @@ typedef struct tcdtw_index tcdtw_index; /* opaque; created by tcdtw_build */
  *  no_prune  1 = the "default windowed DTW without lower bounds" the paper measures
  *          its speedups against (Section 7.2): the full DTW of every pair, no bound,
  *          no abandoning; the answer is the same (0).
- *  use_graph  1 = tcdtw_nn replays a captured CUDA graph of its kernel sequence when
- *          called again with the same (q, M, idx, dist) (1).
+ *  use_graph  1 = a tcdtw_nn call of at most one query block (M <= qblock) runs on the
+ *          index's own query and answer buffers: it copies the queries in, runs the
+ *          kernel sequence -- eagerly the first time a given M is seen, then as a CUDA
+ *          graph captured on the second call with that M and replayed afterwards --
+ *          and copies the answers out, all on `stream`.  The caller may pass different
+ *          buffers on every call (1).
  *  select  1 = TC-DTW's data-adaptive choice (Section 6, "TC-DTW"; parameter ranges of
  *          Section 7.1): the first tcdtw_nn call on an index times, on up to 32 of
  *          its queries, LB_MV alone, LB_TI with e_ti in {0.05, 0.1, 0.2} and LB_PC with

@@ -239,8 +239,8 @@ class Index:
     def nn(self, q: torch.Tensor, stats: bool = False, out=None):
         """(idx int64 [M], dist float64 [M]) of each query's nearest candidate;
         with ``stats=True`` also the search counters (synchronises).  ``out`` =
-        (idx, dist) reuses caller buffers; calls repeated with the same query and
-        output buffers replay a captured CUDA graph."""
+        (idx, dist) reuses caller buffers.  Calls of up to one query block with a
+        query count seen before replay a captured CUDA graph, whatever the buffers."""
         q = _series(q, "q")
         if q.shape[1:] != (self.L, self.D):
             raise ValueError("query shape must be [M][L][D] with the index's L and D")

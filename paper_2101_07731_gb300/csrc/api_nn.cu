@@ -211,12 +211,15 @@ struct tcdtw_index {
     int marks_used = 0;
     double stage_ms[TCDTW_NUM_STAGES] = {0};
     int64_t stage_blocks = 0;
-    // CUDA graphs of the per-call kernel sequence, keyed by the call's pointers
+    // CUDA graphs of the per-call kernel sequence of single-block calls, keyed by the
+    // number of queries: the graph reads the queries from qbuf and writes the answers
+    // to idx_buf / dist_buf, and each call copies in and out around it on its stream,
+    // so replay does not depend on where the caller's buffers are
+    float *qbuf = nullptr;
+    int64_t *idx_buf = nullptr;
+    double *dist_buf = nullptr;
     struct GraphEntry {
-        const float *q;
         int64_t M;
-        int64_t *idx;
-        double *dist;
         int seen;                      // eager calls made with this key
         cudaGraphExec_t exec;          // null until captured
         unsigned long long last_use;
@@ -242,7 +245,7 @@ void free_index(tcdtw_index *x) {
                     x->refine, x->seed_dtw, x->surv_lb, x->surv_dtw, x->refine_d64, x->row_counts,
                     x->row_offsets, x->scalars, x->bsf, x->best64, x->best_idx, x->counters, x->status,
                     x->refine64, x->refine64_d64, x->amb, x->bestdf, x->best_idx_df, x->mv_ws, x->mv_cnt,
-                    x->Uc, x->Lc};
+                    x->Uc, x->Lc, x->qbuf, x->idx_buf, x->dist_buf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete x;
@@ -299,6 +302,11 @@ int alloc_index(tcdtw_index *x) {
     TC_TRY(dalloc(&x->mv_cnt, (size_t)kMvTileCounters));
     TC_TRY(cudaMemset(x->mv_cnt, 0, sizeof(int32_t) * kMvTileCounters));
     TC_TRY(cudaMemset(x->counters, 0, sizeof(unsigned long long) * kNumCounters));
+    if (x->opts.use_graph) {
+        TC_TRY(dalloc(&x->qbuf, (size_t)Mb * L * D));
+        TC_TRY(dalloc(&x->idx_buf, (size_t)Mb));
+        TC_TRY(dalloc(&x->dist_buf, (size_t)Mb));
+    }
     return TCDTW_OK;
 }
 
@@ -513,24 +521,33 @@ cudaError_t select_cascade(tcdtw_index *x, const float *q, int64_t M, cudaStream
     return e;
 }
 
-// All query blocks of one call.  With use_graph, a key (q, M, idx, dist) seen once
-// before is captured into a CUDA graph (on an internal stream) and replayed on s;
-// the first call of a key runs eagerly so that any one-time setup (function
-// attributes, lazy module loading) happens outside capture.
+// All query blocks of one call.  With use_graph, a call of at most one block runs on
+// the index's own query and answer buffers (copied in and out on s, outside the graph)
+// and a query count seen once before is captured into a CUDA graph (on an internal
+// stream) and replayed on s; the first call of a count runs eagerly so that any
+// one-time setup (function attributes, lazy module loading) happens outside capture.
+// Calls of several blocks run eagerly (each block is a long search already).
 cudaError_t run_all_blocks(tcdtw_index *x, const float *q, int64_t M, int64_t *idx, double *dist, cudaStream_t s) {
     const int64_t E = (int64_t)x->L * x->D;
-    auto eager = [&](cudaStream_t st) -> cudaError_t {
+    auto eager = [&](const float *qq, int64_t *ii, double *dd, cudaStream_t st) -> cudaError_t {
         for (int64_t m0 = 0; m0 < M; m0 += x->Mb) {
             const int Mb_cur = (int)((M - m0) < x->Mb ? (M - m0) : x->Mb);
-            cudaError_t e = run_block(x, q + m0 * E, Mb_cur, idx + m0, dist + m0, st);
+            cudaError_t e = run_block(x, qq + m0 * E, Mb_cur, ii + m0, dd + m0, st);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
     };
-    if (!x->opts.use_graph) return eager(s);
+    if (!x->opts.use_graph || M > x->Mb || !x->qbuf) return eager(q, idx, dist, s);
+    cudaError_t e = cudaMemcpyAsync(x->qbuf, q, sizeof(float) * (size_t)(M * E), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    auto copy_out = [&]() -> cudaError_t {
+        cudaError_t e2 = cudaMemcpyAsync(idx, x->idx_buf, sizeof(int64_t) * (size_t)M, cudaMemcpyDeviceToDevice, s);
+        if (e2 != cudaSuccess) return e2;
+        return cudaMemcpyAsync(dist, x->dist_buf, sizeof(double) * (size_t)M, cudaMemcpyDeviceToDevice, s);
+    };
     tcdtw_index::GraphEntry *ent = nullptr;
     for (auto &g : x->graphs)
-        if (g.q == q && g.M == M && g.idx == idx && g.dist == dist && g.profiled == x->profile) ent = &g;
+        if (g.M == M && g.profiled == x->profile) ent = &g;
     if (!ent) {
         if (x->graphs.size() >= 8) {  // drop the least recently used key
             size_t lru = 0;
@@ -539,16 +556,16 @@ cudaError_t run_all_blocks(tcdtw_index *x, const float *q, int64_t M, int64_t *i
             if (x->graphs[lru].exec) cudaGraphExecDestroy(x->graphs[lru].exec);
             x->graphs.erase(x->graphs.begin() + lru);
         }
-        x->graphs.push_back({q, M, idx, dist, 0, nullptr, 0, 0, x->profile, 0});
+        x->graphs.push_back({M, 0, nullptr, 0, 0, x->profile, 0});
         ent = &x->graphs.back();
     }
     ent->last_use = ++x->graph_clock;
     if (!ent->exec && ent->seen == 0) {
         ent->seen = 1;
-        return eager(s);
+        if ((e = eager(x->qbuf, x->idx_buf, x->dist_buf, s)) != cudaSuccess) return e;
+        return copy_out();
     }
     if (!ent->exec) {
-        cudaError_t e;
         if (!x->cap_stream && (e = cudaStreamCreateWithFlags(&x->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
             return e;
         // order the capture stream after the caller's prior work on s
@@ -557,7 +574,7 @@ cudaError_t run_all_blocks(tcdtw_index *x, const float *q, int64_t M, int64_t *i
         x->marks_used = 0;
         x->capturing = true;
         const uint64_t k0 = tcdtw_kernel_launches();
-        cudaError_t run = eager(x->cap_stream);
+        cudaError_t run = eager(x->qbuf, x->idx_buf, x->dist_buf, x->cap_stream);
         ent->kernels = (int)(tcdtw_kernel_launches() - k0);
         note_launches(-(int64_t)ent->kernels);  // captured, not launched yet
         x->capturing = false;
@@ -572,7 +589,8 @@ cudaError_t run_all_blocks(tcdtw_index *x, const float *q, int64_t M, int64_t *i
     }
     x->marks_used = ent->marks;  // the graph records these profiling events
     note_launches(ent->kernels);   // kernels the replay launches
-    return cudaGraphLaunch(ent->exec, s);
+    if ((e = cudaGraphLaunch(ent->exec, s)) != cudaSuccess) return e;
+    return copy_out();
 }
 
 }  // namespace

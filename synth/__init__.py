@@ -12,10 +12,15 @@ used instead:
   uniformly, applies a random monotone time warp (local stretch factors
   U(0.9, 1.1), cumulative sum rescaled onto [0, L-1], linear interpolation per
   dimension) and adds N(0, sigma^2) noise.
+* ``circle`` (D = 2): one turn of a circle, radius U(0.5, 1.5), phase U(-0.3, 0.3),
+  plus N(0, sigma^2) noise.  Smooth series whose query envelopes are loose boxes
+  around an arc, so that the point-based bounds (LB_TI, LB_PC) are much tighter
+  than LB_MV -- the situation of the paper's trajectory datasets.
 
-Every series is then z-normalised per dimension (a constant dimension becomes all
-zeros), as the paper normalises its data and replaces NA values by zero (Section
-7.1).
+Every ``random_walk`` and ``proto_warp`` series is then z-normalised per dimension
+(a constant dimension becomes all zeros), as the paper normalises its data and
+replaces NA values by zero (Section 7.1); ``circle`` series are not (that would
+give every circle the same radius).
 
 Series are generated in chunks of ``CHUNK`` with an independent PCG64 stream per
 chunk (``SeedSequence([seed, role, chunk])``), so any subset of a large set can be
@@ -87,10 +92,20 @@ def _proto_warp_chunk(rng: np.random.Generator, protos: np.ndarray, n: int, sigm
     return x
 
 
+def _circle_chunk(rng: np.random.Generator, n: int, L: int, D: int, sigma: float) -> np.ndarray:
+    if D != 2:
+        raise ValueError("circle series have D = 2")
+    t = np.linspace(0.0, 2.0 * np.pi, L)
+    r = rng.uniform(0.5, 1.5, size=(n, 1))
+    ph = rng.uniform(-0.3, 0.3, size=(n, 1))
+    x = np.stack([r * np.cos(t + ph), r * np.sin(t + ph)], axis=-1)
+    return x + sigma * rng.standard_normal((n, L, D))
+
+
 @dataclasses.dataclass(frozen=True)
 class SeriesSpec:
     """Recipe for one set of series (candidates or queries)."""
-    kind: str            # "random_walk" | "proto_warp"
+    kind: str            # "random_walk" | "proto_warp" | "circle"
     L: int
     D: int
     seed: int
@@ -116,9 +131,11 @@ def generate(spec: SeriesSpec, role: int, count: int, start: int = 0) -> np.ndar
             x = _random_walk_chunk(rng, CHUNK, L, D)
         elif spec.kind == "proto_warp":
             x = _proto_warp_chunk(rng, protos, CHUNK, spec.sigma)
+        elif spec.kind == "circle":
+            x = _circle_chunk(rng, CHUNK, L, D, spec.sigma)
         else:
             raise ValueError(f"unknown kind {spec.kind!r}")
-        x = _znorm(x).astype(np.float32)
+        x = (x if spec.kind == "circle" else _znorm(x)).astype(np.float32)
         lo = max(start, c * CHUNK) - c * CHUNK
         hi = min(start + count, (c + 1) * CHUNK) - c * CHUNK
         dst = max(start, c * CHUNK) - start

@@ -3,11 +3,14 @@ L = 2,048, D = 32, W = 102 (5% of L), 100 prototypes, sigma = 0.2, LB_PC K = 64
 (26 GB of candidates resident in HBM), in the configuration of the library's
 defaults.
 
-The oracle cannot search 1e8 pairs of 4e5 cells each, so the checks are ones it
-can compute one by one or that hold at any size:
-  * for sampled queries, the returned distance is the FP64 DTW of the returned
-    candidate (oracle, 1e-9 relative: the double-float refine's bound);
-  * for those queries, no candidate of a random sample beats the answer (oracle);
+The GPU searches all 1,024 queries once (module fixture).  The oracle's brute force
+over 1e8 pairs of 4e5 cells each is out of reach, so:
+  * for 16 sampled queries, the oracle's pruned search (LB_MV and early abandoning in
+    FP64, pinned equal to brute force by the oracle's own tests) runs over all
+    100,000 candidates: indices must be identical, distances within 1e-9 relative
+    (the double-float refine's bound);
+  * for 6 more sampled queries, the returned distance is the FP64 DTW of the
+    returned candidate and no candidate of a random sample beats it;
   * for a few queries, the pruned search and a search with every bound and every
     abandoning switched off (no_prune: the DTW of all 100,000 pairs) agree exactly;
   * counters: every pair is accounted for, and pruning removed most DTWs.
@@ -69,12 +72,27 @@ def large():
         shm.unlink()
 
 
-def test_nn_proto_1024x100000_L2048_D32_W102_sampled(large):
+@pytest.fixture(scope="module")
+def search(large):
     cand, Qn, host, sample, sample_idx = large
     index = tc.Index(cand, WL.W, WL.K)
     idx, dist, st = index.nn(torch.from_numpy(Qn).to(DEV), stats=True)
     index.close()
-    gi, gd = idx.cpu().numpy(), dist.cpu().numpy()
+    return idx.cpu().numpy(), dist.cpu().numpy(), st
+
+
+def test_nn_large_16_queries_match_oracle_over_all_candidates(large, search):
+    cand, Qn, host, sample, sample_idx = large
+    gi, gd, _ = search
+    qs = np.sort(np.random.default_rng(5).choice(WL.M, size=16, replace=False))
+    ridx, rdist, _ = O.nn_pruned(Qn[qs], host, WL.W, K=WL.K, use_pc=False, use_ti=False)
+    assert np.array_equal(gi[qs], ridx), (qs, gi[qs], ridx)
+    np.testing.assert_allclose(gd[qs], rdist, rtol=1e-9, atol=0)
+
+
+def test_nn_proto_1024x100000_L2048_D32_W102_sampled(large, search):
+    cand, Qn, host, sample, sample_idx = large
+    gi, gd, st = search
     M, N = WL.M, WL.N
     assert st["pairs"] == M * N
     assert st["pruned_mv"] + st["pruned_pc"] + st["pruned_ti"] + st["dtw_started"] == st["pairs"], st

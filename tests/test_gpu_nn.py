@@ -305,8 +305,25 @@ def test_nn_candidate_side_bound_keeps_answers():
 def test_nn_lb_ti_without_exact_tops_keeps_answers(P):
     # LB_TIP (P = 5) and the basic LB_TI (P >= L) in the cascade, on every survivor
     Q, Cn = _set("proto_warp", 20, 900, 72, 3, 35, n_proto=6)
-    _, _, st = _check_nn(Q, Cn, 7, 8, use_pc=0, use_ti=1, ti_top=0, P=P, e_ti=0.0, select=0)
-    assert st["pruned_ti"] >= 0
+    _check_nn(Q, Cn, 7, 8, use_pc=0, use_ti=1, ti_top=0, P=P, e_ti=0.0, select=0)
+
+
+@pytest.mark.parametrize("use_pc,use_ti,ti_top", [(1, 0, 1), (0, 1, 1), (0, 1, 0)])
+def test_nn_tight_bounds_prune_on_smooth_series(use_pc, use_ti, ti_top):
+    """On smooth 2-D circles of different radii the query envelope is a loose box
+    around an arc, so LB_MV lets through pairs that the point-based bounds reject:
+    LB_PC (Section 5), LB_TI in its TIP_TOP form and LB_TIP (Section 4.2, P = 5) each
+    prune pairs inside the GPU pipeline (the oracle's pairwise bounds, evaluated in
+    the pipeline's order on the same data, prune 713, 261 and 260 of 1,534 LB_MV
+    survivors), and the answers stay the oracle's."""
+    spec = synth.SeriesSpec("circle", 96, 2, 51, sigma=0.01)
+    Q, Cn = synth.generate(spec, synth.ROLE_QUERY, 12), synth.generate(spec, synth.ROLE_CAND, 500)
+    _, _, st = _check_nn(Q, Cn, 12, 8, use_pc=use_pc, use_ti=use_ti, ti_top=ti_top, P=5, e_pc=0.0, e_ti=0.0,
+                         select=0)
+    if use_pc:
+        assert st["pruned_pc"] > 0, st
+    if use_ti:
+        assert st["pruned_ti"] > 0, st
 
 
 def test_sharded_index_single_rank_nccl():
@@ -401,18 +418,19 @@ def test_nn_rejects_non_finite():
     assert np.array_equal(idx.cpu().numpy(), ridx)
 
 
-def test_nn_proto_256x20000_L256_D5_W26_sampled():
-    """The full 256 x 20,000 search (L=256, D=5, W=26, K=16); the oracle checks a
-    sample of 24 queries by brute force over all 20,000 candidates."""
+def test_nn_proto_256x20000_L256_D5_W26_all_queries():
+    """The full 256 x 20,000 search (L=256, D=5, W=26, K=16) against the oracle for
+    every query: the oracle's pruned search (LB_MV and early abandoning, pinned equal
+    to brute force) over all 20,000 candidates."""
     wl = synth.PROTO_256x20000_L256
     Q, Cn = wl.queries(), wl.candidates()
     index = tc.Index(_gpu(Cn), wl.W, wl.K)
     idx, dist, st = index.nn(_gpu(Q), stats=True)
+    index.close()
     gi, gd = idx.cpu().numpy(), dist.cpu().numpy()
-    sample = np.random.default_rng(3).choice(wl.M, 24, replace=False)
-    ridx, rdist = O.nn_brute(Q[sample], Cn, wl.W)
-    assert np.array_equal(gi[sample], ridx)
-    np.testing.assert_allclose(gd[sample], rdist, rtol=DF_RTOL, atol=0)
+    ridx, rdist, _ = O.nn_pruned(Q, Cn, wl.W, K=wl.K, use_pc=False, use_ti=False)
+    assert np.array_equal(gi, ridx), np.nonzero(gi != ridx)
+    np.testing.assert_allclose(gd, rdist, rtol=DF_RTOL, atol=0)
     assert st["pruned_mv"] + st["pruned_pc"] + st["pruned_ti"] + st["dtw_started"] == st["pairs"]
     # pruning must avoid most DTWs on this prototype data
     assert st["dtw_started"] < 0.5 * st["pairs"]
@@ -434,4 +452,28 @@ def test_nn_graph_replay_with_new_query_contents():
         ridx, rdist = O.nn_brute(Qn, Cn, 8)
         assert np.array_equal(idx.cpu().numpy(), ridx), rep
         np.testing.assert_allclose(dist.cpu().numpy(), rdist, rtol=DF_RTOL, atol=0)
+    index.close()
+
+
+def test_nn_graph_replay_with_fresh_buffers_every_call():
+    """A caller that allocates new query and answer tensors for every call (the
+    caching allocator hands out alternating addresses) still gets the replayed graph's
+    answers right: the graph runs on the index's own buffers, keyed by the query count."""
+    spec = synth.SeriesSpec("proto_warp", 64, 3, 28, n_proto=5, sigma=0.1)
+    Cn = synth.generate(spec, synth.ROLE_CAND, 700)
+    index = tc.Index(_gpu(Cn), 6, 8)
+    keep = []
+    for rep in range(5):
+        Qn = synth.generate(spec, synth.ROLE_QUERY, 13, start=13 * rep)
+        q = _gpu(Qn)
+        idx, dist = index.nn(q)
+        keep.append((q, idx, dist))                    # keep the buffers alive: new addresses
+        ridx, rdist = O.nn_brute(Qn, Cn, 6)
+        assert np.array_equal(idx.cpu().numpy(), ridx), rep
+        np.testing.assert_allclose(dist.cpu().numpy(), rdist, rtol=DF_RTOL, atol=0)
+    # a different query count gets its own graph; the first one stays valid
+    Qn = synth.generate(spec, synth.ROLE_QUERY, 5, start=200)
+    for _ in range(3):
+        idx, _ = index.nn(_gpu(Qn))
+        assert np.array_equal(idx.cpu().numpy(), O.nn_brute(Qn, Cn, 6)[0])
     index.close()
