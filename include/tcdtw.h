@@ -271,21 +271,24 @@ int tcdtw_lower_bounds(const float *q, int64_t M, const float *c, int64_t N, int
  * tcdtw_lb_mv_noalloc -- the same values as tcdtw_lower_bounds(..., TCDTW_LB_MV, ...)
  * (all M*N LB_MV bounds, rounded down, out device [M][N] float32), but without any
  * device allocation.  The paper has no counterpart: this is a deployment variant.
- * Who needs it: code that runs while a stream is being captured into a CUDA graph
- * (cudaMalloc is not a stream operation and is refused during capture), serving
- * loops that must not stall (cudaMalloc / cudaFree can synchronise the whole device),
- * and processes whose device memory is owned by a caching allocator or a fixed
- * budget, where a raw cudaMalloc can fail although the application has memory.
+ * Who needs it: serving loops that must not stall (cudaMalloc / cudaFree can
+ * synchronise the whole device), and processes whose device memory is owned by a
+ * caching allocator or a fixed budget, where a raw cudaMalloc can fail although the
+ * application has memory to spare.
  * The envelope scratch is a fixed array inside the library (8 MiB: two halves of
  * 2^20 floats); each loaded device keeps it until the process exits.  Limit:
  * 2*ceil(M/2) * ceil32(L*D) <= 2^20, else TCDTW_ERR_UNSUPPORTED (no work is done).
- * The first call on a device resolves the array's device address (set-up, once per
- * device, with that device current): make that first call before any stream capture.
- * Every call uses the same array, and the scratch keeps the last call's contents
- * (each call rewrites every element it reads, so nothing needs clearing): calls whose
+ * The first call on a device resolves the array's device address (set-up, with that
+ * device current; it is resolved again if the device's context has changed, e.g.
+ * after cudaDeviceReset): make that first call before any stream capture.
+ * Every call uses the same array and the scratch keeps the last call's contents;
+ * each call rewrites, before reading them, the envelope values of all its queries
+ * (with odd M the unused half of the last query pair keeps stale values, which feed
+ * only a discarded lane of the computation), so nothing needs clearing.  Calls whose
  * kernels overlap on the GPU (different streams, or different host threads) race on
- * it and must be serialised by the caller.  Asynchronous on `stream`.
- * Errors: INVALID, UNSUPPORTED (too large), CUDA.
+ * the array and must be serialised by the caller.  Asynchronous on `stream`.
+ * Errors (checked in the order of tcdtw_lower_bounds): INVALID, UNSUPPORTED (D > 64,
+ * M*N >= 4.29e9, or beyond the scratch), CUDA.
  */
 int tcdtw_lb_mv_noalloc(const float *q, int64_t M, const float *c, int64_t N, int32_t L, int32_t D, int32_t W,
                         float *out, void *stream);

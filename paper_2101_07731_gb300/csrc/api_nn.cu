@@ -131,7 +131,7 @@ bool autotune_nn_tile(const float *cand, int64_t N, int L, int D, int W, cudaStr
             dn.Q = cand; dn.C = cand; dn.L = L; dn.D = D; dn.W = W; dn.G = g; dn.N = N; dn.pairs = pairs;
             dn.lb = nullptr; dn.count = nullptr; dn.n_static = (int)P; dn.cursor = cursor; dn.bsf = bsf;
             dn.rho = INFINITY; dn.dtw = dtw; dn.counters = nullptr;
-            int blocks = dtw_occupancy(t, 1) * num_sms();
+            int blocks = dtw_occupancy(t, 1, g) * num_sms();
             if (blocks < 1) blocks = num_sms();
             float ms_best = 1e30f;
             for (int rep = 0; rep < 3 && ok; ++rep) {
@@ -644,7 +644,7 @@ int tcdtw_build(const float *cand, int64_t N, int32_t L, int32_t D, int32_t W, i
     }
     x->R_ref = refine_rows_for(W);
     if (x->R_ref == 0) { free_index(x); return TCDTW_ERR_UNSUPPORTED; }
-    x->blocks_nn = dtw_occupancy(x->tile, 1) * x->sms;
+    x->blocks_nn = dtw_occupancy(x->tile, 1, x->G) * x->sms;
     if (x->blocks_nn < 1) x->blocks_nn = x->sms;
     x->tile_seed = x->tile;
     x->G_seed = x->G;
@@ -657,7 +657,7 @@ int tcdtw_build(const float *cand, int64_t N, int32_t L, int32_t D, int32_t W, i
                 break;
             }
     }
-    x->blocks_seed = dtw_occupancy(x->tile_seed, 1) * x->sms;
+    x->blocks_seed = dtw_occupancy(x->tile_seed, 1, x->G_seed) * x->sms;
     if (x->blocks_seed < 1) x->blocks_seed = x->sms;
     x->blocks_ref = x->sms * 8;  // one-warp blocks
     rc = alloc_index(x);

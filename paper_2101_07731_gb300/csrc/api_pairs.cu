@@ -92,7 +92,7 @@ bool choose_tile(int64_t P, int L, int D, int W, int need_div, int *tile, int *G
 }
 
 int blocks_for(int tile, int which, int64_t groups, int G) {
-    int occ = dtw_occupancy(tile, which);
+    int occ = dtw_occupancy(tile, which, G);
     if (occ <= 0) occ = 1;
     const int64_t gpb = 128 / G;
     int64_t need = (groups + gpb - 1) / gpb;

@@ -121,6 +121,74 @@ __device__ __forceinline__ unsigned row_mask(int lo, int hi, int R) {
 
 constexpr int kAbandonEvery = 8;
 
+// ------------------------------------------------------------------ column / row rings
+// Wide points (DM >= 16) are costly to fetch per lane and step: each lane
+// of a group reads a different candidate point, so a warp-wide load touches 32
+// different cache lines.  In the ring variant (kRing) every lane group keeps in shared
+// memory a ring of the candidate columns its lanes are about to read (RC slots of
+// ring_stride(DM) floats) and a ring of the query rows of its next virtual lanes
+// (kRingRows slots of R*DM floats).  The group fills both with coalesced cp.async
+// copies kRingAhead steps before first use (a prologue covers the first steps) and
+// waits for the fills of kRingAhead steps ago at each step.  Reads then hit shared
+// memory: a float4 per four dimensions, conflict-free across consecutive columns
+// because the slot stride is an odd number of 16-byte units.
+// Sizes (checked against the exact schedule for every small (L, W, R, G)): at most G
+// virtual lanes are active at a time, so the columns in use at step t and those
+// filled for step t + kRingAhead span fewer than kRingAhead + G slots; virtual lanes
+// start at most one per step, so kRingAhead + 2 row slots suffice.
+constexpr int kRingAhead = 4;
+constexpr int kRingRows = 8;
+__host__ __device__ constexpr int ring_stride(int DM) { return ((DM / 4) & 1) ? DM + 8 : DM + 4; }
+__host__ __device__ constexpr int ring_cols(int G) {
+    return (kRingAhead + G) <= 8 ? 8 : (kRingAhead + G) <= 16 ? 16 : (kRingAhead + G) <= 32 ? 32 : 64;
+}
+__host__ __device__ constexpr int ring_group_floats(int R, int DM, int G) {
+    return ring_cols(G) * ring_stride(DM) + kRingRows * R * DM;
+}
+// shared memory of a 128-thread block of the ring variant
+__host__ __device__ constexpr size_t ring_block_bytes(int R, int DM, int G) {
+    return (size_t)(128 / G) * ring_group_floats(R, DM, G) * sizeof(float);
+}
+__device__ __forceinline__ void cp_async_wait_ahead() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kRingAhead) : "memory");
+}
+// smallest virtual lane still active at step T (v0 = 0), and largest started by T
+__device__ __forceinline__ int ring_vmin(int T, int R, int W, int L) {
+    const int x = T - R + 1 - W;
+    const int a = x <= 0 ? 0 : (x + R) / (R + 1);
+    return max(a, T - L + 1);
+}
+__device__ __forceinline__ int ring_vmax(int T, int R, int W, int v1) {
+    return min(v1 - 1, min(T, (T + W) / (R + 1)));
+}
+// Copy n floats from src (global) to dst (shared) with the lanes of a group.
+__device__ __forceinline__ void ring_copy(float *dst, const float *src, int n, bool vec, const Grp &g) {
+    if (vec) {
+        for (int p = g.lig * 4; p < n; p += 4 * g.G) cp_async_16(dst + p, src + p);
+    } else {
+        for (int p = g.lig; p < n; p += g.G) cp_async_4(dst + p, src + p);
+    }
+}
+// Issue the fills needed up to step T: columns [*col_hi, c_end) and the rows of virtual
+// lanes [*v_hi, v_end).
+template <int R, int DM>
+__device__ __forceinline__ void ring_fill(float *rcols, float *rrows, int RC, const float *A, const float *B, int L,
+                                          int D, int W, int v1, int T, int *col_hi, int *v_hi, bool vec,
+                                          const Grp &g) {
+    constexpr int DMS = ring_stride(DM);
+    const int c_end = min(L, T - ring_vmin(T, R, W, L) + 1);
+    for (int c = *col_hi; c < c_end; ++c)
+        ring_copy(rcols + (c & (RC - 1)) * DMS, B + (size_t)c * D, D, vec, g);
+    if (c_end > *col_hi) *col_hi = c_end;
+    const int v_end = min(v1, ring_vmax(T, R, W, v1) + 1);
+    for (int vv = *v_hi; vv < v_end; ++vv) {
+        float *dst = rrows + (vv & (kRingRows - 1)) * R * DM;
+        const int nr = min(R, L - vv * R);
+        for (int r = 0; r < nr; ++r) ring_copy(dst + r * DM, A + (size_t)(vv * R + r) * D, D, vec, g);
+    }
+    if (v_end > *v_hi) *v_hi = v_end;
+}
+
 // Hook sets.  top(j): row above the first virtual lane of a pass (v0 > 0).
 // cell(i, j, val): every in-band cell (kCells).  after_col(i0, j, bottom): once per
 // computed column of a virtual lane.  abandon(m): every kAbandonEvery steps with the
@@ -146,12 +214,17 @@ struct NoHooks {
 // stage (may be null): this lane's shared-memory slot of R*D floats, used to copy
 // the rows of the lane's next virtual lane with cp.async while it works on the
 // current one (a virtual-lane start then reads shared memory, not global memory).
-template <int R, int DM, class Hooks>
+// kRing (wide points only, v0 == 0): candidate columns and query rows come from the
+// group's rings at `ring` (ring_group_floats(R, DM, G) floats, RC = ring_cols(G) column
+// slots, the dimensions D..DM-1 of every slot zero); all lanes of the warp call it.
+template <int R, int DM, class Hooks, bool kRing = false>
 __device__ __forceinline__ float band_pass(const float *__restrict__ A, const float *__restrict__ B, int L, int D,
                                            int W, int v0, int v1, const Grp &g, Hooks &hooks, bool live,
-                                           bool *abandoned, long long *cells, float *stage = nullptr) {
+                                           bool *abandoned, long long *cells, float *stage = nullptr,
+                                           float *ring = nullptr, int RC = 0) {
     const bool stage_vec4 = (((uintptr_t)A) & 15) == 0;
     static_assert(R % 2 == 0, "rows are processed in pairs");
+    static_assert(!kRing || (DM >= 16 && DM % 4 == 0), "rings hold float4-aligned wide points");
     constexpr int RP = R / 2;
     const float INF = TC_INF;
     constexpr bool kDimPack = DM >= 16;
@@ -172,7 +245,25 @@ __device__ __forceinline__ float band_pass(const float *__restrict__ A, const fl
     bool loaded = false, staged = false;
     long long ncell = 0;
     *abandoned = false;
+    float *rcols = ring, *rrows = ring + (kRing ? RC * ring_stride(DM) : 0);
+    int col_hi = 0, v_hi = 0;
+    const bool ring_vec = ((D & 3) == 0) && (((((uintptr_t)A) | ((uintptr_t)B)) & 15) == 0);
+    if (kRing) {
+        // prologue: everything the first kRingAhead steps read, complete before the loop
+        if (!dead)
+            ring_fill<R, DM>(rcols, rrows, RC, A, B, L, D, W, v1, tau0 + kRingAhead - 1, &col_hi, &v_hi, ring_vec, g);
+        cp_async_wait_all();
+        __syncwarp();
+    }
     for (int tau = tau0; tau <= tau_end; ++tau) {
+        if (kRing) {
+            __syncwarp();  // the previous step's reads of the slots refilled below are done
+            if (!dead)
+                ring_fill<R, DM>(rcols, rrows, RC, A, B, L, D, W, v1, tau + kRingAhead, &col_hi, &v_hi, ring_vec, g);
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+            cp_async_wait_ahead();
+            __syncwarp();
+        }
         const float in = __shfl_sync(g.mask, bottom, g.src);
         if (tau > thi && v < v1) {
             v += g.G;
@@ -210,7 +301,19 @@ __device__ __forceinline__ float band_pass(const float *__restrict__ A, const fl
                         }
                     }
                 }
-                if (kDimPack) {
+                if (kDimPack && kRing) {
+                    const float *rr = rrows + (v & (kRingRows - 1)) * R * DM;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+#pragma unroll
+                        for (int k = 0; k < DM / 4; ++k) {
+                            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+                            if (i0 + r < L) x = *reinterpret_cast<const float4 *>(rr + r * DM + 4 * k);
+                            ad[kDimPack ? r : 0][kDimPack ? 2 * k : 0] = pk(x.x, x.y);
+                            ad[kDimPack ? r : 0][kDimPack ? 2 * k + 1 : 0] = pk(x.z, x.w);
+                        }
+                    }
+                } else if (kDimPack) {
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
                         const int i = i0 + r;
@@ -238,7 +341,24 @@ __device__ __forceinline__ float band_pass(const float *__restrict__ A, const fl
                 }
             }
             f2 cs[kDimPack ? R : 1];
-            if (kDimPack) {
+            if (kDimPack && kRing) {
+                // the column from the ring, four dimensions per shared-memory load
+                const float *bc = rcols + (j & (RC - 1)) * ring_stride(DM);
+#pragma unroll
+                for (int r = 0; r < R; ++r) cs[kDimPack ? r : 0] = 0ull;
+#pragma unroll
+                for (int k = 0; k < DM / 4; ++k) {
+                    const float4 x = *reinterpret_cast<const float4 *>(bc + 4 * k);
+                    const f2 b0 = pk(x.x, x.y), b1 = pk(x.z, x.w);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const f2 t0 = sub2(ad[kDimPack ? r : 0][kDimPack ? 2 * k : 0], b0);
+                        cs[kDimPack ? r : 0] = fma2(t0, t0, cs[kDimPack ? r : 0]);
+                        const f2 t1 = sub2(ad[kDimPack ? r : 0][kDimPack ? 2 * k + 1 : 0], b1);
+                        cs[kDimPack ? r : 0] = fma2(t1, t1, cs[kDimPack ? r : 0]);
+                    }
+                }
+            } else if (kDimPack) {
                 // the column two dimensions at a time, each pair used by all R rows
 #pragma unroll
                 for (int r = 0; r < R; ++r) cs[kDimPack ? r : 0] = 0ull;
@@ -337,6 +457,11 @@ __device__ __forceinline__ float band_pass(const float *__restrict__ A, const fl
         }
     }
     *cells = ncell;
+    if (kRing) {
+        // no fill of this pair may land after the next pair's fills of the same slots
+        cp_async_wait_all();
+        __syncwarp();
+    }
     // R(L-1, L-1): the last cell of the last virtual lane, still in its lane's column
     // registers (the lane computes nothing after that virtual lane's last column)
     if (!*abandoned && live && ((vlast - v0) % g.G) == g.lig && vlast >= v0 && vlast < v1) {
@@ -373,12 +498,25 @@ struct CkptHooks {
 template <int R, int DM>
 constexpr size_t stage_bytes() { return (size_t)128 * R * DM * sizeof(float); }
 
-template <int R, int DM>
+// Block rings of the ring variant: the group's slice of the dynamic shared memory,
+// zeroed once (the dimensions D..DM-1 of every slot are never written afterwards).
+template <int R, int DM, bool kRing>
+__device__ __forceinline__ float *block_ring(float *smem, int G) {
+    if (!kRing) return nullptr;
+    const int gf = ring_group_floats(R, DM, G);
+    for (int k = threadIdx.x; k < (128 / G) * gf; k += blockDim.x) smem[k] = 0.f;
+    __syncthreads();
+    return smem + (size_t)(threadIdx.x / G) * gf;
+}
+
+template <int R, int DM, bool kRing>
 __global__ void __launch_bounds__(128) k_dtw_pairs(const float *__restrict__ A, const float *__restrict__ B, int64_t P,
                                                     int L, int D, int W, int G, float *__restrict__ dist,
                                                     float *__restrict__ ckpt, int C) {
-    extern __shared__ float stage_smem[];
-    float *stage = stage_smem + (size_t)threadIdx.x * R * DM;
+    extern __shared__ __align__(16) float stage_smem[];
+    float *stage = kRing ? nullptr : stage_smem + (size_t)threadIdx.x * R * DM;
+    float *ring = block_ring<R, DM, kRing>(stage_smem, G);
+    const int RC = ring_cols(G);
     Grp g = make_grp(G);
     g.mask = 0xffffffffu;  // lockstep: every group of the warp runs the same schedule
     const int gpw = 32 / G;
@@ -397,8 +535,8 @@ __global__ void __launch_bounds__(128) k_dtw_pairs(const float *__restrict__ A, 
         bool ab = false;
         long long cells;
         const int64_t pp = live ? p : 0;
-        float r = band_pass<R, DM>(A + (size_t)pp * L * D, B + (size_t)pp * L * D, L, D, W, 0, nv, g, h, live, &ab,
-                                   &cells, stage);
+        float r = band_pass<R, DM, CkptHooks<R>, kRing>(A + (size_t)pp * L * D, B + (size_t)pp * L * D, L, D, W, 0,
+                                                       nv, g, h, live, &ab, &cells, stage, ring, RC);
         r = grp_min(r, g);
         if (live && g.lig == 0) dist[p] = r;
     }
@@ -420,15 +558,17 @@ struct NnHooks {
 // entry's best lower bound (+inf = already dropped; lb == null: 0).  Writes dtw[e]
 // (FP32 DTW, or +inf when pruned / abandoned) and lowers bsf[m].
 // R = 16 with up to 5 dimensions: capped at 128 registers (4 CTAs, 16 warps per SM)
-template <int R, int DM>
+template <int R, int DM, bool kRing>
 __global__ void __launch_bounds__(128, (R >= 16 && DM <= 5) ? 4 : 1) k_dtw_nn(const float *__restrict__ Q, const float *__restrict__ Cand, int L,
                                                  int D, int W, int G, int64_t N, const uint32_t *__restrict__ pairs,
                                                  const float *__restrict__ lb, const int32_t *__restrict__ count,
                                                  int n_static, int *__restrict__ cursor, unsigned long long *bsf,
                                                  float rho, float *__restrict__ dtw,
                                                  unsigned long long *__restrict__ counters) {
-    extern __shared__ float stage_smem[];
-    float *stage = stage_smem + (size_t)threadIdx.x * R * DM;
+    extern __shared__ __align__(16) float stage_smem[];
+    float *stage = kRing ? nullptr : stage_smem + (size_t)threadIdx.x * R * DM;
+    float *ring = block_ring<R, DM, kRing>(stage_smem, G);
+    const int RC = ring_cols(G);
     Grp g = make_grp(G);
     g.mask = 0xffffffffu;  // lockstep: every group of the warp runs the same schedule
     const int gpw = 32 / G;
@@ -462,8 +602,8 @@ __global__ void __launch_bounds__(128, (R >= 16 && DM <= 5) ? 4 : 1) k_dtw_nn(co
         h.rho = rho;
         bool ab = false;
         long long cells = 0;
-        float r = band_pass<R, DM>(Q + (size_t)m * L * D, Cand + (size_t)n * L * D, L, D, W, 0, nv, g, h, live, &ab,
-                                   &cells, stage);
+        float r = band_pass<R, DM, NnHooks, kRing>(Q + (size_t)m * L * D, Cand + (size_t)n * L * D, L, D, W, 0, nv, g,
+                                                   h, live, &ab, &cells, stage, ring, RC);
         r = grp_min(r, g);
         long long cs = cells;
         for (int o = G >> 1; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
@@ -702,15 +842,33 @@ __device__ double band_pass64(const float *__restrict__ A, const float *__restri
 }
 
 // ============================================================= per-tile launchers
+// The ring variant is compiled for the wide-point tiles (DM >= 16, a multiple of 4) and
+// used when its shared memory for the launch's G stays within kRingSmemMax (two blocks
+// per SM); otherwise, and for narrow points, the plain variant runs.
+constexpr size_t kRingSmemMax = 100 * 1024;
+
 template <int R, int DM>
 struct TileKernels {
-    static cudaError_t prepare() {  // allow the staging slots above 48 KB (once)
+    static constexpr bool kHasRing = DM >= 16 && DM % 4 == 0;
+    static constexpr bool kDimPack = DM >= 16;
+    // the plain variant's staging slots (narrow points only; wide points read rows directly)
+    static constexpr size_t plain_bytes() { return kDimPack ? 0 : stage_bytes<R, DM>(); }
+    static bool use_ring(int G) { return kHasRing && ring_block_bytes(R, DM, G) <= kRingSmemMax; }
+    static cudaError_t prepare() {  // allow dynamic shared memory above 48 KB (once)
         static bool done = false;
         if (done) return cudaSuccess;
-        const int sb = (int)stage_bytes<R, DM>();
-        cudaError_t e = cudaFuncSetAttribute(k_dtw_pairs<R, DM>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+        const int sb = (int)(plain_bytes() > 0 ? plain_bytes() : 1024);
+        cudaError_t e = cudaFuncSetAttribute(k_dtw_pairs<R, DM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_dtw_nn<R, DM>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+            e = cudaFuncSetAttribute(k_dtw_nn<R, DM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+        if constexpr (kHasRing) {
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_dtw_pairs<R, DM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kRingSmemMax);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_dtw_nn<R, DM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kRingSmemMax);
+        }
         done = e == cudaSuccess;
         return e;
     }
@@ -718,14 +876,31 @@ struct TileKernels {
                              int D, int W, float *dist, float *ck, int C) {
         cudaError_t e = prepare();
         if (e != cudaSuccess) return e;
-        k_dtw_pairs<R, DM><<<blocks, 128, stage_bytes<R, DM>(), s>>>(A, B, P, L, D, W, G, dist, ck, C);
+        if constexpr (kHasRing) {
+            if (use_ring(G)) {
+                k_dtw_pairs<R, DM, true><<<blocks, 128, ring_block_bytes(R, DM, G), s>>>(A, B, P, L, D, W, G, dist,
+                                                                                          ck, C);
+                note_launch();
+                return cudaGetLastError();
+            }
+        }
+        k_dtw_pairs<R, DM, false><<<blocks, 128, plain_bytes(), s>>>(A, B, P, L, D, W, G, dist, ck, C);
         note_launch();
         return cudaGetLastError();
     }
     static cudaError_t nn(int blocks, cudaStream_t s, const DtwNnArgs &x) {
         cudaError_t e = prepare();
         if (e != cudaSuccess) return e;
-        k_dtw_nn<R, DM><<<blocks, 128, stage_bytes<R, DM>(), s>>>(x.Q, x.C, x.L, x.D, x.W, x.G, x.N, x.pairs, x.lb,
+        if constexpr (kHasRing) {
+            if (use_ring(x.G)) {
+                k_dtw_nn<R, DM, true><<<blocks, 128, ring_block_bytes(R, DM, x.G), s>>>(
+                    x.Q, x.C, x.L, x.D, x.W, x.G, x.N, x.pairs, x.lb, x.count, x.n_static, x.cursor, x.bsf, x.rho,
+                    x.dtw, x.counters);
+                note_launch();
+                return cudaGetLastError();
+            }
+        }
+        k_dtw_nn<R, DM, false><<<blocks, 128, plain_bytes(), s>>>(x.Q, x.C, x.L, x.D, x.W, x.G, x.N, x.pairs, x.lb,
                                                                    x.count, x.n_static, x.cursor, x.bsf, x.rho, x.dtw,
                                                                    x.counters);
         note_launch();
@@ -744,13 +919,24 @@ struct TileKernels {
         note_launch();
         return cudaGetLastError();
     }
-    static int occupancy(int which) {
+    // resident blocks per SM of the variant a launch with G runs (which: 0 pairs, 1 search)
+    static int occupancy(int which, int G) {
         int n = 0;
         if (prepare() != cudaSuccess) return 0;
+        if constexpr (kHasRing) {
+            if (use_ring(G)) {
+                const size_t sb = ring_block_bytes(R, DM, G);
+                if (which == 0)
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dtw_pairs<R, DM, true>, 128, sb);
+                else
+                    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dtw_nn<R, DM, true>, 128, sb);
+                return n;
+            }
+        }
         if (which == 0)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dtw_pairs<R, DM>, 128, stage_bytes<R, DM>());
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dtw_pairs<R, DM, false>, 128, plain_bytes());
         else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dtw_nn<R, DM>, 128, stage_bytes<R, DM>());
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dtw_nn<R, DM, false>, 128, plain_bytes());
         return n;
     }
 };
@@ -763,7 +949,7 @@ struct TileKernels {
     cudaError_t tile##id##_backward(int G, int blocks, int threads, size_t smem, cudaStream_t s, const float *A,   \
                                     const float *B, const float *ck, int C, const float *gd, int64_t P, int L,     \
                                     int D, int W, float *gA, float *gB);                                           \
-    int tile##id##_occupancy(int which);
+    int tile##id##_occupancy(int which, int G);
 
 #define TC_TILE_DEF(id, R, DM)                                                                                      \
     cudaError_t tile##id##_pairs(int G, int blocks, cudaStream_t s, const float *A, const float *B, int64_t P,     \
@@ -778,6 +964,6 @@ struct TileKernels {
                                     int D, int W, float *gA, float *gB) {                                          \
         return TileKernels<R, DM>::backward(G, blocks, threads, smem, s, A, B, ck, C, gd, P, L, D, W, gA, gB);      \
     }                                                                                                               \
-    int tile##id##_occupancy(int which) { return TileKernels<R, DM>::occupancy(which); }
+    int tile##id##_occupancy(int which, int G) { return TileKernels<R, DM>::occupancy(which, G); }
 
 }  // namespace tc

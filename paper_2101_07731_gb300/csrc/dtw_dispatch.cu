@@ -236,11 +236,11 @@ cudaError_t dtw_backward_launch(int tile, int G, int blocks, size_t smem, cudaSt
     return cudaErrorInvalidValue;
 }
 
-int dtw_occupancy(int tile, int which) {
+int dtw_occupancy(int tile, int which, int G) {
     switch (tile) {
 #define X(id, R, DM) \
     case id:         \
-        return tile##id##_occupancy(which);
+        return tile##id##_occupancy(which, G);
         TC_TILES(X)
 #undef X
     }

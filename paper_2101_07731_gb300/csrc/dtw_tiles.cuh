@@ -70,6 +70,8 @@ int refine_rows_for(int W);  // smallest compiled R with 32*(R+1) >= 2W+R, or 0
 cudaError_t dtw_backward_launch(int tile, int G, int blocks, size_t smem, cudaStream_t s, const float *A,
                                 const float *B, const float *ck, int C, const float *gd, int64_t P, int L, int D,
                                 int W, float *gA, float *gB, int threads);
-int dtw_occupancy(int tile, int which);
+// resident blocks per SM of a launch of the tile with G lanes per pair (which: 0 pairs,
+// 1 search)
+int dtw_occupancy(int tile, int which, int G);
 
 }  // namespace tc

@@ -154,3 +154,27 @@ def test_argument_errors_of_the_newer_calls(lib):
     assert lib.tcdtw_lb_mv_selftest_timeout(0, None) == tc.ERR_INVALID
     assert lib.tcdtw_lb_mv_selftest_timeout(10_000_001, None) == tc.ERR_INVALID
     assert lib.tcdtw_batch_selftest_timeout(0, None) == tc.ERR_INVALID
+
+
+def test_noalloc_refuses_what_the_allocating_call_refuses(lib):
+    # tcdtw_lb_mv_noalloc promises the values of tcdtw_lower_bounds(TCDTW_LB_MV), so it
+    # must refuse the same arguments with the same codes, before any CUDA call
+    import paper_2101_07731_gb300 as tc
+    dummy = C.c_void_p(256)
+    f = lib.tcdtw_lower_bounds
+    f.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                  C.POINTER(tc.Opts), C.c_int32, C.c_void_p, C.c_void_p]
+    g = lib.tcdtw_lb_mv_noalloc
+    g.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
+                  C.c_void_p]
+    o = tc.default_opts()
+    cases = [(2, 3, 8, 65, 2),            # D > TCDTW_MAX_D: UNSUPPORTED
+             (70000, 70000, 8, 2, 2),     # M*N >= 4.29e9: UNSUPPORTED
+             (-1, 3, 8, 2, 2), (2, 3, 0, 2, 2), (2, 3, 8, 0, 2), (2, 3, 8, 2, -1),   # INVALID
+             (0, 3, 8, 2, 2), (2, 0, 8, 2, 2)]                                         # nothing to do
+    for M, N, L, D, W in cases:
+        a = f(dummy, M, dummy, N, L, D, W, 16, C.byref(o), tc.LB_MV, dummy, None)
+        b = g(dummy, M, dummy, N, L, D, W, dummy, None)
+        assert a == b, (M, N, L, D, W, a, b)
+    assert g(dummy, 2, dummy, 3, 8, 65, 2, dummy, None) == tc.ERR_UNSUPPORTED
+    assert g(None, 2, dummy, 3, 8, 2, 2, dummy, None) == tc.ERR_INVALID

@@ -33,6 +33,10 @@ CASES = [
     (5, 90, 16, 9), (4, 60, 32, 6), (3, 50, 64, 4), (17, 40, 1, 0), (9, 31, 2, 200),
     (6, 1, 3, 0), (7, 2, 4, 5), (11, 129, 6, 47), (5, 300, 4, 120),
     (9, 77, 9, 8), (10, 64, 10, 30), (7, 45, 11, 4),   # exact-width tiles of D = 9..11
+    # wide points through the shared-memory rings: D not a multiple of 4 (4-byte
+    # copies), ragged L, one pair per warp (large W), the 2,048 x 32 shape with W = 102
+    (6, 75, 17, 20), (5, 200, 27, 102), (4, 130, 40, 35), (3, 64, 13, 3), (5, 301, 32, 60),
+    (3, 2048, 32, 102),
 ]
 
 
@@ -80,7 +84,7 @@ def test_dtw_backward_matches_oracle_gradient(P, L, D, W):
     checked = 0
     for p in range(P):
         rd, ra, rb, path, margin = O.dtw_grad(A[p], B[p], W)
-        assert abs(float(d[p]) - rd) <= RTOL * max(rd, 1e-30)
+        assert abs(float(d[p].detach()) - rd) <= RTOL * max(rd, 1e-30)
         if margin < 1e-4:
             continue   # path not unique by a safe margin: FP32 may pick another optimum
         gp = float(g[p])

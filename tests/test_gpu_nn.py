@@ -280,7 +280,9 @@ def test_nn_query_blocks_and_seeds(seed_s, qblock):
 
 @pytest.mark.parametrize("M,N,L,D,W", [(1, 1, 16, 2, 3), (3, 5, 1, 3, 0), (4, 9, 20, 1, 0), (5, 40, 30, 2, 100),
                                        (2, 300, 50, 12, 5), (2, 80, 40, 32, 4), (2, 60, 24, 64, 3),
-                                       (3, 150, 60, 9, 6), (4, 130, 70, 10, 30), (2, 90, 33, 11, 3)])
+                                       (3, 150, 60, 9, 6), (4, 130, 70, 10, 30), (2, 90, 33, 11, 3),
+                                       (3, 200, 120, 32, 30), (2, 150, 300, 16, 40), (3, 120, 97, 21, 25),
+                                       (2, 100, 64, 44, 20)])
 def test_nn_edge_shapes(M, N, L, D, W):
     Q, Cn = _set("random_walk", M, N, L, D, 23)
     _check_nn(Q, Cn, W, 4)
