@@ -365,6 +365,14 @@ int tcdtw_lb_mv_selftest_timeout(int64_t wait_us, void *stream);
 int tcdtw_tile_count(void);
 int tcdtw_tile_info(int32_t t, int32_t *G, int32_t *R, int32_t *maxD);
 
+/* Failure injection for tests (host side; not in the paper): after `after` more
+ * successful device allocations by the library, every later one fails as if the
+ * device were out of memory -- no cudaMalloc is made -- and the calling entry point
+ * returns TCDTW_ERR_NOMEM after releasing what it had allocated.  after = -1 turns
+ * the injection off (the default); after = 0 fails the next allocation.  The setting
+ * is process-wide.  Errors: INVALID (after < -1). */
+int tcdtw_inject_alloc_failure(int64_t after);
+
 /* Static message for an error code. */
 const char *tcdtw_strerror(int code);
 

@@ -93,6 +93,7 @@ _SIGS = {
     "tcdtw_batch_selftest_timeout": (C.c_int, [_I64, _P]),
     "tcdtw_lb_mv_selftest_timeout": (C.c_int, [_I64, _P]),
     "tcdtw_batch_release": (C.c_int, []),
+    "tcdtw_inject_alloc_failure": (C.c_int, [_I64]),
     "tcdtw_tile_count": (C.c_int, []),
     "tcdtw_set_profiling": (C.c_int, [_P, _I32]),
     "tcdtw_stage_times": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(_I64)]),

@@ -12,6 +12,9 @@ int blocks_for(int tile, int which, int64_t groups, int G);
 int ckpt_rows(int L, int W);
 int64_t ckpt_floats(int64_t P, int L, int W);
 int cuda_err(cudaError_t e);
+// Every device allocation of the library: cudaMalloc, unless a failure was injected
+// with tcdtw_inject_alloc_failure (then cudaErrorMemoryAllocation, nothing allocated).
+cudaError_t dev_malloc(void **p, size_t bytes);
 const char *last_detail();
 float prune_rho(int L, int D);
 double refine_kappa(int L, int D);

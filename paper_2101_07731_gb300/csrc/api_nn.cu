@@ -109,9 +109,9 @@ bool autotune_nn_tile(const float *cand, int64_t N, int L, int D, int W, cudaStr
     unsigned long long *bsf = nullptr;
     float *dtw = nullptr;
     int *cursor = nullptr;
-    bool ok = cudaMalloc(&pairs, sizeof(uint32_t) * P) == cudaSuccess &&
-              cudaMalloc(&bsf, sizeof(unsigned long long) * Mq) == cudaSuccess &&
-              cudaMalloc(&dtw, sizeof(float) * P) == cudaSuccess && cudaMalloc(&cursor, sizeof(int)) == cudaSuccess;
+    bool ok = dev_malloc((void **)&pairs, sizeof(uint32_t) * P) == cudaSuccess &&
+              dev_malloc((void **)&bsf, sizeof(unsigned long long) * Mq) == cudaSuccess &&
+              dev_malloc((void **)&dtw, sizeof(float) * P) == cudaSuccess && dev_malloc((void **)&cursor, sizeof(int)) == cudaSuccess;
     std::vector<uint32_t> h(P);
     for (int64_t i = 0; i < P; ++i) {
         const int64_t m = (i / 64) % Mq, n = (i * 7919 + 13) % N;
@@ -160,7 +160,7 @@ template <typename T>
 cudaError_t dalloc(T **p, size_t n) {
     *p = nullptr;
     if (n == 0) n = 1;
-    return cudaMalloc((void **)p, n * sizeof(T));
+    return dev_malloc((void **)p, n * sizeof(T));
 }
 
 enum Counter {
@@ -201,6 +201,8 @@ struct tcdtw_index {
     unsigned long long *bestdf = nullptr, *best_idx_df = nullptr;
     DevStatus *status = nullptr;
     float *Uc = nullptr, *Lc = nullptr;  // candidate envelopes [N][L*D] (use_rev)
+    float2 *ref_tab = nullptr;   // global cost tables of the double-float refine (long bands)
+    int ref_slots = 0;
     float *mv_ws = nullptr;      // partial sums of split LB_MV tiles
     int64_t mv_ws_floats = 0;
     int32_t *mv_cnt = nullptr;   // their per-tile arrival counters (kept zero)
@@ -245,7 +247,7 @@ void free_index(tcdtw_index *x) {
                     x->refine, x->seed_dtw, x->surv_lb, x->surv_dtw, x->refine_d64, x->row_counts,
                     x->row_offsets, x->scalars, x->bsf, x->best64, x->best_idx, x->counters, x->status,
                     x->refine64, x->refine64_d64, x->amb, x->bestdf, x->best_idx_df, x->mv_ws, x->mv_cnt,
-                    x->Uc, x->Lc, x->qbuf, x->idx_buf, x->dist_buf};
+                    x->Uc, x->Lc, x->qbuf, x->idx_buf, x->dist_buf, x->ref_tab};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete x;
@@ -302,6 +304,15 @@ int alloc_index(tcdtw_index *x) {
     TC_TRY(dalloc(&x->mv_cnt, (size_t)kMvTileCounters));
     TC_TRY(cudaMemset(x->mv_cnt, 0, sizeof(int32_t) * kMvTileCounters));
     TC_TRY(cudaMemset(x->counters, 0, sizeof(unsigned long long) * kNumCounters));
+    if (!refine_df_table_fits_smem(L, D, x->W)) {
+        // one table slot per SM (bounded to ~1 GB), each L*(2W+1) double-float costs
+        const size_t slot = refine_gtab_slot_bytes(L, x->W);
+        int64_t slots = (int64_t)(1.0e9 / (double)slot);
+        if (slots > x->sms) slots = x->sms;
+        if (slots < 1) slots = 1;
+        x->ref_slots = (int)slots;
+        TC_TRY(dalloc(&x->ref_tab, (size_t)slots * slot / sizeof(float2)));
+    }
     if (x->opts.use_graph) {
         TC_TRY(dalloc(&x->qbuf, (size_t)Mb * L * D));
         TC_TRY(dalloc(&x->idx_buf, (size_t)Mb));
@@ -439,7 +450,9 @@ cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_o
     DtwRefineArgs rf;
     rf.Q = q; rf.C = x->cand; rf.L = L; rf.D = D; rf.W = W; rf.N = N;
     rf.pairs = x->refine; rf.count = x->scalars + kRefineCount; rf.d64 = x->refine_d64; rf.best64 = x->bestdf;
-    if ((e = dtw_refine_df_launch(x->R_ref, x->blocks_ref, s, rf)) != cudaSuccess) return e;
+    e = x->ref_tab ? dtw_refine_df_gtab_launch(x->R_ref, x->ref_slots, s, rf, x->ref_tab)
+                   : dtw_refine_df_launch(x->R_ref, x->blocks_ref, s, rf);
+    if (e != cudaSuccess) return e;
     if ((e = launch_refine_amb(x->refine, x->refine_d64, x->scalars + kRefineCount, N, x->bestdf, x->kappa, x->amb,
                                x->best_idx_df, x->sms, s)) != cudaSuccess)
         return e;
@@ -473,6 +486,7 @@ cudaError_t select_cascade(tcdtw_index *x, const float *q, int64_t M, cudaStream
     x->selected = true;
     tcdtw_opts &o = x->opts;
     if (!o.select || o.no_prune || (!o.use_pc && !o.use_ti)) return cudaSuccess;
+    const tcdtw_opts given = o;
     const int n = (int)std::min<int64_t>(M, std::min<int64_t>(x->Mb, 32));
     struct Cfg { int pc, ti, Lq; float e_pc, e_ti; };
     std::vector<Cfg> cfgs = {{0, 0, o.Lq, o.e_pc, o.e_ti}};
@@ -485,8 +499,8 @@ cudaError_t select_cascade(tcdtw_index *x, const float *q, int64_t M, cudaStream
     int64_t *sidx = nullptr;
     double *sdist = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    cudaError_t e = cudaMalloc(&sidx, sizeof(int64_t) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&sdist, sizeof(double) * n);
+    cudaError_t e = dev_malloc((void **)&sidx, sizeof(int64_t) * n);
+    if (e == cudaSuccess) e = dev_malloc((void **)&sdist, sizeof(double) * n);
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     const bool prof = x->profile;
@@ -514,6 +528,10 @@ cudaError_t select_cascade(tcdtw_index *x, const float *q, int64_t M, cudaStream
     o.Lq = best.Lq;
     o.e_pc = best.e_pc;
     o.e_ti = best.e_ti;
+    if (e != cudaSuccess) {  // keep the given bounds; the next call chooses again
+        o = given;
+        x->selected = false;
+    }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaFree(sidx);
@@ -865,10 +883,10 @@ int tcdtw_lower_bounds(const float *q, int64_t M, const float *c, int64_t N, int
             cudaFree(ws);
             cudaFree(cnt);
         };
-        if (cudaMalloc(&U, sizeof(float) * Mp * ldE) != cudaSuccess ||
-            cudaMalloc(&Lo, sizeof(float) * Mp * ldE) != cudaSuccess ||
-            cudaMalloc(&st, sizeof(DevStatus)) != cudaSuccess || cudaMalloc(&ws, sizeof(float) * ws_floats) != cudaSuccess ||
-            cudaMalloc(&cnt, sizeof(int32_t) * kMvTileCounters) != cudaSuccess) {
+        if (dev_malloc((void **)&U, sizeof(float) * Mp * ldE) != cudaSuccess ||
+            dev_malloc((void **)&Lo, sizeof(float) * Mp * ldE) != cudaSuccess ||
+            dev_malloc((void **)&st, sizeof(DevStatus)) != cudaSuccess || dev_malloc((void **)&ws, sizeof(float) * ws_floats) != cudaSuccess ||
+            dev_malloc((void **)&cnt, sizeof(int32_t) * kMvTileCounters) != cudaSuccess) {
             release();
             return TCDTW_ERR_NOMEM;
         }
@@ -901,8 +919,8 @@ int tcdtw_lower_bounds(const float *q, int64_t M, const float *c, int64_t N, int
     unsigned long long *bsf = nullptr;
     float *aux1 = nullptr, *aux2 = nullptr;
     int32_t *cnts = nullptr;
-    cudaError_t e = cudaMalloc(&pairs, sizeof(uint32_t) * P);
-    if (e == cudaSuccess) e = cudaMalloc(&bsf, sizeof(unsigned long long) * M);
+    cudaError_t e = dev_malloc((void **)&pairs, sizeof(uint32_t) * P);
+    if (e == cudaSuccess) e = dev_malloc((void **)&bsf, sizeof(unsigned long long) * M);
     if (e == cudaSuccess) e = launch_iota_pairs(pairs, P, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(out, 0, sizeof(float) * P, s);
     if (e == cudaSuccess) e = launch_init_block(M, bsf, nullptr, nullptr, nullptr, nullptr, nullptr, s);
@@ -912,8 +930,8 @@ int tcdtw_lower_bounds(const float *q, int64_t M, const float *c, int64_t N, int
     const float rho = 1.0f;
     if (which == TCDTW_LB_PC) {
         const int G = (L + o.w - 1) / o.w;
-        if (e == cudaSuccess) e = cudaMalloc(&aux1, sizeof(float) * M * G * K * 2 * D);
-        if (e == cudaSuccess) e = cudaMalloc(&cnts, sizeof(int32_t) * M * G);
+        if (e == cudaSuccess) e = dev_malloc((void **)&aux1, sizeof(float) * M * G * K * 2 * D);
+        if (e == cudaSuccess) e = dev_malloc((void **)&cnts, sizeof(int32_t) * M * G);
         for (int64_t m0 = 0; m0 < M && e == cudaSuccess; m0 += 65535) {
             const int64_t mc = (M - m0) < 65535 ? (M - m0) : 65535;
             e = launch_pc_boxes(q + m0 * E, mc, L, D, W, K, o.Lq, o.w, aux1 + m0 * G * K * 2 * D, cnts + m0 * G, s);
@@ -921,16 +939,16 @@ int tcdtw_lower_bounds(const float *q, int64_t M, const float *c, int64_t N, int
         if (e == cudaSuccess) e = launch_lb_pc_list(pl, aux1, cnts, K, o.w, bsf, rho, -1.0f, nullptr, P, sms, s);
     } else if (which == TCDTW_LB_MV_REV) {
         // envelopes of the candidates, then every pair's reverse bound
-        if (e == cudaSuccess) e = cudaMalloc(&aux1, sizeof(float) * N * E);
-        if (e == cudaSuccess) e = cudaMalloc(&aux2, sizeof(float) * N * E);
+        if (e == cudaSuccess) e = dev_malloc((void **)&aux1, sizeof(float) * N * E);
+        if (e == cudaSuccess) e = dev_malloc((void **)&aux2, sizeof(float) * N * E);
         for (int64_t n0 = 0; n0 < N && e == cudaSuccess; n0 += 65535) {
             const int64_t nc = (N - n0) < 65535 ? (N - n0) : 65535;
             e = launch_envelope(c + n0 * E, nc, L, D, W, aux1 + n0 * E, aux2 + n0 * E, E, s);
         }
         if (e == cudaSuccess) e = launch_lb_rev_list(pl, aux1, aux2, nullptr, rho, nullptr, P, sms, s);
     } else {
-        if (e == cudaSuccess) e = cudaMalloc(&aux1, sizeof(float) * M * L);
-        if (e == cudaSuccess) e = cudaMalloc(&aux2, sizeof(float) * M * L);
+        if (e == cudaSuccess) e = dev_malloc((void **)&aux1, sizeof(float) * M * L);
+        if (e == cudaSuccess) e = dev_malloc((void **)&aux2, sizeof(float) * M * L);
         if (e == cudaSuccess) e = launch_query_dq(q, M, L, D, aux1, aux2, s);
         if (e == cudaSuccess)
             e = o.ti_top ? launch_lb_ti_list(pl, aux1, aux2, o.P, bsf, rho, -1.0f, nullptr, P, sms, s)

@@ -131,6 +131,20 @@ int cuda_err(cudaError_t e) {
 
 const char *last_detail() { return g_last_detail; }
 
+// Allocation-failure injection on the host (tcdtw_inject_alloc_failure): how many more
+// device allocations may succeed, or -1 for no limit.
+static std::atomic<int64_t> g_alloc_allow{-1};
+
+cudaError_t dev_malloc(void **p, size_t bytes) {
+    *p = nullptr;
+    int64_t a = g_alloc_allow.load();
+    while (a >= 0) {
+        if (a == 0) return cudaErrorMemoryAllocation;
+        if (g_alloc_allow.compare_exchange_weak(a, a - 1)) break;
+    }
+    return cudaMalloc(p, bytes);
+}
+
 }  // namespace tc
 
 using namespace tc;
@@ -173,6 +187,12 @@ const char *tcdtw_strerror(int code) {
 int tcdtw_tile_count(void) { return kNumTiles; }
 
 const char *tcdtw_last_error_detail(void) { return last_detail(); }
+
+int tcdtw_inject_alloc_failure(int64_t after) {
+    if (after < -1) return TCDTW_ERR_INVALID;
+    g_alloc_allow.store(after);
+    return TCDTW_OK;
+}
 
 uint64_t tcdtw_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 

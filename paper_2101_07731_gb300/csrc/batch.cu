@@ -765,7 +765,7 @@ int build_plan(const tcdtw_dataset *sets, const std::vector<int> &mk, const tcdt
     p->n_items = (int)items.size();
     bytes += carve_bytes<BatchSet>(ns) + carve_bytes<BatchItem>(items.size()) + carve_bytes<BatchCtl>(1) +
              carve_bytes<int>((size_t)kCntPerSet * ns) + carve_bytes<int>(ns);
-    if (cudaMalloc(&p->arena, bytes) != cudaSuccess) {
+    if (dev_malloc((void **)&p->arena, bytes) != cudaSuccess) {
         delete p;
         return TCDTW_ERR_NOMEM;
     }
@@ -1001,10 +1001,10 @@ int tcdtw_batch_selftest_timeout(int64_t spin_limit, void *stream) {
     BatchItem *d_item = nullptr;
     BatchCtl *d_ctl = nullptr;
     BatchSet *d_set = nullptr;
-    cudaError_t e = cudaMalloc(&d_item, sizeof(item));
-    if (e == cudaSuccess) e = cudaMalloc(&d_set, sizeof(BatchSet));
+    cudaError_t e = dev_malloc((void **)&d_item, sizeof(item));
+    if (e == cudaSuccess) e = dev_malloc((void **)&d_set, sizeof(BatchSet));
     if (e == cudaSuccess) e = cudaMemsetAsync(d_set, 0, sizeof(BatchSet), s);
-    if (e == cudaSuccess) e = cudaMalloc(&d_ctl, sizeof(BatchCtl));
+    if (e == cudaSuccess) e = dev_malloc((void **)&d_ctl, sizeof(BatchCtl));
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_item, &item, sizeof(item), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_ctl, 0, sizeof(BatchCtl), s);
     int grid = 0;

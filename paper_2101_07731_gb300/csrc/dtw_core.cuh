@@ -129,15 +129,16 @@ constexpr int kAbandonEvery = 8;
 // ring_stride(DM) floats) and a ring of the query rows of its next virtual lanes
 // (kRingRows slots of R*DM floats).  The group fills both with coalesced cp.async
 // copies kRingAhead steps before first use (a prologue covers the first steps) and
-// waits for the fills of kRingAhead steps ago at each step.  Reads then hit shared
+// waits for the fills of kRingAhead steps ago at each step (the candidates stream from
+// HBM: the lookahead covers its latency).  Reads then hit shared
 // memory: a float4 per four dimensions, conflict-free across consecutive columns
 // because the slot stride is an odd number of 16-byte units.
 // Sizes (checked against the exact schedule for every small (L, W, R, G)): at most G
 // virtual lanes are active at a time, so the columns in use at step t and those
 // filled for step t + kRingAhead span fewer than kRingAhead + G slots; virtual lanes
 // start at most one per step, so kRingAhead + 2 row slots suffice.
-constexpr int kRingAhead = 4;
-constexpr int kRingRows = 8;
+constexpr int kRingAhead = 12;
+constexpr int kRingRows = 16;
 __host__ __device__ constexpr int ring_stride(int DM) { return ((DM / 4) & 1) ? DM + 8 : DM + 4; }
 __host__ __device__ constexpr int ring_cols(int G) {
     return (kRingAhead + G) <= 8 ? 8 : (kRingAhead + G) <= 16 ? 16 : (kRingAhead + G) <= 32 ? 32 : 64;
@@ -845,7 +846,7 @@ __device__ double band_pass64(const float *__restrict__ A, const float *__restri
 // The ring variant is compiled for the wide-point tiles (DM >= 16, a multiple of 4) and
 // used when its shared memory for the launch's G stays within kRingSmemMax (two blocks
 // per SM); otherwise, and for narrow points, the plain variant runs.
-constexpr size_t kRingSmemMax = 100 * 1024;
+constexpr size_t kRingSmemMax = 112 * 1024;
 
 template <int R, int DM>
 struct TileKernels {

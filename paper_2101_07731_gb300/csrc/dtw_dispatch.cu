@@ -140,6 +140,10 @@ cudaError_t launch_refine_df_band(int blocks, cudaStream_t s, const DtwRefineArg
 }
 }  // namespace
 
+bool refine_df_table_fits_smem(int L, int D, int W) {
+    return refine_rows_for(W) <= 2 && D <= 32 && df_band_smem(L, D, W) <= kDfBandSmemMax;
+}
+
 cudaError_t dtw_refine_df_launch(int R, int blocks, cudaStream_t s, const DtwRefineArgs &x) {
     const size_t smem = df_band_smem(x.L, x.D, x.W);
     if ((R == 1 || R == 2) && x.D <= 32 && smem <= kDfBandSmemMax) {

@@ -1,0 +1,89 @@
+// dtw_refine_gtab.cu -- double-float refine of long bands with the cell-cost table in
+// global memory.
+//
+// The tabulated refine (k_dtw_refine_df_band, dtw_dispatch.cu) takes the double-float
+// cost arithmetic off the sequential DP path: a block computes every in-band cell's
+// cost in parallel into a table, then one warp sweeps the band reading the table.  Its
+// table lives in shared memory, L*(2W+1)*8 bytes, so long bands (L = 2,048, W = 102:
+// 3.4 MB) fell back to one warp doing both, with the cost of 32 dimensions in
+// double-float as one long serial chain per cell (~26 ms for one pair).  Here each
+// block owns a slot of a global-memory table instead: it writes its entry's costs with
+// all threads (coalesced, consecutive cells of the band-major layout), synchronises,
+// and its first warp runs the same band_pass_df_table sweep.  Same operations in the
+// same order, so the value is bit-identical to k_dtw_refine_df and to the
+// shared-memory table kernel.
+#include "df.cuh"
+#include "dtw_core.cuh"
+
+namespace tc {
+
+constexpr int kGtabThreads = 256;
+
+template <int R, int DM>
+__global__ void __launch_bounds__(kGtabThreads) k_dtw_refine_df_gtab(const float *__restrict__ Q,
+                                                                     const float *__restrict__ Cand, int L, int D,
+                                                                     int W, int64_t N,
+                                                                     const uint32_t *__restrict__ pairs,
+                                                                     const int32_t *__restrict__ count,
+                                                                     float2 *__restrict__ tab,
+                                                                     double *__restrict__ v,
+                                                                     unsigned long long *__restrict__ bestdf) {
+    const int E = L * D, BW = 2 * W + 1, cells = L * BW;
+    float2 *cost = tab + (size_t)blockIdx.x * cells;
+    const int n_entries = *count;
+    for (int e = blockIdx.x; e < n_entries; e += gridDim.x) {
+        const uint32_t pid = pairs[e];
+        const int m = (int)(pid / (uint32_t)N);
+        const int64_t n = (int64_t)(pid - (uint32_t)m * (uint32_t)N);
+        const float *qa = Q + (size_t)m * E, *cb = Cand + (size_t)n * E;
+        __syncthreads();  // the previous entry's sweep is done with the slot
+        for (int k0 = threadIdx.x; k0 < cells; k0 += 2 * kGtabThreads) {
+            float ch[2], cl[2];
+            bool in[2];
+            int kk[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                kk[u] = k0 + u * kGtabThreads;
+                const int k = kk[u] < cells ? kk[u] : cells - 1;
+                const int i = k / BW, j = i + (k - i * BW) - W;
+                in[u] = kk[u] < cells && j >= 0 && j < L;
+                const int jj = in[u] ? j : i;
+                df_cell_cost<DM>(qa + (size_t)i * D, cb + (size_t)jj * D, D, ch[u], cl[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+                if (in[u]) cost[kk[u]] = make_float2(ch[u], cl[u]);
+        }
+        __syncthreads();  // the block's table writes are visible to its first warp
+        if (threadIdx.x < 32) {
+            Grp g = make_grp(32);
+            double r = band_pass_df_table<R>(cost, L, W, g);
+            r = grp_min(r, g);
+            if (g.lig == 0) {
+                v[e] = r;
+                atomicMin(bestdf + m, (unsigned long long)__double_as_longlong(r));
+            }
+        }
+    }
+}
+
+size_t refine_gtab_slot_bytes(int L, int W) { return (size_t)L * (2 * W + 1) * sizeof(float2); }
+
+// Launch with `slots` blocks (one table slot each; tab holds slots * L*(2W+1) float2).
+cudaError_t dtw_refine_df_gtab_launch(int R, int slots, cudaStream_t s, const DtwRefineArgs &x, float2 *tab) {
+    const int dm = x.D <= 8 ? 8 : x.D <= 32 ? 32 : 64;
+#define TC_GT(RV, DMV)                                                                                         \
+    if (R == RV && dm == DMV) {                                                                                \
+        k_dtw_refine_df_gtab<RV, DMV><<<slots, kGtabThreads, 0, s>>>(x.Q, x.C, x.L, x.D, x.W, x.N, x.pairs,     \
+                                                                     x.count, tab, x.d64, x.best64);           \
+        note_launch();                                                                                         \
+        return cudaGetLastError();                                                                             \
+    }
+#define TC_GT_R(RV) TC_GT(RV, 8) TC_GT(RV, 32) TC_GT(RV, 64)
+    TC_REFINE_RS(TC_GT_R)
+#undef TC_GT_R
+#undef TC_GT
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace tc

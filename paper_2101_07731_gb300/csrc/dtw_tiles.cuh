@@ -66,6 +66,12 @@ cudaError_t dtw_nn_launch(int tile, int blocks, cudaStream_t s, const DtwNnArgs 
 cudaError_t dtw_refine_launch(int R, int blocks, cudaStream_t s, const DtwRefineArgs &x);
 // double-float pass: d64 receives the double-float values, best64 the per-query minimum
 cudaError_t dtw_refine_df_launch(int R, int blocks, cudaStream_t s, const DtwRefineArgs &x);
+// whether dtw_refine_df_launch keeps the band's cost table in shared memory
+bool refine_df_table_fits_smem(int L, int D, int W);
+// the same pass with the cost table in global memory: `slots` blocks, tab holding
+// slots * refine_gtab_slot_bytes(L, W) bytes
+size_t refine_gtab_slot_bytes(int L, int W);
+cudaError_t dtw_refine_df_gtab_launch(int R, int slots, cudaStream_t s, const DtwRefineArgs &x, float2 *tab);
 int refine_rows_for(int W);  // smallest compiled R with 32*(R+1) >= 2W+R, or 0
 cudaError_t dtw_backward_launch(int tile, int G, int blocks, size_t smem, cudaStream_t s, const float *A,
                                 const float *B, const float *ck, int C, const float *gd, int64_t P, int L, int D,

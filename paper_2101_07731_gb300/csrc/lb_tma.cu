@@ -461,8 +461,8 @@ extern "C" int tcdtw_lb_mv_selftest_timeout(int64_t wait_us, void *stream) {
     DevStatus *st = nullptr;
     const int64_t E = kMvChunk, ldE = kMvChunk;
     const size_t floats = kMvRows * E + 2 * 2 * ldE + kMvRows;  // candidates, U, Lo (two pairs), lb
-    if (cudaMalloc(&buf, floats * sizeof(float)) != cudaSuccess) return TCDTW_ERR_NOMEM;
-    if (cudaMalloc(&st, sizeof(DevStatus)) != cudaSuccess) { cudaFree(buf); return TCDTW_ERR_NOMEM; }
+    if (dev_malloc((void **)&buf, floats * sizeof(float)) != cudaSuccess) return TCDTW_ERR_NOMEM;
+    if (dev_malloc((void **)&st, sizeof(DevStatus)) != cudaSuccess) { cudaFree(buf); return TCDTW_ERR_NOMEM; }
     cudaError_t e = cudaMemsetAsync(buf, 0, floats * sizeof(float), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
     LbMvArgs a;

@@ -32,7 +32,8 @@ cudaError_t launch_check_finite(const float *x, int64_t n, DevStatus *st, int wh
 }
 
 // ------------------------------------------------------------------ envelope
-// Block (tile t, query m) produces rows [t*TP, t*TP+TP) of U and Lo.  The query
+// Window scan (series longer than the van Herk kernel below stages): block (tile t,
+// query m) produces rows [t*TP, t*TP+TP) of U and Lo.  The query
 // points those rows need, [t*TP - W, t*TP + TP - 1 + W] clipped, are staged in
 // shared memory with coalesced loads when they fit; each output element is then the
 // max / min over its clipped window.  Output rows are written with stride ldE per
@@ -80,13 +81,104 @@ __global__ void k_envelope(const float *__restrict__ q, int L, int D, int W, flo
     }
 }
 
+// Sliding max / min by van Herk / Gil-Werman: in padded coordinates x' = i + W
+// (positions outside [0, L-1] hold -inf for the maximum and +inf for the minimum) the
+// window of output i is [i, i + 2W], of width w = 2W + 1.  Cut the padded series into
+// blocks of w starting at 0; a window either is one whole block or spans the end of one
+// block and the start of the next, so U[i] = max(suffix max of i within its block,
+// prefix max of i + 2W within its block) -- about three comparisons per element,
+// whatever W.  One CTA per (query, group of Dg dimensions) stages the group's L x Dg
+// values in shared memory, computes the suffixes of every block (phase 1), then scans
+// the prefixes forward and writes the outputs (phase 2); each (dimension, block) pair
+// is one thread's sequential scan.  Exact (max / min only).
+constexpr int kEnvVhThreads = 128;
+constexpr size_t kEnvVhSmemMax = 96 * 1024;
+
+__global__ void __launch_bounds__(kEnvVhThreads) k_envelope_vhgw(const float *__restrict__ q, int L, int D, int W,
+                                                                 int Dg, float *__restrict__ U,
+                                                                 float *__restrict__ Lo, int64_t ldE, int pad,
+                                                                 int pairs) {
+    extern __shared__ float sh[];
+    float *x = sh, *hmax = sh + (size_t)L * Dg, *hmin = hmax + (size_t)L * Dg;
+    const int m = blockIdx.y, p0 = blockIdx.x * Dg, ng = min(Dg, D - p0);
+    const float *qm = q + (size_t)m * L * D;
+    for (int k = threadIdx.x; k < L * ng; k += blockDim.x) {
+        const int i = k / ng, pp = k - i * ng;
+        x[i * Dg + pp] = __ldg(qm + (size_t)i * D + p0 + pp);
+    }
+    __syncthreads();
+    const int w = 2 * W + 1, Lp = L + 2 * W;
+    // phase 1: suffix max / min within each block, kept where an output window starts
+    const int nb1 = (L - 1) / w + 1;
+    for (int u = threadIdx.x; u < nb1 * ng; u += blockDim.x) {
+        const int b = u / ng, pp = u - b * ng;
+        float mx = -TC_INF, mn = TC_INF;
+        for (int xp = min(b * w + w - 1, Lp - 1); xp >= b * w; --xp) {
+            const int i = xp - W;
+            if (i >= 0 && i < L) {
+                const float v = x[i * Dg + pp];
+                mx = fmaxf(mx, v);
+                mn = fminf(mn, v);
+            }
+            if (xp < L) {
+                hmax[xp * Dg + pp] = mx;
+                hmin[xp * Dg + pp] = mn;
+            }
+        }
+    }
+    __syncthreads();
+    // phase 2: prefix max / min within each block; position xp ends the window of output
+    // xp - 2W
+    const int nb2 = (Lp - 1) / w + 1;
+    for (int u = threadIdx.x; u < nb2 * ng; u += blockDim.x) {
+        const int b = u / ng, pp = u - b * ng, p = p0 + pp;
+        float mx = -TC_INF, mn = TC_INF;
+        for (int xp = b * w; xp < min(b * w + w, Lp); ++xp) {
+            const int i = xp - W;
+            if (i >= 0 && i < L) {
+                const float v = x[i * Dg + pp];
+                mx = fmaxf(mx, v);
+                mn = fminf(mn, v);
+            }
+            const int o = xp - 2 * W;
+            if (o >= 0 && o < L) {
+                U[env_pos(m, (int64_t)o * D + p, ldE, pairs)] = fmaxf(hmax[o * Dg + pp], mx);
+                Lo[env_pos(m, (int64_t)o * D + p, ldE, pairs)] = fminf(hmin[o * Dg + pp], mn);
+            }
+        }
+    }
+    if (pad && blockIdx.x == 0) {
+        for (int64_t k = (int64_t)L * D + threadIdx.x; k < ldE; k += blockDim.x) {
+            U[env_pos(m, k, ldE, pairs)] = TC_INF;
+            Lo[env_pos(m, k, ldE, pairs)] = -TC_INF;
+        }
+    }
+}
+
 static cudaError_t envelope_impl(const float *q, int64_t M, int L, int D, int W, float *U, float *Lo, int ldE,
                                  int pairs, cudaStream_t s) {
     if (M <= 0) return cudaSuccess;
     if (W > L - 1) W = L - 1;
+    const int pad = ldE > L * D;
+    // van Herk / Gil-Werman when a CTA can stage at least one dimension of the series
+    int Dg = (int)(kEnvVhSmemMax / ((size_t)3 * L * sizeof(float)));
+    if (Dg > D) Dg = D;
+    if (Dg >= 1) {
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(k_envelope_vhgw, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)kEnvVhSmemMax);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        dim3 grid((D + Dg - 1) / Dg, (unsigned)M);
+        const size_t sh = (size_t)3 * L * Dg * sizeof(float);
+        k_envelope_vhgw<<<grid, kEnvVhThreads, sh, s>>>(q, L, D, W, Dg, U, Lo, ldE, pad, pairs);
+        note_launch();
+        return cudaGetLastError();
+    }
     dim3 grid((L + kEnvTP - 1) / kEnvTP, (unsigned)M);
     const size_t sh = (size_t)(kEnvTP + 2 * W) * D * sizeof(float);
-    const int pad = ldE > L * D;
     if (sh <= 48 * 1024)
         k_envelope<true><<<grid, 128, sh, s>>>(q, L, D, W, U, Lo, ldE, pad, pairs);
     else

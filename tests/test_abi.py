@@ -178,3 +178,10 @@ def test_noalloc_refuses_what_the_allocating_call_refuses(lib):
         assert a == b, (M, N, L, D, W, a, b)
     assert g(dummy, 2, dummy, 3, 8, 65, 2, dummy, None) == tc.ERR_UNSUPPORTED
     assert g(None, 2, dummy, 3, 8, 2, 2, dummy, None) == tc.ERR_INVALID
+
+
+def test_alloc_failure_injection_switch(lib):
+    lib.tcdtw_inject_alloc_failure.argtypes = [C.c_int64]
+    assert lib.tcdtw_inject_alloc_failure(-2) == 1          # INVALID
+    assert lib.tcdtw_inject_alloc_failure(5) == 0
+    assert lib.tcdtw_inject_alloc_failure(-1) == 0          # off again

@@ -36,7 +36,8 @@ def _set(kind, M, N, L, D, seed, n_proto=5, sigma=0.1):
 # ------------------------------------------------------------------ stages
 
 @pytest.mark.parametrize("M,L,D,W", [(5, 70, 3, 7), (3, 257, 5, 26), (2, 40, 12, 0), (2, 33, 2, 100),
-                                     (4, 1, 3, 0), (2, 300, 32, 30)])
+                                     (4, 1, 3, 0), (2, 300, 32, 30), (2, 2048, 32, 102), (3, 205, 7, 102),
+                                     (2, 9000, 1, 50), (2, 600, 64, 299)])
 def test_envelope_bit_exact(M, L, D, W):
     Q, _ = _set("random_walk", M, 1, L, D, 11)
     U, Lo = tc.envelope(_gpu(Q), W)
@@ -282,7 +283,9 @@ def test_nn_query_blocks_and_seeds(seed_s, qblock):
                                        (2, 300, 50, 12, 5), (2, 80, 40, 32, 4), (2, 60, 24, 64, 3),
                                        (3, 150, 60, 9, 6), (4, 130, 70, 10, 30), (2, 90, 33, 11, 3),
                                        (3, 200, 120, 32, 30), (2, 150, 300, 16, 40), (3, 120, 97, 21, 25),
-                                       (2, 100, 64, 44, 20)])
+                                       (2, 100, 64, 44, 20),
+                                       # long bands: the refine's cost table in global memory
+                                       (2, 60, 400, 3, 150), (3, 80, 300, 6, 70)])
 def test_nn_edge_shapes(M, N, L, D, W):
     Q, Cn = _set("random_walk", M, N, L, D, 23)
     _check_nn(Q, Cn, W, 4)
@@ -479,3 +482,52 @@ def test_nn_graph_replay_with_fresh_buffers_every_call():
         idx, _ = index.nn(_gpu(Qn))
         assert np.array_equal(idx.cpu().numpy(), O.nn_brute(Qn, Cn, 6)[0])
     index.close()
+
+
+def test_allocation_failures_are_reported_and_leak_nothing():
+    """Allocation failure injected on the host (tcdtw_inject_alloc_failure): building an
+    index with every possible allocation failing in turn returns TCDTW_ERR_NOMEM and
+    frees what was allocated; a search and a stage call whose allocation fails do the
+    same; afterwards the context and the index are fully usable."""
+    lib = tc._load()
+    spec = synth.SeriesSpec("proto_warp", 48, 3, 29, n_proto=4, sigma=0.1)
+    Qn, Cn = synth.generate(spec, synth.ROLE_QUERY, 9), synth.generate(spec, synth.ROLE_CAND, 300)
+    cand, q = _gpu(Cn), _gpu(Qn)
+    out = (torch.empty(9, dtype=torch.int64, device=DEV), torch.empty(9, dtype=torch.float64, device=DEV))
+    ridx, _ = O.nn_brute(Qn, Cn, 5)
+    # warm up everything a first use loads or caches (modules, the tile cache, torch's pool)
+    x = tc.Index(cand, 5, 8)
+    for _ in range(3):
+        x.nn(q, out=out)
+    x.close()
+    tc.lower_bounds(q, cand, 5)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    failed = 0
+    try:
+        for n in range(400):
+            lib.tcdtw_inject_alloc_failure(n)
+            try:
+                x = tc.Index(cand, 5, 8)
+            except tc.TcdtwError as e:
+                assert e.code == tc.ERR_NOMEM, e
+                failed += 1
+                continue
+            break
+        torch.cuda.synchronize()
+        lib.tcdtw_inject_alloc_failure(0)
+        with pytest.raises(tc.TcdtwError) as ei:        # the first search allocates (TC-DTW's choice)
+            x.nn(q, out=out)
+        assert ei.value.code == tc.ERR_NOMEM
+        with pytest.raises(tc.TcdtwError) as ei:        # a stage call with its own scratch
+            tc.lower_bounds(q, cand, 5)
+        assert ei.value.code == tc.ERR_NOMEM
+    finally:
+        assert lib.tcdtw_inject_alloc_failure(-1) == 0
+    assert failed >= 20, failed                           # every workspace of the index was tried
+    for _ in range(3):                                    # usable: selection, eager run, graph replay
+        x.nn(q, out=out)
+        assert np.array_equal(out[0].cpu().numpy(), ridx)
+    x.close()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
