@@ -139,7 +139,11 @@ void tcdtw_default_opts(tcdtw_opts *opts);
  *   opts  NULL = defaults.
  *   out   host: receives the new index; it owns its device workspaces.
  * Validates the shapes, scans the candidates for non-finite values (if
- * opts->check_finite), allocates the per-block workspaces and chooses the DTW tile.
+ * opts->check_finite), allocates the per-block workspaces and chooses the DTW tile:
+ * unless opts->tile is set, every valid (tile, G) of the shape is timed on pairs of the
+ * candidates and the fastest kept, per (L, D, W) for the life of the process; with the
+ * environment variable TCDTW_TUNE_CACHE naming a file, choices are also read from and
+ * appended to that file (lines of another device or build are ignored).
  * LB_PC is switched off (results are unchanged, only pruning) when its cell keys
  * Lq^D do not fit in 63 bits.
  * Errors: INVALID, NOMEM, CUDA, NONFINITE, UNSUPPORTED.
@@ -313,7 +317,8 @@ int tcdtw_compact(const float *lb, int64_t M, int64_t N, const float *thresh, in
  * up after about a second (the call then returns TIMEOUT); (2) the seeds' banded DTW,
  * one launch per tile class (D); (3) per query compaction and gated LB_PC / LB_TI;
  * (4) the survivors' DTW with early abandoning, one launch per tile class; (5) per
- * query the refine.  Entries with D > 12 or W > 140 are searched through tcdtw_build
+ * query the refine.  Each set's DTW runs on the band tile the single-set tuner picks for
+ * its shape (tcdtw_batch_tiles).  Entries with D > 12 or W > 140 are searched through tcdtw_build
  * / tcdtw_nn, one after another, after the sequence.  The sequence and its workspace
  * are kept per distinct batch (the descriptors and opts, byte for byte; up to 4
  * batches): the second call with the same batch captures the sequence into a CUDA
@@ -338,6 +343,17 @@ typedef struct {
  * Errors: INVALID, NOMEM, CUDA, NONFINITE, TIMEOUT, UNSUPPORTED (D > 64). */
 int tcdtw_batch_nn(const tcdtw_dataset *sets, int32_t nsets, const tcdtw_opts *opts,
                    tcdtw_stats *stats, void *stream);
+
+/* The band tile tcdtw_batch_nn gives each set (host outputs R[k], G[k]: rows per lane
+ * and lanes per pair of its DTW launches; 0, 0 for a set searched through tcdtw_nn or
+ * with M == 0).  Each set of the batched path takes the (tile, G) that the single-set
+ * tuner measures fastest for its (L, D, W) on its own candidates (cached per shape; see
+ * TCDTW_TUNE_CACHE at tcdtw_build), when the batched launches compile that tile (R in
+ * {4, 8, 16} for D <= 8, {4, 8} for D = 9..12), else 8 rows per lane with the smallest
+ * valid G.  May run the tuner (kernels on `stream`, synchronised).
+ * Errors: INVALID, NOMEM, CUDA. */
+int tcdtw_batch_tiles(const tcdtw_dataset *sets, int32_t nsets, const tcdtw_opts *opts, int32_t *R,
+                      int32_t *G, void *stream);
 
 /* Release the batch sequences tcdtw_batch_nn keeps (CUDA graphs and workspaces of
  * up to 4 distinct batches) after waiting for the device; the next call builds its

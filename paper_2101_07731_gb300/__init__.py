@@ -20,7 +20,7 @@ import os
 
 import torch
 
-__all__ = ["Index", "dtw", "dtw_pairs", "dtw_pairs_backward", "batch_nn", "batch_release", "batch_selftest_timeout", "lb_mv_selftest_timeout", "envelope", "query_dq",
+__all__ = ["Index", "dtw", "dtw_pairs", "dtw_pairs_backward", "batch_nn", "batch_tiles", "batch_release", "batch_selftest_timeout", "lb_mv_selftest_timeout", "envelope", "query_dq",
            "pc_boxes", "lower_bounds", "compact", "Opts", "Stats", "TcdtwError", "lib_path",
            "LB_MV", "LB_PC", "LB_TI", "LB_MV_REV", "default_opts"]
 
@@ -93,6 +93,7 @@ _SIGS = {
     "tcdtw_batch_selftest_timeout": (C.c_int, [_I64, _P]),
     "tcdtw_lb_mv_selftest_timeout": (C.c_int, [_I64, _P]),
     "tcdtw_batch_release": (C.c_int, []),
+    "tcdtw_batch_tiles": (C.c_int, [C.POINTER(Dataset), _I32, C.POINTER(Opts), C.POINTER(_I32), C.POINTER(_I32), _P]),
     "tcdtw_inject_alloc_failure": (C.c_int, [_I64]),
     "tcdtw_tile_count": (C.c_int, []),
     "tcdtw_set_profiling": (C.c_int, [_P, _I32]),
@@ -337,6 +338,25 @@ def batch_nn(sets, stats: bool = False, out=None, **opts):
     st = Stats()
     _call("tcdtw_batch_nn", arr, len(descs), C.byref(o), C.byref(st) if stats else None, _stream())
     return (outs, st.as_dict()) if stats else outs
+
+
+def batch_tiles(sets, **opts):
+    """[(R, G)] per set: the band tile (rows per lane, lanes per pair) the batched
+    search gives each set -- the single-set tuner's choice for its shape; (0, 0) for a
+    set searched one at a time."""
+    sets = list(sets)
+    descs = []
+    for s in sets:
+        cand, q = _series(s["cand"], "cand"), _series(s["q"], "q")
+        N, L, D = cand.shape
+        descs.append(Dataset(cand.data_ptr(), N, L, D, int(s["W"]), int(s.get("K", 16)), q.data_ptr(), q.shape[0],
+                             None, None))
+    arr = (Dataset * len(descs))(*descs)
+    R = (_I32 * max(1, len(descs)))()
+    G = (_I32 * max(1, len(descs)))()
+    o = default_opts(**opts)
+    _call("tcdtw_batch_tiles", arr, len(descs), C.byref(o), R, G, _stream())
+    return [(int(R[k]), int(G[k])) for k in range(len(descs))]
 
 
 def batch_release():

@@ -19,4 +19,7 @@ const char *last_detail();
 float prune_rho(int L, int D);
 double refine_kappa(int L, int D);
 bool pc_key_fits(int Lq, int D);
+// The single-set DTW tuner: the fastest valid (tile, G) for (L, D, W), timed on pairs of
+// the given candidates; cached per shape (and in the TCDTW_TUNE_CACHE file when set).
+bool autotune_nn_tile(const float *cand, int64_t N, int L, int D, int W, cudaStream_t s, int *tile, int *G);
 }  // namespace tc

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -87,10 +88,73 @@ struct TuneVal {
 static std::vector<std::pair<TuneKey, TuneVal>> g_tune_cache;
 static std::mutex g_tune_mu;  // indexes may be built from several host threads
 
+// Persistent tuner cache: with the environment variable TCDTW_TUNE_CACHE naming a file,
+// results are read from it on first use and appended to it after each new tuning, one
+// line "tcdtw-tune <tile-table signature> <device name> L D W tile G" per shape; lines of
+// another device or another build's tile table are ignored.
+static bool g_tune_file_read = false;
+
+static unsigned tile_table_signature() {
+    unsigned h = 2166136261u;  // FNV-1a over the compiled tiles
+    for (int t = 0; t < kNumTiles; ++t) {
+        h = (h ^ (unsigned)kTiles[t].R) * 16777619u;
+        h = (h ^ (unsigned)kTiles[t].DMAX) * 16777619u;
+    }
+    return h;
+}
+
+static void device_tag(char *out, size_t n) {
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        snprintf(out, n, "unknown");
+        return;
+    }
+    snprintf(out, n, "%s", prop.name);
+    for (char *c = out; *c; ++c)
+        if (*c == ' ' || *c == '\t') *c = '_';
+}
+
+static void tune_file_load_locked() {
+    if (g_tune_file_read) return;
+    g_tune_file_read = true;
+    const char *path = getenv("TCDTW_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    char tag[256], line[512], ftag[256];
+    device_tag(tag, sizeof(tag));
+    const unsigned sig = tile_table_signature();
+    while (fgets(line, sizeof(line), f)) {
+        unsigned fsig = 0;
+        int L, D, W, tile, G;
+        if (sscanf(line, "tcdtw-tune %x %255s %d %d %d %d %d", &fsig, ftag, &L, &D, &W, &tile, &G) != 7) continue;
+        if (fsig != sig || strcmp(ftag, tag) != 0 || tile < 0 || tile >= kNumTiles) continue;
+        if (kTiles[tile].DMAX != dmax_for(D) || !tile_valid(tile, G, W)) continue;
+        const TuneKey key{L, D, W};
+        bool have = false;
+        for (auto &kv : g_tune_cache) have = have || kv.first == key;
+        if (!have) g_tune_cache.push_back({key, TuneVal{tile, G}});
+    }
+    fclose(f);
+}
+
+static void tune_file_append(const TuneKey &k, const TuneVal &v) {
+    const char *path = getenv("TCDTW_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    char tag[256];
+    device_tag(tag, sizeof(tag));
+    fprintf(f, "tcdtw-tune %x %s %d %d %d %d %d\n", tile_table_signature(), tag, k.L, k.D, k.W, v.tile, v.G);
+    fclose(f);
+}
+
 bool autotune_nn_tile(const float *cand, int64_t N, int L, int D, int W, cudaStream_t s, int *tile, int *G) {
     const TuneKey key{L, D, W};
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
+        tune_file_load_locked();
         for (auto &kv : g_tune_cache)
             if (kv.first == key) { *tile = kv.second.tile; *G = kv.second.G; return true; }
     }
@@ -152,6 +216,7 @@ bool autotune_nn_tile(const float *cand, int64_t N, int L, int D, int W, cudaStr
     if (found) {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tune_cache.push_back({key, TuneVal{*tile, *G}});
+        tune_file_append(key, TuneVal{*tile, *G});
     }
     return found;
 }
@@ -305,10 +370,11 @@ int alloc_index(tcdtw_index *x) {
     TC_TRY(cudaMemset(x->mv_cnt, 0, sizeof(int32_t) * kMvTileCounters));
     TC_TRY(cudaMemset(x->counters, 0, sizeof(unsigned long long) * kNumCounters));
     if (!refine_df_table_fits_smem(L, D, x->W)) {
-        // one table slot per SM (bounded to ~1 GB), each L*(2W+1) double-float costs
+        // two table slots per SM (bounded to ~1.1 GB), each L*(2W+1) double-float costs:
+        // a block of up to 256 queries refines its ~one entry per query in one round
         const size_t slot = refine_gtab_slot_bytes(L, x->W);
-        int64_t slots = (int64_t)(1.0e9 / (double)slot);
-        if (slots > x->sms) slots = x->sms;
+        int64_t slots = (int64_t)(1.1e9 / (double)slot);
+        if (slots > 2 * x->sms) slots = 2 * x->sms;
         if (slots < 1) slots = 1;
         x->ref_slots = (int)slots;
         TC_TRY(dalloc(&x->ref_tab, (size_t)slots * slot / sizeof(float2)));

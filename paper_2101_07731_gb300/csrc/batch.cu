@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "api_internal.h"
+#include "batch_internal.cuh"
 #include "df.cuh"
 #include "dtw_core.cuh"
 #include "lb_device.cuh"
@@ -40,58 +41,6 @@
 #include "prep_device.cuh"
 
 namespace tc {
-
-constexpr int kBatchR = 8;          // rows per lane of the batched DTW
-constexpr int kBatchMaxD = 12;      // dimensions of the batched path (one exact-width tile per D)
-constexpr int kBatchThreads = 128;  // 4 warps per CTA
-constexpr int kBatchQB = 32;        // queries per LB_MV tile
-constexpr int kSeedSlots = 8;       // seed slots per query
-constexpr long long kSpinLimit = 4000000;  // ~1 s of 256 ns sleeps
-constexpr size_t kBatchSmem = 48 * 1024;   // LB_MV double buffers / box scratch / FP64 row slots
-
-// Per-set counters (ints, zeroed before every run).
-enum : int { kCntPrep = 0, kCntMv, kCntList, kCntSeedCursor, kCntSurvCursor, kCntPerSet };
-
-struct BatchSet {
-    const float *cand, *q;
-    int64_t *idx;
-    double *dist;
-    int64_t N;
-    int L, D, W, K, M;
-    int G, dcase, Rref, S;  // DTW lanes per pair and tile DM; FP64 rows per lane; seeds per query
-    int use_pc, use_ti, Lq, w, P, Gpc, np2, vec4, check_finite;
-    float e_pc, e_ti, rho, rho_ref;
-    double kappa;
-    int64_t ldE;
-    int n_qtiles, n_ctiles;
-    float *U, *Lo, *dq_lo, *dq_hi, *boxes;
-    int32_t *box_counts;
-    float *lbm;                          // [M][N] LB_MV
-    uint32_t *surv;                      // [M][N] survivor candidate ids, per query
-    float *surv_lb, *surv_dtw;           // [M][N]
-    uint32_t *list;                      // [M*N] DTW work list: q*N + position in the query's survivors
-    uint32_t *seeds;                     // [M][8] (UINT32_MAX: empty slot)
-    float *seed_dtw;                     // [M][8]
-    double *d64;                         // [M][N+8] refine values
-    unsigned long long *bsf;             // [M] packed best-so-far
-    int *nseed, *ncnt;                   // [M]
-    int *cnt;                            // kCntPerSet counters
-};
-
-enum : int { kItemPrep = 0, kItemMv, kItemSeed, kItemMid, kItemRefine, kItemStall };
-constexpr int kRefinePerItem = 4;  // queries per refine item (one per warp)
-struct BatchItem {
-    int kind, set, a, b;
-};
-
-struct BatchCtl {
-    int next[3];  // cursors of the front, mid and refine item ranges
-    int abort;
-    int never;    // stays 0: the self-test waits on it
-    DevStatus status;
-    unsigned long long counters[9];  // started, abandoned, cells, pruned at DTW, pruned MV, PC, TI, refined,
-                                     // refined in FP64
-};
 
 // Grab the next item index of range [begin, end) for the CTA (end when aborted).
 __device__ __forceinline__ int grab_item(BatchCtl *ctl, int which, int begin, int end) {
@@ -281,117 +230,15 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_front(const BatchSet *_
 }
 
 // ------------------------------------------------------------------ DTW launches
-// Phase 0: the seed entries i < M*8 (query i/8, slot i%8); phase 1: the work list.
-// A warp takes 32/G consecutive entries of one set (one per lane group) and runs
-// them in lockstep, as the single-set kernel does; the sets follow each other in
-// the order given, each with its own cursor, so warps move on as a set runs dry.
-template <int DM>
-__device__ __forceinline__ void dtw_set(const BatchSet &S, int phase, float *stage, BatchCtl *ctl) {
-    Grp g = make_grp(S.G);
-    g.mask = 0xffffffffu;
-    const int G = S.G, gpw = 32 / G;
-    const int L = S.L, D = S.D, W = S.W;
-    const int64_t N = S.N;
-    const int nv = (L + kBatchR - 1) / kBatchR;
-    const int n_entries = phase == 0 ? S.M * kSeedSlots : S.cnt[kCntList];
-    int *cursor = S.cnt + (phase == 0 ? kCntSeedCursor : kCntSurvCursor);
-    unsigned long long started = 0, aband = 0, ncells = 0, pruned = 0;
-    for (;;) {
-        int base = 0;
-        if ((threadIdx.x & 31) == 0) base = atomicAdd(cursor, gpw);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= n_entries) break;
-        const int e = base + (threadIdx.x & 31) / G;
-        bool live = e < n_entries;
-        int q = 0;
-        uint32_t cn = 0;
-        float lbe = 0.f;
-        float *out = nullptr;
-        if (live) {
-            if (phase == 0) {
-                q = e / kSeedSlots;
-                cn = S.seeds[e];
-                out = S.seed_dtw + e;
-                live = cn != 0xffffffffu;
-            } else {
-                const uint32_t pid = S.list[e];
-                q = (int)(pid / (uint64_t)N);
-                cn = S.surv[pid];
-                lbe = S.surv_lb[pid];
-                out = S.surv_dtw + pid;
-            }
-        }
-        if (live) {
-            const float thr = prune_threshold(ld_volatile_u64(S.bsf + q), S.rho);
-            if (!(lbe <= thr) || lbe == TC_INF) {
-                if (g.lig == 0 && lbe != TC_INF) ++pruned;
-                if (g.lig == 0) *out = TC_INF;
-                live = false;
-            }
-        }
-        NnHooks h;
-        h.bsf = S.bsf + q;
-        h.rho = S.rho;
-        bool ab = false;
-        long long cells = 0;
-        float r = band_pass<kBatchR, DM>(S.q + (size_t)q * L * D, S.cand + (size_t)cn * L * D, L, D, W, 0, nv, g, h,
-                                         live, &ab, &cells, stage);
-        r = grp_min(r, g);
-        long long cs = cells;
-        for (int o = G >> 1; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
-        if (live && g.lig == 0) {
-            ++started;
-            ncells += (unsigned long long)cs;
-            if (ab) {
-                ++aband;
-                *out = TC_INF;
-            } else {
-                *out = r;
-                atomicMin(S.bsf + q, pack_best(r, cn));
-            }
-        }
-    }
-    if (g.lig == 0 && (started | pruned)) {
-        atomicAdd(&ctl->counters[0], started);
-        atomicAdd(&ctl->counters[1], aband);
-        atomicAdd(&ctl->counters[2], ncells);
-        atomicAdd(&ctl->counters[3], pruned);
-    }
-}
-
-// One launch per tile class (DM) and phase: the sets order[0..nsets) of the class.
-// (One kernel holding every DM variant does not reuse registers across them and
-// spills inside the DP loop.)
-template <int DM>
-__global__ void __launch_bounds__(kBatchThreads, 3) k_batch_dtw(const BatchSet *__restrict__ sets,
-                                                                const int *__restrict__ order, int nsets, int phase,
-                                                                BatchCtl *ctl) {
-    extern __shared__ __align__(16) float stage_smem[];
-    float *stage = stage_smem + (size_t)threadIdx.x * kBatchR * DM;
-    for (int oi = 0; oi < nsets; ++oi) dtw_set<DM>(sets[order[oi]], phase, stage, ctl);
-}
-
-#define TC_BATCH_DMS(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)
-constexpr int kNumDmClasses = 12;
-__host__ __device__ constexpr int dm_class_of(int D) { return D - 1; }
-constexpr int kDmOfClass[kNumDmClasses] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12};
-
-cudaError_t launch_batch_dtw(int dm, int grid, cudaStream_t s, const BatchSet *sets, const int *order, int nsets,
-                             int phase, BatchCtl *ctl) {
-    switch (dm) {
-#define TC_BL(DMV)                                                                                        \
-    case DMV:                                                                                             \
-        k_batch_dtw<DMV><<<grid, kBatchThreads, (size_t)kBatchThreads * kBatchR * DMV * sizeof(float), s>>>( \
-            sets, order, nsets, phase, ctl);                                                              \
-        return cudaGetLastError();
-        TC_BATCH_DMS(TC_BL)
-#undef TC_BL
-    }
+// (the kernels: batch_internal.cuh, instantiated per rows-per-lane in batch_dtw_r*.cu)
+cudaError_t launch_batch_dtw(int R, int dm, int grid, cudaStream_t s, const BatchSet *sets, const int *order,
+                             int nsets, int phase, BatchCtl *ctl) {
+    if (R == 4) return batch_dtw_launch_r4(dm, grid, s, sets, order, nsets, phase, ctl);
+    if (R == 8) return batch_dtw_launch_r8(dm, grid, s, sets, order, nsets, phase, ctl);
+    if (R == 16) return batch_dtw_launch_r16(dm, grid, s, sets, order, nsets, phase, ctl);
     return cudaErrorInvalidValue;
 }
 
-// Opt the kernel in to `smem` bytes of dynamic shared memory (its static shared
-// memory comes on top, so 48 KB of dynamic memory already needs the opt-in).
 cudaError_t kernel_grid(const void *fn, size_t smem, int *grid) {
     if (smem > 0) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -404,13 +251,10 @@ cudaError_t kernel_grid(const void *fn, size_t smem, int *grid) {
     return cudaSuccess;
 }
 
-cudaError_t batch_dtw_grid(int dm, int *grid) {
-    switch (dm) {
-#define TC_BO(DMV) \
-    case DMV: return kernel_grid((const void *)k_batch_dtw<DMV>, (size_t)kBatchThreads * kBatchR * DMV * sizeof(float), grid);
-        TC_BATCH_DMS(TC_BO)
-#undef TC_BO
-    }
+cudaError_t batch_dtw_grid(int R, int dm, int *grid) {
+    if (R == 4) return batch_dtw_grid_r4(dm, grid);
+    if (R == 8) return batch_dtw_grid_r8(dm, grid);
+    if (R == 16) return batch_dtw_grid_r16(dm, grid);
     return cudaErrorInvalidValue;
 }
 
@@ -622,10 +466,28 @@ static_assert(2 * kMvRows * kMvChunk * 4 + 4 * kBatchQB * kMvChunk * 4 <= kBatch
 // ------------------------------------------------------------------ host side
 namespace {
 
-int batch_G(int W) {
+// Smallest lane-group size G with G*(R+1) >= 2W+R (no overlap of a lane's virtual
+// lanes), or 0.
+int batch_G(int R, int W) {
     for (int g = 4; g <= 32; g *= 2)
-        if (g * (kBatchR + 1) >= 2 * W + kBatchR) return g;
+        if (g * (R + 1) >= 2 * W + R) return g;
     return 0;
+}
+
+// The band tile of one set: the single-set tuner's fastest (tile, G) for its (L, D, W)
+// -- timed on the set's own candidates, cached per shape for the process (and in the
+// TCDTW_TUNE_CACHE file) -- when the batched launches compile that tile; else 8 rows
+// per lane with the smallest valid G.
+void choose_batch_tile(const tcdtw_dataset &d, int W, cudaStream_t s, int *R, int *G) {
+    int tile = -1, g = 0;
+    if (autotune_nn_tile(d.cand, d.N, d.L, d.D, W, s, &tile, &g) && tile >= 0 && kTiles[tile].DMAX == d.D &&
+        batch_tile_compiled(kTiles[tile].R, d.D) && g * (kTiles[tile].R + 1) >= 2 * W + kTiles[tile].R) {
+        *R = kTiles[tile].R;
+        *G = g;
+        return;
+    }
+    *R = 8;
+    *G = batch_G(8, W);
 }
 
 // A workspace arena and a captured graph per batch description.
@@ -641,7 +503,7 @@ struct BatchPlan {
     int front_end = 0, mid_end = 0, n_items = 0;  // item ranges [0, front_end), [front_end, mid_end), [mid_end, n_items)
     int grid_front = 0, grid_mid = 0, grid_refine = 0;
     // DTW launches: per tile class present, its sets d_order[off, off + n) and grid
-    struct DtwClass { int dm, off, n, grid; };
+    struct DtwClass { int R, dm, off, n, grid; };
     std::vector<DtwClass> classes;
     cudaGraphExec_t exec = nullptr;
     int launches = 0;
@@ -665,7 +527,7 @@ bool same_key(const BatchPlan *p, const tcdtw_dataset *sets, int n, const tcdtw_
 
 bool graph_path_ok(const tcdtw_dataset &d, const tcdtw_opts &o) {
     const int W = d.W > d.L - 1 ? d.L - 1 : d.W;
-    return d.D <= kBatchMaxD && batch_G(W) > 0 && refine_rows_for(W) > 0 && d.M <= 65535 &&
+    return d.D <= kBatchMaxD && batch_G(8, W) > 0 && refine_rows_for(W) > 0 && d.M <= 65535 &&
            o.seed_s <= kSeedSlots && (double)d.M * (double)d.N < 4.29e9;
 }
 
@@ -691,7 +553,7 @@ int build_plan(const tcdtw_dataset *sets, const std::vector<int> &mk, const tcdt
         memset(&b, 0, sizeof(b));
         b.cand = d.cand; b.q = d.q; b.idx = d.idx; b.dist = d.dist;
         b.N = d.N; b.L = d.L; b.D = d.D; b.W = d.W > d.L - 1 ? d.L - 1 : d.W; b.K = d.K; b.M = (int)d.M;
-        b.G = batch_G(b.W);
+        choose_batch_tile(d, b.W, s, &b.R, &b.G);
         b.dcase = d.D;
         b.Rref = refine_rows_for(b.W);
         b.S = (int)(o.seed_s < d.N ? o.seed_s : d.N);
@@ -727,26 +589,30 @@ int build_plan(const tcdtw_dataset *sets, const std::vector<int> &mk, const tcdt
     std::vector<int> order(ns);
     for (int k = 0; k < ns; ++k) order[k] = k;
     std::sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-    // DTW order: tile classes by total cost, the sets of a class by cost
-    std::vector<double> class_cost(kNumDmClasses, 0.0);
-    for (int k = 0; k < ns; ++k) class_cost[dm_class_of(hs[k].D)] += cost[k];
-    std::vector<int> cls(kNumDmClasses);
-    for (int c = 0; c < kNumDmClasses; ++c) cls[c] = c;
+    // DTW order: tile classes (R, D) by total cost, the sets of a class by cost
+    std::vector<std::pair<int, int>> tiles;  // distinct (R, D)
+    std::vector<double> class_cost;
+    for (int k = 0; k < ns; ++k) {
+        const std::pair<int, int> t{hs[k].R, hs[k].D};
+        size_t c = std::find(tiles.begin(), tiles.end(), t) - tiles.begin();
+        if (c == tiles.size()) { tiles.push_back(t); class_cost.push_back(0.0); }
+        class_cost[c] += cost[k];
+    }
+    std::vector<int> cls(tiles.size());
+    for (size_t c = 0; c < tiles.size(); ++c) cls[c] = (int)c;
     std::sort(cls.begin(), cls.end(), [&](int a, int b) { return class_cost[a] > class_cost[b]; });
     std::vector<int> dtw_order;
     for (int c : cls) {
-        BatchPlan::DtwClass dc{kDmOfClass[c], (int)dtw_order.size(), 0, 0};
+        BatchPlan::DtwClass dc{tiles[c].first, tiles[c].second, (int)dtw_order.size(), 0, 0};
         for (int k : order)
-            if (dm_class_of(hs[k].D) == c) dtw_order.push_back(k);
+            if (hs[k].R == dc.R && hs[k].D == dc.dm) dtw_order.push_back(k);
         dc.n = (int)dtw_order.size() - dc.off;
-        if (dc.n > 0) {
-            const cudaError_t e = batch_dtw_grid(dc.dm, &dc.grid);
-            if (e != cudaSuccess) {
-                delete p;
-                return cuda_err(e);
-            }
-            p->classes.push_back(dc);
+        const cudaError_t e = batch_dtw_grid(dc.R, dc.dm, &dc.grid);
+        if (e != cudaSuccess) {
+            delete p;
+            return cuda_err(e);
         }
+        p->classes.push_back(dc);
     }
     std::vector<BatchItem> items;
     for (int k : order)
@@ -833,11 +699,13 @@ cudaError_t enqueue_plan(BatchPlan *p, cudaStream_t s, long long spin_limit) {
     k_batch_front<<<p->grid_front, kBatchThreads, kBatchSmem, s>>>(p->d_sets, p->d_items, 0, p->front_end, p->d_ctl,
                                                                    spin_limit);
     for (const auto &c : p->classes)
-        if ((e = launch_batch_dtw(c.dm, c.grid, s, p->d_sets, p->d_order + c.off, c.n, 0, p->d_ctl)) != cudaSuccess)
+        if ((e = launch_batch_dtw(c.R, c.dm, c.grid, s, p->d_sets, p->d_order + c.off, c.n, 0, p->d_ctl)) !=
+            cudaSuccess)
             return e;
     k_batch_mid<<<p->grid_mid, kBatchThreads, 0, s>>>(p->d_sets, p->d_items, p->front_end, p->mid_end, p->d_ctl);
     for (const auto &c : p->classes)
-        if ((e = launch_batch_dtw(c.dm, c.grid, s, p->d_sets, p->d_order + c.off, c.n, 1, p->d_ctl)) != cudaSuccess)
+        if ((e = launch_batch_dtw(c.R, c.dm, c.grid, s, p->d_sets, p->d_order + c.off, c.n, 1, p->d_ctl)) !=
+            cudaSuccess)
             return e;
     k_batch_refine<<<p->grid_refine, kBatchThreads, kBatchSmem, s>>>(p->d_sets, p->d_items, p->mid_end, p->n_items,
                                                                      p->d_ctl);
@@ -979,6 +847,22 @@ int tcdtw_batch_nn(const tcdtw_dataset *sets, int32_t nsets, const tcdtw_opts *o
     }
     if (stats) stats->pairs = pairs;
     return TCDTW_OK;
+}
+
+int tcdtw_batch_tiles(const tcdtw_dataset *sets, int32_t nsets, const tcdtw_opts *opts, int32_t *R, int32_t *G,
+                      void *stream) {
+    if (nsets < 0 || (nsets > 0 && (!sets || !R || !G))) return TCDTW_ERR_INVALID;
+    tcdtw_opts o;
+    if (opts) o = *opts; else tcdtw_default_opts(&o);
+    for (int32_t k = 0; k < nsets; ++k) {
+        const tcdtw_dataset &d = sets[k];
+        if (d.N < 1 || d.L < 1 || d.D < 1 || d.W < 0 || d.K < 1 || d.M < 0 || !d.cand) return TCDTW_ERR_INVALID;
+        R[k] = G[k] = 0;
+        if (d.M == 0 || !graph_path_ok(d, o)) continue;
+        choose_batch_tile(d, d.W > d.L - 1 ? d.L - 1 : d.W, (cudaStream_t)stream, &R[k], &G[k]);
+    }
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? TCDTW_OK : cuda_err(e);
 }
 
 // Free every cached batch sequence (graph and workspace); the next tcdtw_batch_nn
