@@ -181,6 +181,9 @@ def batched_leg(tc, dev, reps=5):
             ts.append(e0.elapsed_time(e1))
         return statistics.median(ts)
 
+    t0 = time.perf_counter()
+    tiles = tc.batch_tiles(sets)
+    tune_s = time.perf_counter() - t0
     _, st = tc.batch_nn(sets, out=out, stats=True)
     l0 = tc.kernel_launches()
     b_ms = timed(lambda: tc.batch_nn(sets, out=out))
@@ -204,7 +207,10 @@ def batched_leg(tc, dev, reps=5):
             "dtw_cells": st["cells"], "cell_updates_per_s": st["cells"] / (b_ms / 1e3),
             "pruning_rate": 1.0 - st["dtw_started"] / st["pairs"], "kernels_per_call": int(b_launches),
             "per_set_calls_ms": s_ms, "speedup_vs_per_set_calls": s_ms / b_ms, "same_indices": same,
-            "generation_s": gen_s, "note": "device-resident inputs, L2 not flushed (5.8 GB of candidates >> L2)"}
+            "tiles_R_G": tiles, "tile_choice_s": tune_s,
+            "tile_shapes_L_D_W": [[w.spec.L, w.spec.D, w.W] for w in wls],
+            "generation_s": gen_s, "note": "device-resident inputs, L2 not flushed (5.8 GB of candidates >> L2); "
+                                           "per-set band tiles from the single-set tuner (tiles_R_G)"}
 
 
 def _fill_large_chunk(args):
@@ -320,16 +326,19 @@ def reverse_lb_leg(tc, cand, q, wl, flush, stream, ms_default, reps=5):
 
 
 def ti_variants_leg(tc, cand, q, wl, flush, stream, reps=3):
-    """Ablation of the LB_TI variants (Section 4.2) on the benchmark search: each one
-    alone behind LB_MV on every survivor (LB_PC off, TI gate e = 0), and LB_MV alone."""
+    """Ablation of the tight bounds on a search: each LB_TI variant (Section 4.2) and
+    LB_PC (Section 5) alone behind LB_MV on every survivor (gate e = 0), and LB_MV
+    alone."""
     import torch
     L = wl.spec.L
-    cases = [("lb_mv_only", dict(use_ti=0)), ("tip_top_P5", dict(P=5, ti_top=1)), ("tip_P5", dict(P=5, ti_top=0)),
-             ("top", dict(P=L, ti_top=1)), ("basic", dict(P=L, ti_top=0))]
+    ti = dict(use_pc=0, use_ti=1, e_ti=0.0)
+    cases = [("lb_mv_only", dict(use_pc=0, use_ti=0)), ("tip_top_P5", dict(ti, P=5, ti_top=1)),
+             ("tip_P5", dict(ti, P=5, ti_top=0)), ("top", dict(ti, P=L, ti_top=1)), ("basic", dict(ti, P=L, ti_top=0)),
+             ("lb_pc_Lq2", dict(use_pc=1, use_ti=0, e_pc=0.0, Lq=2)), ("lb_pc_Lq3", dict(use_pc=1, use_ti=0, e_pc=0.0, Lq=3))]
     out = {}
     o = (torch.empty(wl.M, dtype=torch.int64, device=q.device), torch.empty(wl.M, dtype=torch.float64, device=q.device))
     for name, kw in cases:
-        x = tc.Index(cand, wl.W, wl.K, select=0, use_pc=0, use_ti=kw.pop("use_ti", 1), e_ti=0.0, **kw)
+        x = tc.Index(cand, wl.W, wl.K, select=0, **kw)
         _, _, st = x.nn(q, stats=True)
         for _ in range(2):
             x.nn(q, out=o)
@@ -344,9 +353,10 @@ def ti_variants_leg(tc, cand, q, wl, flush, stream, reps=3):
             e1.synchronize()
             tot += e0.elapsed_time(e1)
         x.close()
-        out[name] = {"ms_per_step": tot / reps, "pruned_ti": st["pruned_ti"], "dtw_started": st["dtw_started"],
-                     "cells": st["cells"]}
-    out["note"] = "each variant alone behind LB_MV on every survivor (e_ti = 0, LB_PC off); P = L: no periodic rows"
+        out[name] = {"ms_per_step": tot / reps, "pruned_ti": st["pruned_ti"], "pruned_pc": st["pruned_pc"],
+                     "dtw_started": st["dtw_started"], "cells": st["cells"]}
+    out["note"] = ("each bound alone behind LB_MV on every survivor (gate e = 0): the LB_TI variants (P = L: no "
+                   "periodic exact rows) and LB_PC with Lq = 2, 3")
     return out
 
 

@@ -508,6 +508,12 @@ struct BatchPlan {
     cudaGraphExec_t exec = nullptr;
     int launches = 0;
     unsigned long long last_use = 0;
+    // the tile classes of a phase are independent (different sets): they run on side
+    // streams forked from and joined back to the caller's stream, so that one class's
+    // tail (its last, longest pairs on a few warps) overlaps the others' work
+    static constexpr int kSide = 4;
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t ev_fork[2] = {}, ev_join[2][kSide] = {};
 };
 std::vector<BatchPlan *> g_plans;
 std::mutex g_plans_mu;
@@ -516,6 +522,13 @@ unsigned long long g_plan_clock = 0;
 void free_plan(BatchPlan *p) {
     if (!p) return;
     if (p->exec) cudaGraphExecDestroy(p->exec);
+    for (int k = 0; k < BatchPlan::kSide; ++k) {
+        if (p->side[k]) cudaStreamDestroy(p->side[k]);
+        for (int ph = 0; ph < 2; ++ph)
+            if (p->ev_join[ph][k]) cudaEventDestroy(p->ev_join[ph][k]);
+    }
+    for (int ph = 0; ph < 2; ++ph)
+        if (p->ev_fork[ph]) cudaEventDestroy(p->ev_fork[ph]);
     cudaFree(p->arena);
     delete p;
 }
@@ -675,6 +688,12 @@ int build_plan(const tcdtw_dataset *sets, const std::vector<int> &mk, const tcdt
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(p->d_order, dtw_order.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (int k = 0; k < BatchPlan::kSide && e == cudaSuccess; ++k) {
+        e = cudaStreamCreateWithFlags(&p->side[k], cudaStreamNonBlocking);
+        for (int ph = 0; ph < 2 && e == cudaSuccess; ++ph)
+            e = cudaEventCreateWithFlags(&p->ev_join[ph][k], cudaEventDisableTiming);
+    }
+    for (int ph = 0; ph < 2 && e == cudaSuccess; ++ph) e = cudaEventCreateWithFlags(&p->ev_fork[ph], cudaEventDisableTiming);
     if (e == cudaSuccess) e = kernel_grid((const void *)k_batch_front, kBatchSmem, &p->grid_front);
     if (e == cudaSuccess) e = kernel_grid((const void *)k_batch_mid, 0, &p->grid_mid);
     if (e == cudaSuccess) e = kernel_grid((const void *)k_batch_refine, kBatchSmem, &p->grid_refine);
@@ -692,21 +711,38 @@ int build_plan(const tcdtw_dataset *sets, const std::vector<int> &mk, const tcdt
 
 int kernels_per_run(const BatchPlan *p) { return 3 + 2 * (int)p->classes.size(); }
 
+// One DTW phase: the classes (largest first) round robin over the side streams, each
+// side stream ordered after the work already on s and s after all of them.
+cudaError_t run_dtw_classes(BatchPlan *p, cudaStream_t s, int phase) {
+    const int nc = (int)p->classes.size();
+    if (nc == 1) {
+        const auto &c = p->classes[0];
+        return launch_batch_dtw(c.R, c.dm, c.grid, s, p->d_sets, p->d_order + c.off, c.n, phase, p->d_ctl);
+    }
+    const int ns = nc < BatchPlan::kSide ? nc : BatchPlan::kSide;
+    cudaError_t e = cudaEventRecord(p->ev_fork[phase], s);
+    for (int k = 0; k < ns && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(p->side[k], p->ev_fork[phase], 0);
+    for (int i = 0; i < nc && e == cudaSuccess; ++i) {
+        const auto &c = p->classes[i];
+        e = launch_batch_dtw(c.R, c.dm, c.grid, p->side[i % ns], p->d_sets, p->d_order + c.off, c.n, phase,
+                             p->d_ctl);
+    }
+    for (int k = 0; k < ns && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(p->ev_join[phase][k], p->side[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join[phase][k], 0);
+    }
+    return e;
+}
+
 cudaError_t enqueue_plan(BatchPlan *p, cudaStream_t s, long long spin_limit) {
     cudaError_t e = cudaMemsetAsync(p->d_ctl, 0, sizeof(BatchCtl), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_counts, 0, sizeof(int) * kCntPerSet * p->n_sets, s);
     if (e != cudaSuccess) return e;
     k_batch_front<<<p->grid_front, kBatchThreads, kBatchSmem, s>>>(p->d_sets, p->d_items, 0, p->front_end, p->d_ctl,
                                                                    spin_limit);
-    for (const auto &c : p->classes)
-        if ((e = launch_batch_dtw(c.R, c.dm, c.grid, s, p->d_sets, p->d_order + c.off, c.n, 0, p->d_ctl)) !=
-            cudaSuccess)
-            return e;
+    if ((e = run_dtw_classes(p, s, 0)) != cudaSuccess) return e;
     k_batch_mid<<<p->grid_mid, kBatchThreads, 0, s>>>(p->d_sets, p->d_items, p->front_end, p->mid_end, p->d_ctl);
-    for (const auto &c : p->classes)
-        if ((e = launch_batch_dtw(c.R, c.dm, c.grid, s, p->d_sets, p->d_order + c.off, c.n, 1, p->d_ctl)) !=
-            cudaSuccess)
-            return e;
+    if ((e = run_dtw_classes(p, s, 1)) != cudaSuccess) return e;
     k_batch_refine<<<p->grid_refine, kBatchThreads, kBatchSmem, s>>>(p->d_sets, p->d_items, p->mid_end, p->n_items,
                                                                      p->d_ctl);
     note_launches(kernels_per_run(p));

@@ -292,32 +292,63 @@ __global__ void __launch_bounds__(128) k_lb_pc_list(PairListArgs a, const float 
     if (lane == 0 && pruned && stat_pruned) atomicAdd(stat_pruned, pruned);
 }
 
+// One warp per listed pair; the block takes runs of kTiChunk consecutive entries (the
+// survivor lists are ordered by query, so a run rarely spans two queries) and stages
+// the query of the run's first entry -- its points and the [dq_lo, dq_hi] interval of
+// its neighbour distances -- in shared memory when they fit (sq_floats > 0); entries
+// of another query read theirs from global memory.
+constexpr int kTiChunk = 64;
+
 template <int DMAX>
 __global__ void __launch_bounds__(128) k_lb_ti_list(PairListArgs a, const float *__restrict__ dq_lo,
                                                     const float *__restrict__ dq_hi, int P,
                                                     const unsigned long long *bsf, float rho, float e_gate,
-                                                    unsigned long long *stat_pruned) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+                                                    unsigned long long *stat_pruned, int stage) {
+    extern __shared__ float sq[];  // [L][D] query points, [L] dq_lo, [L] dq_hi
+    __shared__ int64_t s_m;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t n_entries = a.count ? (int64_t)*a.count : a.n_static;
+    const int L = a.L, D = a.D;
     unsigned long long pruned = 0;
-    for (int64_t e = warp; e < n_entries; e += nwarps) {
-        const uint32_t pid = a.pairs[e];
-        if (pid == 0xffffffffu) continue;
-        const float cur = a.lb[e];
-        if (!(cur < TC_INF)) continue;
-        const int64_t m = pid / (uint64_t)a.N, n = pid - m * a.N;
-        const unsigned long long key = ld_volatile_u64(bsf + m);
-        if (cur > prune_threshold(key, rho)) continue;  // dropped (and counted) by the DTW stage
-        if (!(cur > e_gate * best_dist(key))) continue;
-        float bound;
-        const bool dropped = lb_ti_pair<DMAX>(a.C + (size_t)n * a.L * a.D, a.Q + (size_t)m * a.L * a.D,
-                                              dq_lo + (size_t)m * a.L, dq_hi + (size_t)m * a.L, a.L, a.D, a.W, P,
-                                              bsf + m, rho, &bound);
-        if (lane == 0) {
-            if (dropped) { a.lb[e] = TC_INF; ++pruned; }
-            else a.lb[e] = fmaxf(cur, bound);
+    for (int64_t c0 = (int64_t)blockIdx.x * kTiChunk; c0 < n_entries; c0 += (int64_t)gridDim.x * kTiChunk) {
+        const int64_t c1 = min(c0 + kTiChunk, n_entries);
+        if (stage) {
+            __syncthreads();  // the previous run is done with the staged query
+            if (threadIdx.x == 0) {
+                const uint32_t pid = a.pairs[c0];
+                s_m = pid == 0xffffffffu ? -1 : (int64_t)(pid / (uint64_t)a.N);
+            }
+            __syncthreads();
+            if (s_m >= 0) {
+                const float *qm = a.Q + (size_t)s_m * L * D;
+                for (int k = threadIdx.x; k < L * D; k += blockDim.x) sq[k] = __ldg(qm + k);
+                for (int k = threadIdx.x; k < L; k += blockDim.x) {
+                    sq[L * D + k] = __ldg(dq_lo + (size_t)s_m * L + k);
+                    sq[L * D + L + k] = __ldg(dq_hi + (size_t)s_m * L + k);
+                }
+            }
+            __syncthreads();
+        }
+        for (int64_t e = c0 + warp; e < c1; e += 4) {
+            const uint32_t pid = a.pairs[e];
+            if (pid == 0xffffffffu) continue;
+            const float cur = a.lb[e];
+            if (!(cur < TC_INF)) continue;
+            const int64_t m = pid / (uint64_t)a.N, n = pid - m * a.N;
+            const unsigned long long key = ld_volatile_u64(bsf + m);
+            if (cur > prune_threshold(key, rho)) continue;  // dropped (and counted) by the DTW stage
+            if (!(cur > e_gate * best_dist(key))) continue;
+            const bool staged = stage && m == s_m;
+            const float *qp = staged ? sq : a.Q + (size_t)m * L * D;
+            const float *dl = staged ? sq + L * D : dq_lo + (size_t)m * L;
+            const float *dh = staged ? sq + L * D + L : dq_hi + (size_t)m * L;
+            float bound;
+            const bool dropped = lb_ti_pair<DMAX>(a.C + (size_t)n * L * D, qp, dl, dh, L, D, a.W, P, bsf + m, rho,
+                                                  &bound);
+            if (lane == 0) {
+                if (dropped) { a.lb[e] = TC_INF; ++pruned; }
+                else a.lb[e] = fmaxf(cur, bound);
+            }
         }
     }
     if (lane == 0 && pruned && stat_pruned) atomicAdd(stat_pruned, pruned);
@@ -384,8 +415,13 @@ cudaError_t launch_lb_pc_list(const PairListArgs &a, const float *boxes, const i
 cudaError_t launch_lb_ti_list(const PairListArgs &a, const float *dq_lo, const float *dq_hi, int P,
                               const unsigned long long *bsf, float rho, float e_gate, unsigned long long *stat_pruned,
                               int64_t n_hint, int sms, cudaStream_t s) {
-    const int blocks = list_blocks(n_hint, sms);
-#define TC_TI_CALL(DM) k_lb_ti_list<DM><<<blocks, 128, 0, s>>>(a, dq_lo, dq_hi, P, bsf, rho, e_gate, stat_pruned)
+    int blocks = (int)((n_hint + kTiChunk - 1) / kTiChunk);
+    if (blocks > sms * 16) blocks = sms * 16;
+    if (blocks < 1) blocks = 1;
+    const size_t sq = (size_t)a.L * (a.D + 2) * sizeof(float);
+    const int stage = sq <= 32 * 1024;  // the staged query in shared memory (else global memory)
+#define TC_TI_CALL(DM) \
+    k_lb_ti_list<DM><<<blocks, 128, stage ? sq : 0, s>>>(a, dq_lo, dq_hi, P, bsf, rho, e_gate, stat_pruned, stage)
     TC_DMAX_DISPATCH(a.D, TC_TI_CALL); note_launch();
 #undef TC_TI_CALL
     return cudaGetLastError();

@@ -315,43 +315,98 @@ __device__ __forceinline__ void exact_interval(const float *__restrict__ qi, con
     *hi = __fsqrt_ru(sh);
 }
 
+// |q_i - x| as an interval [lo, hi] from one FP32 sum.  s = sum_p (q_p - x_p)^2 with
+// round-to-nearest subtractions and fused multiply-adds: s lies within a factor
+// (1 +- u)^2 (1 +- g_D) of the exact squared distance S (g_D = D u / (1 - D u), u =
+// 2^-24), and r = sqrt(s) correctly rounded within (1 +- u) of sqrt(s), so sqrt(S) lies
+// in [r (1 - k), r (1 + k)] with k = (D + 4) u (covering 2u + g_D / 2 + O(u^2)).  The
+// factors are applied with directed rounding (klo = 1 - k rounded down, khi = 1 + k
+// rounded up), and 2^-70 of absolute slack covers terms that fall into the subnormal
+// range (D terms of at most 2^-150 absolute error each; sqrt(64 * 2^-149) < 2^-70).
+// One square root per exact cell instead of two directed-rounding ones.
+template <int DMAX>
+__device__ __forceinline__ void exact_interval(const float *qi, const float (&x)[DMAX], int D, float klo, float khi,
+                                               float *lo, float *hi) {
+    float sum = 0.f;
+#pragma unroll
+    for (int p = 0; p < DMAX; ++p) {
+        if (p < D) {
+            const float d = __fsub_rn(qi[p], x[p]);
+            sum = __fmaf_rn(d, d, sum);
+        }
+    }
+    const float r = __fsqrt_rn(sum);
+    const float slack = 8.470329472543003e-22f;  // 2^-70
+    *lo = fmaxf(__fsub_rd(__fmul_rd(r, klo), slack), 0.f);
+    *hi = __fadd_ru(__fmul_ru(r, khi), slack);
+}
+
+// The relative widening factors of exact_interval for D dimensions.
+__device__ __forceinline__ void exact_interval_factors(int D, float *klo, float *khi) {
+    const float k = (float)(D + 4) * 5.9604644775390625e-8f;  // (D + 4) * 2^-24, exact
+    *klo = __fsub_rd(1.f, k);
+    *khi = __fadd_ru(1.f, k);
+}
+
 // LB_TI, TIP_TOP (Section 4).  Lane = candidate point j (column of the cost matrix);
 // the rows of its window are i in [i0, i1] = [max(0, j-W), min(L-1, j+W)].  Row i0 is
 // exact (the top of the window of row j-W, or row 0, and 0 mod P == 0); rows with
 // i mod P == 0 are exact; the others follow Lb = max(Lb - dq_i, dq_i - Ub, 0),
 // Ub = Ub + dq_i with dq_i rounded up where it is subtracted from Lb / added to Ub
 // and rounded down where Ub is subtracted from it.  bound = sum_j (min_i Lb)^2.
-template <int DMAX, bool kCoherent = false>
-__device__ __forceinline__ bool lb_ti_pair(const float *__restrict__ c, const float *__restrict__ q,
-                                           const float *__restrict__ dql, const float *__restrict__ dqh, int L, int D,
-                                           int W, int P, const unsigned long long *bsf_m, float rho, float *bound) {
+// Each lane carries two columns (j and j + 32) through their windows together: two
+// independent chains of the row recursion.  q, dql, dqh may point to shared memory
+// (a staged query) or to global memory.  Abandons against the live threshold every
+// 64 columns.
+template <int DMAX>
+__device__ __forceinline__ bool lb_ti_pair(const float *__restrict__ c, const float *q, const float *dql,
+                                           const float *dqh, int L, int D, int W, int P,
+                                           const unsigned long long *bsf_m, float rho, float *bound) {
     const int lane = threadIdx.x & 31;
+    float klo, khi;
+    exact_interval_factors(D, &klo, &khi);
     float acc = 0.f;
-    for (int j0 = 0; j0 < L; j0 += 32) {
-        const int j = j0 + lane;
-        if (j < L) {
-            float x[DMAX];
+    for (int j0 = 0; j0 < L; j0 += 64) {
+        float x[2][DMAX];
+        int i0[2], i1[2], nx[2];
+        float lbv[2], ubv[2], mj[2];
+        bool on[2];
 #pragma unroll
-            for (int p = 0; p < DMAX; ++p) x[p] = p < D ? __ldg(c + (size_t)j * D + p) : 0.f;
-            const int i0 = max(0, j - W), i1 = min(L - 1, j + W);
-            float lbv, ubv;
-            exact_interval<DMAX>(q + (size_t)i0 * D, x, D, &lbv, &ubv);
-            float mj = lbv;
-            int next_exact = (i0 / P + 1) * P;
-            for (int i = i0 + 1; i <= i1; ++i) {
-                if (i == next_exact) {
-                    exact_interval<DMAX>(q + (size_t)i * D, x, D, &lbv, &ubv);
-                    next_exact += P;
-                } else {
-                    const float dl = ld_q<kCoherent>(dql + i), dh = ld_q<kCoherent>(dqh + i);
-                    const float nl = fmaxf(fmaxf(__fsub_rd(lbv, dh), __fsub_rd(dl, ubv)), 0.f);
-                    ubv = __fadd_ru(ubv, dh);
-                    lbv = nl;
-                }
-                mj = fminf(mj, lbv);
-            }
-            acc = __fmaf_rd(mj, mj, acc);
+        for (int u = 0; u < 2; ++u) {
+            const int j = j0 + lane + 32 * u;
+            on[u] = j < L;
+            const int jj = on[u] ? j : L - 1;
+#pragma unroll
+            for (int p = 0; p < DMAX; ++p) x[u][p] = p < D ? __ldg(c + (size_t)jj * D + p) : 0.f;
+            i0[u] = max(0, jj - W);
+            i1[u] = min(L - 1, jj + W);
+            exact_interval<DMAX>(q + (size_t)i0[u] * D, x[u], D, klo, khi, &lbv[u], &ubv[u]);
+            mj[u] = lbv[u];
+            nx[u] = (i0[u] / P + 1) * P;
         }
+        // rows by offset t from each column's window top: both chains advance together
+        const int span = max(i1[0] - i0[0], i1[1] - i0[1]);
+        for (int t = 1; t <= span; ++t) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int i = i0[u] + t;
+                if (i <= i1[u]) {
+                    if (i == nx[u]) {
+                        exact_interval<DMAX>(q + (size_t)i * D, x[u], D, klo, khi, &lbv[u], &ubv[u]);
+                        nx[u] += P;
+                    } else {
+                        const float dl = dql[i], dh = dqh[i];
+                        const float nl = fmaxf(fmaxf(__fsub_rd(lbv[u], dh), __fsub_rd(dl, ubv[u])), 0.f);
+                        ubv[u] = __fadd_ru(ubv[u], dh);
+                        lbv[u] = nl;
+                    }
+                    mj[u] = fminf(mj[u], lbv[u]);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+            if (on[u]) acc = __fmaf_rd(mj[u], mj[u], acc);
         const float tot = warp_sum_rd(acc);
         if (tot > prune_threshold(ld_volatile_u64(bsf_m), rho)) return true;
     }

@@ -205,3 +205,56 @@ def test_batch_rejects_bad_descriptors():
     with pytest.raises(tc.TcdtwError) as ei:
         tc.batch_nn(sets, seed_s=9)
     assert ei.value.code == tc.ERR_INVALID
+
+
+def test_batch_tiles_are_the_tuners_choice():
+    """Each set of the batched path runs on the band tile the single-set tuner picks
+    for its (L, D, W) on its candidates: the same (R, G) as an index of that set reports
+    when the batched launches compile the tile, valid (no overlap of a lane's virtual
+    lanes) in every case; sets outside the batched family report (0, 0)."""
+    shapes = UNEVEN + [(2, 50, 40, 20, 4, 4)]        # D = 20: searched one at a time
+    host, sets = _make(shapes, seed0=70)
+    tiles = tc.batch_tiles(sets)
+    assert len(tiles) == len(sets)
+    for (M, N, L, D, W, K), s, (R, G) in zip(shapes, sets, tiles):
+        if D > 12:
+            assert (R, G) == (0, 0)
+            continue
+        Wc = min(W, L - 1)
+        assert R in (4, 8, 16) and G in (4, 8, 16, 32) and G * (R + 1) >= 2 * Wc + R, (L, D, W, R, G)
+        x = tc.Index(s["cand"], W, K)
+        info = x.info()
+        x.close()
+        if info["DM"] == D:
+            assert (info["R"], info["G"]) == (R, G), (L, D, W, info, R, G)
+    outs = tc.batch_nn(sets)
+    _check(host, outs)
+
+
+def test_tune_cache_file_is_written_and_read(tmp_path):
+    """TCDTW_TUNE_CACHE: a process that tunes a shape appends its choice to the file; a
+    later process reads the file and uses the stored choice without tuning (here a
+    stored, valid but deliberately different G is taken as given)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    path = tmp_path / "tune.txt"
+    prog = ("import sys, torch, numpy as np; sys.path.insert(0, %r); import paper_2101_07731_gb300 as tc; "
+            "c = torch.from_numpy(np.random.default_rng(0).standard_normal((300, 60, 3)).astype(np.float32)).cuda(); "
+            "x = tc.Index(c, 5, 4); i = x.info(); print(i['tile'], i['G'])" % root)
+    env = dict(os.environ, TCDTW_TUNE_CACHE=str(path))
+    r = subprocess.run([sys.executable, "-c", prog], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    tile, G = map(int, r.stdout.split()[-2:])
+    lines = path.read_text().splitlines()
+    assert len(lines) == 1
+    f = lines[0].split()
+    assert f[0] == "tcdtw-tune" and list(map(int, f[3:])) == [60, 3, 5, tile, G]
+    # a stored choice with another valid G (W = 5: G = 32 is valid for every tile) is used as is
+    G2 = 32 if G != 32 else 16
+    path.write_text(" ".join(f[:7]) + f" {G2}\n")
+    r = subprocess.run([sys.executable, "-c", prog], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert list(map(int, r.stdout.split()[-2:])) == [tile, G2]
+    assert len(path.read_text().splitlines()) == 1          # nothing tuned, nothing appended
