@@ -475,29 +475,36 @@ def _peaks():
         return {}
 
 
-def _profile_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary of `kernel`, if the
-    kernel source has not changed since the capture (else None)."""
-    path = os.path.join(ROOT, "profiles", f"ncu_{kernel}.md")
+def _profile_traffic(profile: str, pairs=None):
+    """DRAM bytes per launch from the committed ncu summary profiles/<profile>.md, if the
+    kernel source has not changed since the capture (else None): the recorded bytes per
+    launch, or the recorded bytes per pair times `pairs` (a capture of a smaller launch
+    of the same kernel scaled to the timed one)."""
+    path = os.path.join(ROOT, "profiles", f"{profile}.md")
     try:
         text = open(path).read()
     except OSError:
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    mp = re.search(r"traffic_bytes_per_pair:\s*([0-9.eE+]+)", text)
     h = re.search(r"source_sha256:\s*([0-9a-f]+)", text)
     src = re.search(r"source_file:\s*(\S+)", text)
-    if not (m and h and src):
+    if not ((m or mp) and h and src):
         return None
     try:
         cur = hashlib.sha256(open(os.path.join(ROOT, src.group(1)), "rb").read()).hexdigest()
     except OSError:
         return None
-    return float(m.group(1)) if cur.startswith(h.group(1)) else None
+    if not cur.startswith(h.group(1)):
+        return None
+    if m:
+        return float(m.group(1))
+    return float(mp.group(1)) * pairs if pairs else None
 
 
 # ----------------------------------------------------------------- our arm
 
-def _roofline(stage_ms_step, st, M, N, L, D, n_sm, peaks):
+def _roofline(stage_ms_step, st, M, N, L, D, n_sm, peaks, profile_dtw="ncu_k_dtw_nn", profile_mv="ncu_k_lb_mv"):
     """Roofline of the dominant stage of a search step: algorithmic FP32 flops of the
     stage (DTW: (3D+3) per computed band cell -- D subtractions, D multiplies, D
     additions, two minima and one addition; LB_MV: 4 per element and query) over its
@@ -510,12 +517,14 @@ def _roofline(stage_ms_step, st, M, N, L, D, n_sm, peaks):
     if dtw_s >= mv_s:
         flops, secs, kern = st["cells"] * (3.0 * D + 3.0), dtw_s, "k_dtw_nn"
         what = "DTW stage (seeds + survivors): (3D+3) flops per computed band cell"
+        traffic = _profile_traffic(profile_dtw, st.get("dtw_started"))
     else:
         flops, secs, kern = M * N * L * D * 4.0, mv_s, "k_lb_mv"
         what = "LB_MV stage: 4 flops per (candidate element, query)"
+        traffic = _profile_traffic(profile_mv)
     ach = flops / secs / 1e12
     return {"bound": "alu", "kernel": kern, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-            "traffic": _profile_traffic(kern),
+            "traffic": traffic,
             "peak_note": f"{n_sm} SMs x 128 FP32 lanes x 2 (FMA) x {sm_mhz:.0f} MHz (derived, not measured)",
             "achieved_note": what + ", per step, over its CUDA-event time inside the timed region"}
 
@@ -752,7 +761,11 @@ def run_ours(a):
            "stage_ms_per_step": stage_step, "dtw_tile": index.info(),
            "setup_s": {"generation": gen_s, "build": build_s}}
     res["clocks"] = clocks.summary()
-    res["roofline"] = _roofline(stage_step, per_step, B, N, L, D, n_sm, _peaks())
+    res["roofline"] = _roofline(stage_step, per_step, B, N, L, D, n_sm, _peaks(),
+                                profile_dtw="ncu_k_dtw_nn_6_32_ring_proto_1024x100000")
+    if res["roofline"]["traffic"] is not None:
+        res["roofline"]["traffic_note"] = ("DRAM bytes per pair of an ncu capture of the same kernel (the tuner's "
+                                           "16,384-pair launch on a slice of the workload) x the step's DTW pairs")
     mv_s = stage_step["lb_mv"] / 1e3
     if mv_s > 0:
         hbm = _peaks().get("hbm_gbs", 6790.0)

@@ -127,21 +127,27 @@ constexpr int kAbandonEvery = 8;
 // different cache lines.  In the ring variant (kRing) every lane group keeps in shared
 // memory a ring of the candidate columns its lanes are about to read (RC slots of
 // ring_stride(DM) floats) and a ring of the query rows of its next virtual lanes
-// (kRingRows slots of R*DM floats).  The group fills both with coalesced cp.async
-// copies kRingAhead steps before first use (a prologue covers the first steps) and
-// waits for the fills of kRingAhead steps ago at each step (the candidates stream from
-// HBM: the lookahead covers its latency).  Reads then hit shared
-// memory: a float4 per four dimensions, conflict-free across consecutive columns
+// (kRingRows slots of R*DM floats).  Every kRingFill steps the group fills both with
+// coalesced cp.async copies for the steps of the next kRingAhead periods (a prologue
+// covers the first periods), then waits for the fills of kRingAhead periods ago (the
+// candidates stream from HBM: the lookahead covers its latency, and the fill
+// bookkeeping, commit, wait and warp barriers run once per period).  Reads then hit
+// shared memory: a float4 per four dimensions, conflict-free across consecutive columns
 // because the slot stride is an odd number of 16-byte units.
 // Sizes (checked against the exact schedule for every small (L, W, R, G)): at most G
-// virtual lanes are active at a time, so the columns in use at step t and those
-// filled for step t + kRingAhead span fewer than kRingAhead + G slots; virtual lanes
-// start at most one per step, so kRingAhead + 2 row slots suffice.
-constexpr int kRingAhead = 12;
+// virtual lanes are active at a time, so the columns in use at step t and those filled
+// at t for up to kRingFill*(kRingAhead+1) - 1 steps ahead span fewer than
+// kRingFill*(kRingAhead+1) + G slots; virtual lanes start at most one per step, so
+// kRingFill*(kRingAhead+1) row slots suffice.
+constexpr int kRingFill = 4;
+constexpr int kRingAhead = 3;
 constexpr int kRingRows = 16;
+static_assert(kRingRows >= kRingFill * (kRingAhead + 1), "row ring too small");
 __host__ __device__ constexpr int ring_stride(int DM) { return ((DM / 4) & 1) ? DM + 8 : DM + 4; }
 __host__ __device__ constexpr int ring_cols(int G) {
-    return (kRingAhead + G) <= 8 ? 8 : (kRingAhead + G) <= 16 ? 16 : (kRingAhead + G) <= 32 ? 32 : 64;
+    return (kRingFill * (kRingAhead + 1) + G) <= 16   ? 16
+           : (kRingFill * (kRingAhead + 1) + G) <= 32 ? 32
+                                                       : 64;
 }
 __host__ __device__ constexpr int ring_group_floats(int R, int DM, int G) {
     return ring_cols(G) * ring_stride(DM) + kRingRows * R * DM;
@@ -250,19 +256,21 @@ __device__ __forceinline__ float band_pass(const float *__restrict__ A, const fl
     int col_hi = 0, v_hi = 0;
     const bool ring_vec = ((D & 3) == 0) && (((((uintptr_t)A) | ((uintptr_t)B)) & 15) == 0);
     if (kRing) {
-        // prologue: everything the first kRingAhead steps read, complete before the loop
+        // prologue: everything the first kRingAhead periods read, complete before the loop
         if (!dead)
-            ring_fill<R, DM>(rcols, rrows, RC, A, B, L, D, W, v1, tau0 + kRingAhead - 1, &col_hi, &v_hi, ring_vec, g);
+            ring_fill<R, DM>(rcols, rrows, RC, A, B, L, D, W, v1, tau0 + kRingFill * kRingAhead - 1, &col_hi, &v_hi,
+                             ring_vec, g);
         cp_async_wait_all();
         __syncwarp();
     }
     for (int tau = tau0; tau <= tau_end; ++tau) {
-        if (kRing) {
-            __syncwarp();  // the previous step's reads of the slots refilled below are done
+        if (kRing && ((tau - tau0) & (kRingFill - 1)) == 0) {
+            __syncwarp();  // the earlier steps' reads of the slots refilled below are done
             if (!dead)
-                ring_fill<R, DM>(rcols, rrows, RC, A, B, L, D, W, v1, tau + kRingAhead, &col_hi, &v_hi, ring_vec, g);
+                ring_fill<R, DM>(rcols, rrows, RC, A, B, L, D, W, v1, tau + kRingFill * (kRingAhead + 1) - 1, &col_hi,
+                                 &v_hi, ring_vec, g);
             asm volatile("cp.async.commit_group;\n" ::: "memory");
-            cp_async_wait_ahead();
+            cp_async_wait_ahead();  // the fills of kRingAhead periods ago cover this period
             __syncwarp();
         }
         const float in = __shfl_sync(g.mask, bottom, g.src);

@@ -254,7 +254,7 @@ __device__ inline void seed_topk_row(float *__restrict__ row, int64_t N, int S, 
 // or, for data written earlier in the same launch (kCoherent), through L2 only.
 template <bool kCoherent>
 __device__ __forceinline__ float ld_q(const float *p) {
-    return kCoherent ? __ldcg(p) : __ldg(p);
+    return kCoherent ? __ldcg(p) : *p;  // plain: p may also point to shared memory
 }
 
 __device__ __forceinline__ float warp_sum_rd(float v) {
@@ -296,15 +296,17 @@ __device__ __forceinline__ bool lb_pc_pair(const float *__restrict__ c, const fl
     return false;
 }
 
-// |q_i - c| as an interval: rounded-down / rounded-up Euclidean distance.
+// |q_i - c| as an interval with directed rounding throughout (two sums, two square
+// roots): exact whenever every step is (small-integer series).  Used by the row-sweep
+// variants, whose exact rows are few.
 template <int DMAX>
-__device__ __forceinline__ void exact_interval(const float *__restrict__ qi, const float (&x)[DMAX], int D, float *lo,
-                                               float *hi) {
+__device__ __forceinline__ void exact_interval_rd(const float *__restrict__ qi, const float (&x)[DMAX], int D,
+                                                  float *lo, float *hi) {
     float sl = 0.f, sh = 0.f;
 #pragma unroll
     for (int p = 0; p < DMAX; ++p) {
         if (p < D) {
-            const float y = __ldg(qi + p);
+            const float y = qi[p];
             const float dl = fmaxf(__fsub_rd(x[p], y), __fsub_rd(y, x[p]));
             const float dh = fmaxf(__fsub_ru(x[p], y), __fsub_ru(y, x[p]));
             sl = __fmaf_rd(dl, dl, sl);
@@ -354,10 +356,13 @@ __device__ __forceinline__ void exact_interval_factors(int D, float *klo, float 
 // i mod P == 0 are exact; the others follow Lb = max(Lb - dq_i, dq_i - Ub, 0),
 // Ub = Ub + dq_i with dq_i rounded up where it is subtracted from Lb / added to Ub
 // and rounded down where Ub is subtracted from it.  bound = sum_j (min_i Lb)^2.
-// Each lane carries two columns (j and j + 32) through their windows together: two
-// independent chains of the row recursion.  q, dql, dqh may point to shared memory
-// (a staged query) or to global memory.  Abandons against the live threshold every
-// 64 columns.
+// The lanes of a round take columns of one residue class modulo P (j = r, r+P, ...):
+// their window tops j - W share a residue, so at each step of the row recursion either
+// every lane's row is exact or none is, and the warp does not run both paths every
+// step (with P >= L no row after the top is exact and the columns go in order); each
+// lane carries two columns of the class.  q, dql, dqh may point to shared memory (a
+// staged query) or to global memory.  Abandons against the live threshold after every
+// round.
 template <int DMAX>
 __device__ __forceinline__ bool lb_ti_pair(const float *__restrict__ c, const float *q, const float *dql,
                                            const float *dqh, int L, int D, int W, int P,
@@ -365,50 +370,54 @@ __device__ __forceinline__ bool lb_ti_pair(const float *__restrict__ c, const fl
     const int lane = threadIdx.x & 31;
     float klo, khi;
     exact_interval_factors(D, &klo, &khi);
+    const int nphase = P < L ? P : 1, stride = P < L ? P : 1;
     float acc = 0.f;
-    for (int j0 = 0; j0 < L; j0 += 64) {
-        float x[2][DMAX];
-        int i0[2], i1[2], nx[2];
-        float lbv[2], ubv[2], mj[2];
-        bool on[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int j = j0 + lane + 32 * u;
-            on[u] = j < L;
-            const int jj = on[u] ? j : L - 1;
-#pragma unroll
-            for (int p = 0; p < DMAX; ++p) x[u][p] = p < D ? __ldg(c + (size_t)jj * D + p) : 0.f;
-            i0[u] = max(0, jj - W);
-            i1[u] = min(L - 1, jj + W);
-            exact_interval<DMAX>(q + (size_t)i0[u] * D, x[u], D, klo, khi, &lbv[u], &ubv[u]);
-            mj[u] = lbv[u];
-            nx[u] = (i0[u] / P + 1) * P;
-        }
-        // rows by offset t from each column's window top: both chains advance together
-        const int span = max(i1[0] - i0[0], i1[1] - i0[1]);
-        for (int t = 1; t <= span; ++t) {
+    for (int r = 0; r < nphase; ++r) {
+        // a round: 64 columns of the class, two per lane (two independent chains whose
+        // exact rows fall on the same steps)
+        for (int jb = r; jb < L; jb += 64 * stride) {
+            float x[2][DMAX];
+            float lbv[2], ubv[2], mj[2];
+            int i0[2], i1[2], nx[2];
+            bool on[2];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
-                const int i = i0[u] + t;
-                if (i <= i1[u]) {
-                    if (i == nx[u]) {
-                        exact_interval<DMAX>(q + (size_t)i * D, x[u], D, klo, khi, &lbv[u], &ubv[u]);
-                        nx[u] += P;
-                    } else {
-                        const float dl = dql[i], dh = dqh[i];
-                        const float nl = fmaxf(fmaxf(__fsub_rd(lbv[u], dh), __fsub_rd(dl, ubv[u])), 0.f);
-                        ubv[u] = __fadd_ru(ubv[u], dh);
-                        lbv[u] = nl;
+                const int j = jb + stride * (lane + 32 * u);
+                on[u] = j < L;
+                const int jj = on[u] ? j : L - 1;
+#pragma unroll
+                for (int p = 0; p < DMAX; ++p) x[u][p] = p < D ? __ldg(c + (size_t)jj * D + p) : 0.f;
+                i0[u] = max(0, jj - W);
+                i1[u] = on[u] ? min(L - 1, jj + W) : i0[u];
+                exact_interval<DMAX>(q + (size_t)i0[u] * D, x[u], D, klo, khi, &lbv[u], &ubv[u]);
+                mj[u] = lbv[u];
+                nx[u] = (i0[u] / P + 1) * P;
+            }
+            const int span = max(i1[0] - i0[0], i1[1] - i0[1]);
+            for (int t = 1; t <= span; ++t) {
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int i = i0[u] + t;
+                    if (i <= i1[u]) {
+                        if (i == nx[u]) {
+                            exact_interval<DMAX>(q + (size_t)i * D, x[u], D, klo, khi, &lbv[u], &ubv[u]);
+                            nx[u] += P;
+                        } else {
+                            const float dl = dql[i], dh = dqh[i];
+                            const float nl = fmaxf(fmaxf(__fsub_rd(lbv[u], dh), __fsub_rd(dl, ubv[u])), 0.f);
+                            ubv[u] = __fadd_ru(ubv[u], dh);
+                            lbv[u] = nl;
+                        }
+                        mj[u] = fminf(mj[u], lbv[u]);
                     }
-                    mj[u] = fminf(mj[u], lbv[u]);
                 }
             }
-        }
 #pragma unroll
-        for (int u = 0; u < 2; ++u)
-            if (on[u]) acc = __fmaf_rd(mj[u], mj[u], acc);
-        const float tot = warp_sum_rd(acc);
-        if (tot > prune_threshold(ld_volatile_u64(bsf_m), rho)) return true;
+            for (int u = 0; u < 2; ++u)
+                if (on[u]) acc = __fmaf_rd(mj[u], mj[u], acc);
+            const float tot = warp_sum_rd(acc);
+            if (tot > prune_threshold(ld_volatile_u64(bsf_m), rho)) return true;
+        }
     }
     *bound = warp_sum_rd(acc);
     return false;
@@ -486,7 +495,7 @@ __device__ __forceinline__ float lb_ti_rows_pair(const float *__restrict__ c, co
 #pragma unroll
                 for (int p = 0; p < DMAX; ++p) x[p] = p < D ? __ldg(c + (size_t)j * D + p) : 0.f;
                 float lo, hi;
-                exact_interval<DMAX>(q + (size_t)i * D, x, D, &lo, &hi);
+                exact_interval_rd<DMAX>(q + (size_t)i * D, x, D, &lo, &hi);
                 lb[s] = lo;
                 ub[s] = hi;
                 mn[s] = k == kt ? lo : fminf(mn[s], lo);
