@@ -261,73 +261,43 @@ cudaError_t launch_seed_topk(float *lb, int64_t M, int64_t N, int64_t ldLb, int 
 // current bound lbv[e] (+inf: already dropped).  The gate of selective deployment
 // (Section 6): the tight bound runs only if e_gate * bsf < lbv[e] <= threshold.
 // A pair whose tight bound exceeds the threshold gets lbv[e] = +inf.
-// Runs of kTiChunk consecutive entries per block, as k_lb_ti_list below: the run's query
-// boxes and box counts are staged in shared memory when they fit (stage != 0).
 template <int DMAX>
 __global__ void __launch_bounds__(128) k_lb_pc_list(PairListArgs a, const float *__restrict__ boxes,
                                                     const int32_t *__restrict__ counts, int K, int w,
                                                     const unsigned long long *bsf, float rho, float e_gate,
-                                                    unsigned long long *stat_pruned, int stage);
-
-// One warp per listed pair; the block takes runs of kTiChunk consecutive entries (the
-// survivor lists are ordered by query, so a run rarely spans two queries) and stages
-// the query of the run's first entry in shared memory when it fits; entries of another
-// query read theirs from global memory.
-constexpr int kTiChunk = 64;
-
-template <int DMAX>
-__global__ void __launch_bounds__(128) k_lb_pc_list(PairListArgs a, const float *__restrict__ boxes,
-                                                    const int32_t *__restrict__ counts, int K, int w,
-                                                    const unsigned long long *bsf, float rho, float e_gate,
-                                                    unsigned long long *stat_pruned, int stage) {
-    extern __shared__ float sb[];  // [G][K][2][D] boxes, then [G] counts
-    __shared__ int64_t s_m;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+                                                    unsigned long long *stat_pruned) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t n_entries = a.count ? (int64_t)*a.count : a.n_static;
     const int G = (a.L + w - 1) / w;
-    const int nbox = G * K * 2 * a.D;
-    int32_t *scnt = (int32_t *)(sb + nbox);
     unsigned long long pruned = 0;
-    for (int64_t c0 = (int64_t)blockIdx.x * kTiChunk; c0 < n_entries; c0 += (int64_t)gridDim.x * kTiChunk) {
-        const int64_t c1 = min(c0 + kTiChunk, n_entries);
-        if (stage) {
-            __syncthreads();  // the previous run is done with the staged boxes
-            if (threadIdx.x == 0) {
-                const uint32_t pid = a.pairs[c0];
-                s_m = pid == 0xffffffffu ? -1 : (int64_t)(pid / (uint64_t)a.N);
-            }
-            __syncthreads();
-            if (s_m >= 0) {
-                for (int k = threadIdx.x; k < nbox; k += blockDim.x) sb[k] = __ldg(boxes + (size_t)s_m * nbox + k);
-                for (int k = threadIdx.x; k < G; k += blockDim.x) scnt[k] = __ldg(counts + (size_t)s_m * G + k);
-            }
-            __syncthreads();
-        }
-        for (int64_t e = c0 + warp; e < c1; e += 4) {
-            const uint32_t pid = a.pairs[e];
-            if (pid == 0xffffffffu) continue;
-            const float cur = a.lb[e];
-            if (!(cur < TC_INF)) continue;
-            const int64_t m = pid / (uint64_t)a.N, n = pid - m * a.N;
-            const unsigned long long key = ld_volatile_u64(bsf + m);
-            if (cur > prune_threshold(key, rho)) continue;  // dropped (and counted) by the DTW stage
-            if (!(cur > e_gate * best_dist(key))) continue;
-            const bool staged = stage && m == s_m;
-            float bound;
-            const bool dropped =
-                lb_pc_pair<DMAX>(a.C + (size_t)n * a.L * a.D, staged ? sb : boxes + (size_t)m * nbox,
-                                 staged ? scnt : counts + (size_t)m * G, a.L, a.D, K, w, bsf + m, rho, &bound);
-            if (lane == 0) {
-                if (dropped) { a.lb[e] = TC_INF; ++pruned; }
-                else a.lb[e] = fmaxf(cur, bound);
-            }
+    for (int64_t e = warp; e < n_entries; e += nwarps) {
+        const uint32_t pid = a.pairs[e];
+        if (pid == 0xffffffffu) continue;
+        const float cur = a.lb[e];
+        if (!(cur < TC_INF)) continue;
+        const int64_t m = pid / (uint64_t)a.N, n = pid - m * a.N;
+        const unsigned long long key = ld_volatile_u64(bsf + m);
+        if (cur > prune_threshold(key, rho)) continue;  // dropped (and counted) by the DTW stage
+        if (!(cur > e_gate * best_dist(key))) continue;
+        float bound;
+        const bool dropped = lb_pc_pair<DMAX>(a.C + (size_t)n * a.L * a.D, boxes + (size_t)m * G * K * 2 * a.D,
+                                              counts + (size_t)m * G, a.L, a.D, K, w, bsf + m, rho, &bound);
+        if (lane == 0) {
+            if (dropped) { a.lb[e] = TC_INF; ++pruned; }
+            else a.lb[e] = fmaxf(cur, bound);
         }
     }
     if (lane == 0 && pruned && stat_pruned) atomicAdd(stat_pruned, pruned);
 }
 
-// LB_TI of the listed pairs (same runs and staging as k_lb_pc_list): the staged query
-// is its points and the [dq_lo, dq_hi] interval of its neighbour distances.
+// LB_TI of the listed pairs, one warp per pair.  The block takes runs of kTiChunk
+// consecutive entries (the survivor lists are ordered by query, so a run rarely spans
+// two queries) and stages the query of the run's first entry -- its points and the
+// [dq_lo, dq_hi] interval of its neighbour distances -- in shared memory when it fits;
+// entries of another query read theirs from global memory.
+constexpr int kTiChunk = 64;
 
 template <int DMAX>
 __global__ void __launch_bounds__(128) k_lb_ti_list(PairListArgs a, const float *__restrict__ dq_lo,
@@ -435,13 +405,8 @@ static int list_blocks(int64_t n_entries_hint, int sms) {
 cudaError_t launch_lb_pc_list(const PairListArgs &a, const float *boxes, const int32_t *counts, int K, int w,
                               const unsigned long long *bsf, float rho, float e_gate, unsigned long long *stat_pruned,
                               int64_t n_hint, int sms, cudaStream_t s) {
-    (void)n_hint;  // the entry count is on the device: a full grid, runs taken by striding
-    const int blocks = sms * 16;
-    const int G = (a.L + w - 1) / w;
-    const size_t sb = (size_t)G * K * 2 * a.D * sizeof(float) + (size_t)G * sizeof(int32_t);
-    const int stage = sb <= 32 * 1024;
-#define TC_PC_CALL(DM) \
-    k_lb_pc_list<DM><<<blocks, 128, stage ? sb : 0, s>>>(a, boxes, counts, K, w, bsf, rho, e_gate, stat_pruned, stage)
+    const int blocks = list_blocks(n_hint, sms);
+#define TC_PC_CALL(DM) k_lb_pc_list<DM><<<blocks, 128, 0, s>>>(a, boxes, counts, K, w, bsf, rho, e_gate, stat_pruned)
     TC_DMAX_DISPATCH(a.D, TC_PC_CALL); note_launch();
 #undef TC_PC_CALL
     return cudaGetLastError();

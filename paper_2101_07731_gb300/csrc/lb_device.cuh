@@ -359,10 +359,10 @@ __device__ __forceinline__ void exact_interval_factors(int D, float *klo, float 
 // The lanes of a round take columns of one residue class modulo P (j = r, r+P, ...):
 // their window tops j - W share a residue, so at each step of the row recursion either
 // every lane's row is exact or none is, and the warp does not run both paths every
-// step (with P >= L no row after the top is exact and the columns go in order); each
-// lane carries two columns of the class.  q, dql, dqh may point to shared memory (a
-// staged query) or to global memory.  Abandons against the live threshold after every
-// round.
+// step (with P >= L no row after the top is exact and the columns go in order).  (Two
+// columns of the class per lane, as two interleaved chains, measured slower.)  q, dql,
+// dqh may point to shared memory (a staged query) or to global memory.  Abandons
+// against the live threshold after every round.
 template <int DMAX>
 __device__ __forceinline__ bool lb_ti_pair(const float *__restrict__ c, const float *q, const float *dql,
                                            const float *dqh, int L, int D, int W, int P,
@@ -373,48 +373,31 @@ __device__ __forceinline__ bool lb_ti_pair(const float *__restrict__ c, const fl
     const int nphase = P < L ? P : 1, stride = P < L ? P : 1;
     float acc = 0.f;
     for (int r = 0; r < nphase; ++r) {
-        // a round: 64 columns of the class, two per lane (two independent chains whose
-        // exact rows fall on the same steps)
-        for (int jb = r; jb < L; jb += 64 * stride) {
-            float x[2][DMAX];
-            float lbv[2], ubv[2], mj[2];
-            int i0[2], i1[2], nx[2];
-            bool on[2];
+        for (int jb = r; jb < L; jb += 32 * stride) {
+            const int j = jb + stride * lane;
+            if (j < L) {
+                float x[DMAX];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int j = jb + stride * (lane + 32 * u);
-                on[u] = j < L;
-                const int jj = on[u] ? j : L - 1;
-#pragma unroll
-                for (int p = 0; p < DMAX; ++p) x[u][p] = p < D ? __ldg(c + (size_t)jj * D + p) : 0.f;
-                i0[u] = max(0, jj - W);
-                i1[u] = on[u] ? min(L - 1, jj + W) : i0[u];
-                exact_interval<DMAX>(q + (size_t)i0[u] * D, x[u], D, klo, khi, &lbv[u], &ubv[u]);
-                mj[u] = lbv[u];
-                nx[u] = (i0[u] / P + 1) * P;
-            }
-            const int span = max(i1[0] - i0[0], i1[1] - i0[1]);
-            for (int t = 1; t <= span; ++t) {
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int i = i0[u] + t;
-                    if (i <= i1[u]) {
-                        if (i == nx[u]) {
-                            exact_interval<DMAX>(q + (size_t)i * D, x[u], D, klo, khi, &lbv[u], &ubv[u]);
-                            nx[u] += P;
-                        } else {
-                            const float dl = dql[i], dh = dqh[i];
-                            const float nl = fmaxf(fmaxf(__fsub_rd(lbv[u], dh), __fsub_rd(dl, ubv[u])), 0.f);
-                            ubv[u] = __fadd_ru(ubv[u], dh);
-                            lbv[u] = nl;
-                        }
-                        mj[u] = fminf(mj[u], lbv[u]);
+                for (int p = 0; p < DMAX; ++p) x[p] = p < D ? __ldg(c + (size_t)j * D + p) : 0.f;
+                const int i0 = max(0, j - W), i1 = min(L - 1, j + W);
+                float lbv, ubv;
+                exact_interval<DMAX>(q + (size_t)i0 * D, x, D, klo, khi, &lbv, &ubv);
+                float mj = lbv;
+                int next_exact = (i0 / P + 1) * P;
+                for (int i = i0 + 1; i <= i1; ++i) {
+                    if (i == next_exact) {
+                        exact_interval<DMAX>(q + (size_t)i * D, x, D, klo, khi, &lbv, &ubv);
+                        next_exact += P;
+                    } else {
+                        const float dl = dql[i], dh = dqh[i];
+                        const float nl = fmaxf(fmaxf(__fsub_rd(lbv, dh), __fsub_rd(dl, ubv)), 0.f);
+                        ubv = __fadd_ru(ubv, dh);
+                        lbv = nl;
                     }
+                    mj = fminf(mj, lbv);
                 }
+                acc = __fmaf_rd(mj, mj, acc);
             }
-#pragma unroll
-            for (int u = 0; u < 2; ++u)
-                if (on[u]) acc = __fmaf_rd(mj[u], mj[u], acc);
             const float tot = warp_sum_rd(acc);
             if (tot > prune_threshold(ld_volatile_u64(bsf_m), rho)) return true;
         }
