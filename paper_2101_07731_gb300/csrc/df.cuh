@@ -252,4 +252,118 @@ __device__ double band_pass_df_table(const float2 *cost, int L, int W, const Grp
     return res_h < INF ? __dadd_rn((double)res_h, (double)res_l) : __longlong_as_double(0x7ff0000000000000LL);
 }
 
+// The same sweep with the cost table in global memory, stored in the order the sweep
+// reads it: the R costs lane l uses at step tau (its virtual lane's rows at column
+// tau - v) are entries ((tau * 32 + l) * R + r) (table_dp_pos).  Each lane streams its
+// own 8R bytes per step through a private ring of kDfRing steps in shared memory (ring:
+// 32 * R * kDfRing float2 per warp), copied with cp.async kDfRing steps ahead, so the
+// latency of the table's L2/HBM reads overlaps the sweep instead of stalling every step.
+// Entries the sweep does not use (outside the band, idle lanes) are never written and
+// never read as costs.  Same operations in the same order: bit-identical.
+constexpr int kDfRing = 8;
+
+__host__ __device__ inline size_t table_dp_pos(int tau, int lane, int R, int r) {
+    return ((size_t)tau * 32 + lane) * R + r;
+}
+
+template <int R>
+__device__ __forceinline__ void df_ring_issue(float2 *slot, const float2 *src) {
+    if ((R * 8) % 16 == 0) {
+#pragma unroll
+        for (int k = 0; k < R / 2; ++k) {
+            const unsigned sa = (unsigned)__cvta_generic_to_shared(slot + 2 * k);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src + 2 * k) : "memory");
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const unsigned sa = (unsigned)__cvta_generic_to_shared(slot + k);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(src + k) : "memory");
+        }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+template <int R>
+__device__ double band_pass_df_table_dp(const float2 *cost, int L, int W, const Grp &g, float2 *ring) {
+    const float INF = TC_INF;
+    float ch[R], cl[R];
+    float bot_h = INF, bot_l = 0.f, prev_h = INF, prev_l = 0.f;
+    float res_h = INF, res_l = 0.f;
+    const int nv = (L + R - 1) / R;
+    const int vlast = (L - 1) / R;
+    int v = g.lig;
+    const int tau_end = v_jhi(nv - 1, R, W, L) + (nv - 1);
+    int tlo = v < nv ? v_jlo(v, R, W) + v : 1 << 30;
+    int thi = v < nv ? v_jhi(v, R, W, L) + v : -1;
+    float2 *myring = ring + (size_t)g.lig * R;  // slot s of this lane: myring + s * 32 * R
+    // prologue: the first kDfRing steps in flight
+#pragma unroll
+    for (int s = 0; s < kDfRing; ++s) {
+        if (s <= tau_end) df_ring_issue<R>(myring + (size_t)s * 32 * R, cost + table_dp_pos(s, g.lig, R, 0));
+        else asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) { ch[r] = INF; cl[r] = 0.f; }
+    for (int tau = 0; tau <= tau_end; ++tau) {
+        const int slot = tau % kDfRing;
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(kDfRing - 1) : "memory");  // this step's copy is in
+        float2 c[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) c[r] = myring[(size_t)slot * 32 * R + r];
+        // the slot now holds this step's costs in registers: refill it for step tau + kDfRing
+        if (tau + kDfRing <= tau_end)
+            df_ring_issue<R>(myring + (size_t)slot * 32 * R, cost + table_dp_pos(tau + kDfRing, g.lig, R, 0));
+        else
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+        const float in_h = __shfl_sync(g.mask, bot_h, g.src);
+        const float in_l = __shfl_sync(g.mask, bot_l, g.src);
+        if (tau > thi && v < nv) {
+            v += g.G;
+            tlo = v < nv ? v_jlo(v, R, W) + v : 1 << 30;
+            thi = v < nv ? v_jhi(v, R, W, L) + v : -1;
+#pragma unroll
+            for (int r = 0; r < R; ++r) { ch[r] = INF; cl[r] = 0.f; }
+        }
+        if (tau >= tlo && tau <= thi) {
+            const int j = tau - v;
+            const int i0 = v * R;
+            float up_h = INF, up_l = 0.f, dg_h = INF, dg_l = 0.f;
+            if (v == 0) {
+                if (j == 0) dg_h = 0.f;
+            } else {
+                if (j <= i0 - 1 + W) { up_h = in_h; up_l = in_l; }
+                if (j >= 1 && j <= i0 + W) { dg_h = prev_h; dg_l = prev_l; }
+            }
+            const unsigned vm = row_mask(j - W - i0, min(j + W - i0, L - 1 - i0), R);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float lh = ch[r], ll = cl[r];
+                float vh = INF, vl = 0.f;
+                if ((vm >> r) & 1u) {
+                    float mh = up_h, ml = up_l;
+                    if (df_less(lh, ll, mh, ml)) { mh = lh; ml = ll; }
+                    if (df_less(dg_h, dg_l, mh, ml)) { mh = dg_h; ml = dg_l; }
+                    if (mh < INF) df_add(c[r].x, c[r].y, mh, ml, vh, vl);
+                }
+                dg_h = lh; dg_l = ll;
+                up_h = vh; up_l = vl;
+                ch[r] = vh; cl[r] = vl;
+            }
+            bot_h = ch[R - 1];
+            bot_l = cl[R - 1];
+            if (v == vlast && j == L - 1) {
+                const int rl = (L - 1) - i0;
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (r == rl) { res_h = ch[r]; res_l = cl[r]; }
+            }
+        }
+        prev_h = in_h;
+        prev_l = in_l;
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    return res_h < INF ? __dadd_rn((double)res_h, (double)res_l) : __longlong_as_double(0x7ff0000000000000LL);
+}
+
 }  // namespace tc

@@ -8,9 +8,12 @@
 // 3.4 MB) fell back to one warp doing both, with the cost of 32 dimensions in
 // double-float as one long serial chain per cell (~26 ms for one pair).  Here each
 // block owns a slot of a global-memory table instead: it writes its entry's costs with
-// all threads (coalesced, consecutive cells of the band-major layout), synchronises,
-// and its first warp runs the same band_pass_df_table sweep.  Same operations in the
-// same order, so the value is bit-identical to k_dtw_refine_df and to the
+// all threads, in the order the sweep reads them (per step, the 32 lanes' R costs
+// contiguous: table_dp_pos), synchronises, and its first warp runs
+// band_pass_df_table_dp, which streams each lane's costs through a shared-memory ring
+// of cp.async copies a few steps ahead (a sweep that loaded its costs from the
+// row-major table step by step waited ~3 us per step on L2/HBM).  Same operations in
+// the same order, so the value is bit-identical to k_dtw_refine_df and to the
 // shared-memory table kernel.
 #include "df.cuh"
 #include "dtw_core.cuh"
@@ -18,6 +21,13 @@
 namespace tc {
 
 constexpr int kGtabThreads = 256;
+
+// Steps of the band sweep with R rows per lane: tau in [0, tau_end].
+__host__ __device__ inline int sweep_steps(int L, int W, int R) {
+    const int nv = (L + R - 1) / R;
+    const int jhi = min(L - 1, (nv - 1) * R + R - 1 + W);
+    return jhi + nv;  // tau_end + 1
+}
 
 template <int R, int DM>
 __global__ void __launch_bounds__(kGtabThreads) k_dtw_refine_df_gtab(const float *__restrict__ Q,
@@ -28,8 +38,9 @@ __global__ void __launch_bounds__(kGtabThreads) k_dtw_refine_df_gtab(const float
                                                                      float2 *__restrict__ tab,
                                                                      double *__restrict__ v,
                                                                      unsigned long long *__restrict__ bestdf) {
+    extern __shared__ __align__(16) float2 dring[];  // the sweep warp's ring, 32 * R * kDfRing
     const int E = L * D, BW = 2 * W + 1, cells = L * BW;
-    float2 *cost = tab + (size_t)blockIdx.x * cells;
+    float2 *cost = tab + (size_t)blockIdx.x * sweep_steps(L, W, R) * 32 * R;
     const int n_entries = *count;
     for (int e = blockIdx.x; e < n_entries; e += gridDim.x) {
         const uint32_t pid = pairs[e];
@@ -40,7 +51,7 @@ __global__ void __launch_bounds__(kGtabThreads) k_dtw_refine_df_gtab(const float
         for (int k0 = threadIdx.x; k0 < cells; k0 += 2 * kGtabThreads) {
             float ch[2], cl[2];
             bool in[2];
-            int kk[2];
+            int kk[2], ii[2], jj2[2];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 kk[u] = k0 + u * kGtabThreads;
@@ -48,16 +59,22 @@ __global__ void __launch_bounds__(kGtabThreads) k_dtw_refine_df_gtab(const float
                 const int i = k / BW, j = i + (k - i * BW) - W;
                 in[u] = kk[u] < cells && j >= 0 && j < L;
                 const int jj = in[u] ? j : i;
+                ii[u] = i;
+                jj2[u] = jj;
                 df_cell_cost<DM>(qa + (size_t)i * D, cb + (size_t)jj * D, D, ch[u], cl[u]);
             }
 #pragma unroll
             for (int u = 0; u < 2; ++u)
-                if (in[u]) cost[kk[u]] = make_float2(ch[u], cl[u]);
+                if (in[u]) {
+                    // cell (i, j) is row r of virtual lane vv = i / R, read by lane vv % 32 at step j + vv
+                    const int vv = ii[u] / R, r = ii[u] - vv * R;
+                    cost[table_dp_pos(jj2[u] + vv, vv & 31, R, r)] = make_float2(ch[u], cl[u]);
+                }
         }
         __syncthreads();  // the block's table writes are visible to its first warp
         if (threadIdx.x < 32) {
             Grp g = make_grp(32);
-            double r = band_pass_df_table<R>(cost, L, W, g);
+            double r = band_pass_df_table_dp<R>(cost, L, W, g, dring);
             r = grp_min(r, g);
             if (g.lig == 0) {
                 v[e] = r;
@@ -67,15 +84,18 @@ __global__ void __launch_bounds__(kGtabThreads) k_dtw_refine_df_gtab(const float
     }
 }
 
-size_t refine_gtab_slot_bytes(int L, int W) { return (size_t)L * (2 * W + 1) * sizeof(float2); }
+size_t refine_gtab_slot_bytes(int L, int W) {
+    const int R = refine_rows_for(W);
+    return (size_t)sweep_steps(L, W, R) * 32 * (R > 0 ? R : 1) * sizeof(float2);
+}
 
 // Launch with `slots` blocks (one table slot each; tab holds slots * L*(2W+1) float2).
 cudaError_t dtw_refine_df_gtab_launch(int R, int slots, cudaStream_t s, const DtwRefineArgs &x, float2 *tab) {
     const int dm = x.D <= 8 ? 8 : x.D <= 32 ? 32 : 64;
 #define TC_GT(RV, DMV)                                                                                         \
     if (R == RV && dm == DMV) {                                                                                \
-        k_dtw_refine_df_gtab<RV, DMV><<<slots, kGtabThreads, 0, s>>>(x.Q, x.C, x.L, x.D, x.W, x.N, x.pairs,     \
-                                                                     x.count, tab, x.d64, x.best64);           \
+        k_dtw_refine_df_gtab<RV, DMV><<<slots, kGtabThreads, (size_t)32 * RV * kDfRing * sizeof(float2), s>>>( \
+            x.Q, x.C, x.L, x.D, x.W, x.N, x.pairs, x.count, tab, x.d64, x.best64);                                 \
         note_launch();                                                                                         \
         return cudaGetLastError();                                                                             \
     }
