@@ -60,6 +60,9 @@ def _args():
     ap.add_argument("--no-few", action="store_true", help="skip the few-queries leg")
     ap.add_argument("--queries", type=int, default=0, help="queries of the workload to use (0 = all 1,024)")
     ap.add_argument("--candidates", type=int, default=0, help="candidates to use (0 = all 100,000)")
+    ap.add_argument("--workload", choices=["large", "mid"], default="large",
+                    help="the search the timed steps run: the 1,024 x 100,000 headline (default) or the 256 x "
+                         "20,000 one (for profiler captures of its kernels)")
     return ap.parse_args()
 
 
@@ -86,14 +89,18 @@ def job_value(world, units_per_rank_step, steps, total_ms):
     return world * units_per_rank_step * steps / (total_ms / 1e3)
 
 
-def _config(M, N, extra=None):
-    wl = WORKLOAD
+def _config(M, N, extra=None, wl=None):
+    wl = wl or WORKLOAD
     name = wl.name if (M, N) == (wl.M, wl.N) else f"{wl.name}_slice_{M}q_{N}c"
+    gen = ("prototype-warp, 100 prototypes, sigma 0.2, z-normalised, seed 0" if wl is WORKLOAD else
+           "prototype-warp, 20 prototypes, sigma 0.1, z-normalised, seed 0")
     c = {"workload": name, "M": M, "N": N, "L": wl.spec.L, "D": wl.spec.D, "W": wl.W, "K": wl.K,
          "queries_per_step": min(STEP_QUERIES, M),
          "step": "one exact search of a batch of the queries against all candidates; batches rotate",
-         "generator": "prototype-warp, 100 prototypes, sigma 0.2, z-normalised, seed 0",
-         "l2": "not flushed: inputs (candidates N*L*D*4 bytes) larger than L2", "parallelism": "replicas"}
+         "generator": gen,
+         "l2": ("not flushed: inputs (candidates N*L*D*4 bytes) larger than L2" if wl is WORKLOAD else
+                "not flushed (a profiling run of the mid-size search; its side leg flushes)"),
+         "parallelism": "replicas"}
     if extra:
         c.update(extra)
     return c
@@ -475,7 +482,7 @@ def _peaks():
         return {}
 
 
-def _profile_traffic(profile: str, pairs=None):
+def _profile_traffic(profile: str, pairs=None, candidates=None):
     """DRAM bytes per launch from the committed ncu summary profiles/<profile>.md, if the
     kernel source has not changed since the capture (else None): the recorded bytes per
     launch, or the recorded bytes per pair times `pairs` (a capture of a smaller launch
@@ -489,7 +496,7 @@ def _profile_traffic(profile: str, pairs=None):
     mp = re.search(r"traffic_bytes_per_pair:\s*([0-9.eE+]+)", text)
     h = re.search(r"source_sha256:\s*([0-9a-f]+)", text)
     src = re.search(r"source_file:\s*(\S+)", text)
-    if not ((m or mp) and h and src):
+    if not ((m or mp or re.search(r"traffic_bytes_per_candidate:", text)) and h and src):
         return None
     try:
         cur = hashlib.sha256(open(os.path.join(ROOT, src.group(1)), "rb").read()).hexdigest()
@@ -497,8 +504,11 @@ def _profile_traffic(profile: str, pairs=None):
         return None
     if not cur.startswith(h.group(1)):
         return None
+    mc = re.search(r"traffic_bytes_per_candidate:\s*([0-9.eE+]+)", text)
     if m:
         return float(m.group(1))
+    if mc:
+        return float(mc.group(1)) * candidates if candidates else None
     return float(mp.group(1)) * pairs if pairs else None
 
 
@@ -521,7 +531,7 @@ def _roofline(stage_ms_step, st, M, N, L, D, n_sm, peaks, profile_dtw="ncu_k_dtw
     else:
         flops, secs, kern = M * N * L * D * 4.0, mv_s, "k_lb_mv"
         what = "LB_MV stage: 4 flops per (candidate element, query)"
-        traffic = _profile_traffic(profile_mv)
+        traffic = _profile_traffic(profile_mv, candidates=N)
     ach = flops / secs / 1e12
     return {"bound": "alu", "kernel": kern, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
             "traffic": traffic,
@@ -687,14 +697,14 @@ def run_ours(a):
     dev = torch.device("cuda", local)
     import paper_2101_07731_gb300 as tc
 
-    wl = WORKLOAD
+    wl = WORKLOAD if a.workload == "large" else SIDE
     M = a.queries or wl.M
     N = a.candidates or wl.N
     B = min(STEP_QUERIES, M)
     nb = max(1, M // B)                       # batches of B queries (a ragged rest is not used)
     L, D = wl.spec.L, wl.spec.D
     t0 = time.perf_counter()
-    cand = large_candidates(N, dev)
+    cand = large_candidates(N, dev) if wl is WORKLOAD else torch.from_numpy(wl.candidates(N)).to(dev)
     Qn = wl.queries(M)
     gen_s = time.perf_counter() - t0
     q = torch.from_numpy(Qn).to(dev)
@@ -752,7 +762,7 @@ def run_ours(a):
     res = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": _config(M, N, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
+           "config": _config(M, N, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}, wl),
            "gpu_launches": int(launches),
            "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms)},
            "cell_updates_per_s": {"computed_over_dtw_time": per_step["cells"] / dtw_s if dtw_s > 0 else None,
@@ -763,6 +773,14 @@ def run_ours(a):
     res["clocks"] = clocks.summary()
     res["roofline"] = _roofline(stage_step, per_step, B, N, L, D, n_sm, _peaks(),
                                 profile_dtw="ncu_k_dtw_nn_6_32_ring_proto_1024x100000")
+    # the other large stage against the same FP32 roof
+    other = dict(stage_step)
+    if res["roofline"]["kernel"] == "k_dtw_nn":
+        other["dtw"] = other["seed"] = 0.0
+    else:
+        other["lb_mv"] = 0.0
+    res["roofline_other_stage"] = _roofline(other, per_step, B, N, L, D, n_sm, _peaks(),
+                                            profile_mv="ncu_k_lb_mv_32_proto_1024x100000")
     if res["roofline"]["traffic"] is not None:
         res["roofline"]["traffic_note"] = ("DRAM bytes per pair of an ncu capture of the same kernel (the tuner's "
                                            "16,384-pair launch on a slice of the workload) x the step's DTW pairs")
