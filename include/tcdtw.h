@@ -90,6 +90,15 @@ typedef struct tcdtw_index tcdtw_index; /* opaque; created by tcdtw_build */
  *          P >= L the basic LB_TI, whose only exact row is row 0) (1).  ti_top = 0
  *          needs W <= 127 (else tcdtw_build and tcdtw_lower_bounds return
  *          UNSUPPORTED); tcdtw_batch_nn always uses 1.
+ *  mv_abandon  1 = LB_MV with early abandoning (Section 7.1 applies abandoning to the
+ *          lower bounds as well as to DTW): a block of at least 32 queries sums a prefix
+ *          of every pair's LB_MV elements first (32 * clamp(ceil32(L*D)/512, 1, 8)
+ *          elements), takes seed_s seeds from those prefix sums and runs their DTW,
+ *          then completes LB_MV only for the pairs at or under the seeded threshold
+ *          (the others keep their prefix sum, a lower bound above the threshold), and
+ *          runs the DTW of a second round of seed_s seeds, the smallest completed
+ *          bounds.  Rows of fewer than 128 elements never abandon.  The answers are the
+ *          same (1).
  */
 typedef struct {
     int32_t P;
@@ -108,6 +117,7 @@ typedef struct {
     int32_t select;
     int32_t use_rev;
     int32_t ti_top;
+    int32_t mv_abandon;
 } tcdtw_opts;
 
 /* Counters of one tcdtw_nn call, summed over its queries. */
@@ -124,6 +134,8 @@ typedef struct {
     uint64_t refined64;     /* ... of those, recomputed in FP64 because double-float
                                could not separate them either                      */
     uint64_t pruned_rev;    /* ... pruned by the candidate-side LB_MV (use_rev)      */
+    uint64_t mv_terms;      /* LB_MV terms summed, one per (element, pair); below
+                               pairs*L*D when LB_MV abandons (mv_abandon)          */
 } tcdtw_stats;
 
 /* Fill *opts with the defaults listed above. */
@@ -188,14 +200,16 @@ int tcdtw_index_info(tcdtw_index *index, int32_t *tile, int32_t *G, int32_t *qbl
  * Per-stage timing of tcdtw_nn (tracing; not in the paper).  With profiling on,
  * every query block records CUDA events on the caller's stream at the stage
  * boundaries below and tcdtw_nn synchronises at its end to add the elapsed times.
- * Stages: 0 non-finite scan, 1 query preparation (envelope, dq, boxes), 2 LB_MV,
- * 3 seeds (selection and their DTW), 4 compaction, 5 LB_PC / LB_TI cascade,
- * 6 DTW of the survivors, 7 refine (double-float, then FP64 where needed) and selection.
+ * Stages: 0 non-finite scan, 1 query preparation (envelope, dq, boxes), 2 LB_MV (with
+ * mv_abandon: over the prefix), 3 seeds (selection and their DTW), 4 completion of the
+ * abandoning LB_MV, 5 second seed round (4 and 5 are empty without abandoning),
+ * 6 compaction, 7 LB_PC / LB_TI cascade, 8 DTW of the survivors, 9 refine (double-float,
+ * then FP64 where needed) and selection.
  * tcdtw_set_profiling: enable != 0 turns it on; either way the totals are reset.
  * tcdtw_stage_times: host ms[TCDTW_NUM_STAGES] receives the summed milliseconds,
  * host *blocks (may be NULL) the number of query blocks timed.  Errors: INVALID.
  */
-#define TCDTW_NUM_STAGES 8
+#define TCDTW_NUM_STAGES 10
 int tcdtw_set_profiling(tcdtw_index *index, int32_t enable);
 int tcdtw_stage_times(tcdtw_index *index, double *ms, int64_t *blocks);
 
@@ -270,6 +284,19 @@ int tcdtw_pc_boxes(const float *q, int64_t M, int32_t L, int32_t D, int32_t W, i
 int tcdtw_lower_bounds(const float *q, int64_t M, const float *c, int64_t N, int32_t L, int32_t D,
                        int32_t W, int32_t K, const tcdtw_opts *opts, int32_t which, float *out,
                        void *stream);
+
+/* LB_MV with early abandoning against per-query thresholds (Section 7.1): every pair
+ * first sums a prefix of its elements (the length mv_abandon uses); pairs whose prefix
+ * sum is at most thresh[m] complete the sum, the others stop there.  Hence
+ * out[m][n] <= the exact LB_MV <= DTW(q[m], c[n]); where the computed LB_MV (rounded
+ * down; summation order as in the search, which may differ from tcdtw_lower_bounds in
+ * the last bits) is at most thresh[m], out[m][n] is that value, and elsewhere
+ * out[m][n] > thresh[m].  Rows of fewer than 128 elements (L*D) are summed whole.
+ * q device [M][L][D], c device [N][L][D], thresh device [M] float32 (+inf: every
+ * pair complete), out device [M][N] float32.  Synchronous on `stream`.
+ * Errors: INVALID, UNSUPPORTED (D > 64, M*N >= 4.29e9), NOMEM, CUDA, TIMEOUT. */
+int tcdtw_lb_mv_abandon(const float *q, int64_t M, const float *c, int64_t N, int32_t L, int32_t D,
+                        int32_t W, const float *thresh, float *out, void *stream);
 
 /*
  * tcdtw_lb_mv_noalloc -- the same values as tcdtw_lower_bounds(..., TCDTW_LB_MV, ...)

@@ -53,13 +53,14 @@ class Opts(C.Structure):
                 ("e_ti", C.c_float), ("use_pc", C.c_int32), ("use_ti", C.c_int32),
                 ("seed_s", C.c_int32), ("qblock", C.c_int32), ("tile", C.c_int32),
                 ("check_finite", C.c_int32), ("no_prune", C.c_int32), ("use_graph", C.c_int32),
-                ("select", C.c_int32), ("use_rev", C.c_int32), ("ti_top", C.c_int32)]
+                ("select", C.c_int32), ("use_rev", C.c_int32), ("ti_top", C.c_int32),
+                ("mv_abandon", C.c_int32)]
 
 
 class Stats(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ("pairs", "pruned_mv", "pruned_pc", "pruned_ti", "dtw_started",
                                           "dtw_abandoned", "cells", "refined",
-                                          "refined64", "pruned_rev")]
+                                          "refined64", "pruned_rev", "mv_terms")]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
@@ -88,6 +89,7 @@ _SIGS = {
     "tcdtw_lower_bounds": (C.c_int, [_P, _I64, _P, _I64, _I32, _I32, _I32, _I32, C.POINTER(Opts), _I32, _P,
                                      _P]),
     "tcdtw_compact": (C.c_int, [_P, _I64, _I64, _P, _P, _P, _P]),
+    "tcdtw_lb_mv_abandon": (C.c_int, [_P, _I64, _P, _I64, _I32, _I32, _I32, _P, _P, _P]),
     "tcdtw_lb_mv_noalloc": (C.c_int, [_P, _I64, _P, _I64, _I32, _I32, _I32, _P, _P]),
     "tcdtw_batch_nn": (C.c_int, [C.POINTER(Dataset), _I32, C.POINTER(Opts), C.POINTER(Stats), _P]),
     "tcdtw_batch_selftest_timeout": (C.c_int, [_I64, _P]),
@@ -273,7 +275,7 @@ class Index:
         _call("tcdtw_index_opts", self._h, C.byref(o))
         return {n: getattr(o, n) for n, _ in o._fields_}
 
-    STAGES = ("check", "prep", "lb_mv", "seed", "compact", "cascade", "dtw", "refine")
+    STAGES = ("check", "prep", "lb_mv", "seed", "lb_rest", "seed2", "compact", "cascade", "dtw", "refine")
 
     def set_profiling(self, enable: bool = True):
         """Record per-stage CUDA-event times in every nn() call (synchronises)."""
@@ -414,6 +416,21 @@ def lower_bounds(q: torch.Tensor, c: torch.Tensor, W: int, which: int = LB_MV, K
     o = default_opts(**opts)
     _call("tcdtw_lower_bounds", _ptr(q), M, _ptr(c), N, L, D, int(W), int(K), C.byref(o), int(which), _ptr(out),
           _stream())
+    return out
+
+
+def lb_mv_abandon(q: torch.Tensor, c: torch.Tensor, W: int, thresh: torch.Tensor):
+    """LB_MV of every pair with early abandoning against ``thresh`` ([M] float32):
+    out[m][n] is the (rounded-down) LB_MV where that is at most thresh[m], else a
+    partial sum that already exceeds thresh[m]; always a lower bound of DTW."""
+    q, c = _series(q, "q"), _series(c, "c")
+    M, L, D = q.shape
+    N = c.shape[0]
+    thresh = thresh.contiguous().to(device=q.device, dtype=torch.float32)
+    if thresh.numel() != M:
+        raise ValueError("thresh must hold one threshold per query")
+    out = torch.empty(M, N, dtype=torch.float32, device=q.device)
+    _call("tcdtw_lb_mv_abandon", _ptr(q), M, _ptr(c), N, L, D, int(W), _ptr(thresh), _ptr(out), _stream())
     return out
 
 

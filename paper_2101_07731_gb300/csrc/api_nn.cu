@@ -230,9 +230,9 @@ cudaError_t dalloc(T **p, size_t n) {
 
 enum Counter {
     kStarted = 0, kAbandoned, kCells, kPrunedDtw, kPrunedMv, kPrunedPc, kPrunedTi, kRefined, kRefined64, kPrunedRev,
-    kNumCounters
+    kMvTerms, kNumCounters
 };
-enum Scalar { kSurvTotal = 0, kCursorSeed, kCursorSurv, kRefineCount, kRefine64Count, kNumScalars };
+enum Scalar { kSurvTotal = 0, kCursorSeed, kCursorSurv, kRefineCount, kRefine64Count, kCursorSeed2, kNumScalars };
 constexpr int kFewQueries = 4;  // query blocks at most this big run their survivors on the seed tile
 
 }  // namespace tc
@@ -268,6 +268,12 @@ struct tcdtw_index {
     float *Uc = nullptr, *Lc = nullptr;  // candidate envelopes [N][L*D] (use_rev)
     float2 *ref_tab = nullptr;   // global cost tables of the double-float refine (long bands)
     int ref_slots = 0;
+    // LB_MV with early abandoning (opts.mv_abandon): prefix length (0: off), second-round
+    // seeds per query, the envelope one query per row, the completion kernel's pair lists
+    int mv_prefix = 0, S2 = 0;
+    float *Up = nullptr, *Lp = nullptr;
+    uint32_t *rest_list = nullptr;
+    int64_t rest_list_entries = 0;
     float *mv_ws = nullptr;      // partial sums of split LB_MV tiles
     int64_t mv_ws_floats = 0;
     int32_t *mv_cnt = nullptr;   // their per-tile arrival counters (kept zero)
@@ -308,8 +314,8 @@ void free_index(tcdtw_index *x) {
     for (auto &g : x->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     if (x->cap_stream) cudaStreamDestroy(x->cap_stream);
-    void *ptrs[] = {x->U, x->Lo, x->dq_lo, x->dq_hi, x->boxes, x->lbm, x->box_counts, x->seeds, x->surv,
-                    x->refine, x->seed_dtw, x->surv_lb, x->surv_dtw, x->refine_d64, x->row_counts,
+    void *ptrs[] = {x->U, x->Lo, x->Up, x->Lp, x->rest_list, x->dq_lo, x->dq_hi, x->boxes, x->lbm,
+                    x->box_counts, x->seeds, x->surv, x->refine, x->seed_dtw, x->surv_lb, x->surv_dtw, x->refine_d64, x->row_counts,
                     x->row_offsets, x->scalars, x->bsf, x->best64, x->best_idx, x->counters, x->status,
                     x->refine64, x->refine64_d64, x->amb, x->bestdf, x->best_idx_df, x->mv_ws, x->mv_cnt,
                     x->Uc, x->Lc, x->qbuf, x->idx_buf, x->dist_buf, x->ref_tab};
@@ -342,12 +348,18 @@ int alloc_index(tcdtw_index *x) {
         TC_TRY(dalloc(&x->box_counts, (size_t)Mb * x->G_pc));
     }
     TC_TRY(dalloc(&x->lbm, (size_t)Mb * N));
-    TC_TRY(dalloc(&x->seeds, (size_t)Mb * x->S));
-    TC_TRY(dalloc(&x->seed_dtw, (size_t)Mb * x->S));
+    TC_TRY(dalloc(&x->seeds, (size_t)Mb * (x->S + x->S2)));
+    TC_TRY(dalloc(&x->seed_dtw, (size_t)Mb * (x->S + x->S2)));
+    if (x->mv_prefix > 0) {
+        TC_TRY(dalloc(&x->Up, (size_t)Mb * x->ldE));
+        TC_TRY(dalloc(&x->Lp, (size_t)Mb * x->ldE));
+        x->rest_list_entries = lb_mv_rest_list_entries(N, x->Mb, x->sms);
+        TC_TRY(dalloc(&x->rest_list, (size_t)x->rest_list_entries));
+    }
     TC_TRY(dalloc(&x->surv, (size_t)Mb * N));
     TC_TRY(dalloc(&x->surv_lb, (size_t)Mb * N));
     TC_TRY(dalloc(&x->surv_dtw, (size_t)Mb * N));
-    x->refine_cap = Mb * (N + x->S);
+    x->refine_cap = Mb * (N + x->S + x->S2);
     TC_TRY(dalloc(&x->refine, (size_t)x->refine_cap));
     TC_TRY(dalloc(&x->refine_d64, (size_t)x->refine_cap));
     TC_TRY(dalloc(&x->refine64, (size_t)x->refine_cap));
@@ -391,8 +403,9 @@ int alloc_index(tcdtw_index *x) {
 // With profiling on, every stage is also an NVTX range on the calling thread (seen by
 // Nsight Systems when it is attached; the calls do nothing otherwise).
 const char *const kStageRange[TCDTW_NUM_STAGES] = {"tcdtw check",   "tcdtw prep",    "tcdtw lb_mv",
-                                                   "tcdtw seed",    "tcdtw compact", "tcdtw cascade",
-                                                   "tcdtw dtw",     "tcdtw refine"};
+                                                   "tcdtw seed",    "tcdtw lb_rest", "tcdtw seed2",
+                                                   "tcdtw compact", "tcdtw cascade", "tcdtw dtw",
+                                                   "tcdtw refine"};
 
 cudaError_t mark(tcdtw_index *x, int k, cudaStream_t s) {
     if (!x->profile) return cudaSuccess;
@@ -418,6 +431,18 @@ cudaError_t mark(tcdtw_index *x, int k, cudaStream_t s) {
     } while (0)
 
 // One block of Mb_cur queries.  All launches on stream s; no host synchronisation.
+// Whether a block of Mb_cur queries runs LB_MV with early abandoning.  Below 32 queries
+// the dense stream is bound by one pass over the candidates, which the completion pass
+// repeats for any tile with a live pair, and the second seed round adds a DTW sweep of
+// latency: the plain stream is faster there.
+constexpr int kAbandonMinQueries = 32;
+bool block_abandons(const tcdtw_index *x, int Mb_cur) { return x->mv_prefix > 0 && Mb_cur >= kAbandonMinQueries; }
+
+// Seed entries of a block (both rounds).
+int64_t block_seeds(const tcdtw_index *x, int Mb_cur) {
+    return (int64_t)Mb_cur * (x->S + (block_abandons(x, Mb_cur) ? x->S2 : 0));
+}
+
 cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_out, double *dist_out,
                       cudaStream_t s) {
     const int L = x->L, D = x->D, W = x->W;
@@ -435,8 +460,11 @@ cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_o
     if ((e = launch_init_block(Mb_cur, x->bsf, x->best64, x->best_idx, x->bestdf, x->best_idx_df, x->amb, s)) !=
         cudaSuccess)
         return e;
+    const bool ab = block_abandons(x, Mb_cur) && !x->opts.no_prune;
     // 1. query-side preparation
-    if ((e = launch_envelope_pairs(q, Mb_cur, L, D, W, x->U, x->Lo, (int)x->ldE, s)) != cudaSuccess) return e;
+    e = ab ? launch_envelope_pairs_plain(q, Mb_cur, L, D, W, x->U, x->Lo, x->Up, x->Lp, (int)x->ldE, s)
+           : launch_envelope_pairs(q, Mb_cur, L, D, W, x->U, x->Lo, (int)x->ldE, s);
+    if (e != cudaSuccess) return e;
     if (x->opts.use_ti && (e = launch_query_dq(q, Mb_cur, L, D, x->dq_lo, x->dq_hi, s)) != cudaSuccess) return e;
     if (x->opts.use_pc &&
         (e = launch_pc_boxes(q, Mb_cur, L, D, W, x->K, x->opts.Lq, x->opts.w, x->boxes, x->box_counts, s)) !=
@@ -451,6 +479,10 @@ cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_o
         mv.cand = x->cand; mv.N = N; mv.E = E; mv.U = x->U; mv.Lo = x->Lo; mv.ldE = x->ldE; mv.Mb = Mb_cur;
         mv.lb = x->lbm; mv.ldLb = N; mv.sms = x->sms; mv.status = x->status;
         mv.ws = x->mv_ws; mv.ws_floats = x->mv_ws_floats; mv.tile_cnt = x->mv_cnt; mv.tile_cnt_cap = kMvTileCounters;
+        if (ab) {  // with abandoning: the prefix [0, mv_prefix) of every pair first
+            mv.E = x->mv_prefix;
+            mv.ldC = E;
+        }
         if ((e = launch_lb_mv(mv, s)) != cudaSuccess) return e;
     }
     // 3. seeds and their DTW
@@ -462,9 +494,32 @@ cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_o
     dn.cursor = x->scalars + kCursorSeed; dn.bsf = x->bsf; dn.rho = x->rho; dn.dtw = x->seed_dtw;
     dn.counters = x->counters;
     if ((e = dtw_nn_launch(x->tile_seed, x->blocks_seed, s, dn)) != cudaSuccess) return e;
+    TC_MARK(4);
+    if (ab) {
+        // the pairs still at or under the seeded threshold complete their LB_MV (the
+        // others keep the prefix sum, a lower bound above the threshold) ...
+        LbMvRestArgs ra;
+        ra.cand = x->cand; ra.N = N; ra.E = E; ra.E0 = x->mv_prefix; ra.ldC = E; ra.Up = x->Up; ra.Lp = x->Lp;
+        ra.ldP = x->ldE; ra.Mb = Mb_cur; ra.lb = x->lbm; ra.ldLb = N; ra.thresh = nullptr; ra.bsf = x->bsf;
+        ra.rho = x->rho; ra.list = x->rest_list; ra.list_entries = x->rest_list_entries; ra.sms = x->sms;
+        ra.terms = x->counters + kMvTerms;
+        if ((e = launch_lb_mv_rest(ra, s)) != cudaSuccess) return e;
+    }
+    TC_MARK(5);
+    if (ab) {
+        // ... and a second round of seeds, the smallest completed bounds, starts the best-
+        // so-far closer to the answer (their DTW abandons against the first round's)
+        if (x->S2 > 0) {
+            uint32_t *seeds2 = x->seeds + (size_t)Mb_cur * x->S;
+            if ((e = launch_seed_topk(x->lbm, Mb_cur, N, N, x->S2, seeds2, s)) != cudaSuccess) return e;
+            dn.pairs = seeds2; dn.n_static = Mb_cur * x->S2; dn.cursor = x->scalars + kCursorSeed2;
+            dn.dtw = x->seed_dtw + (size_t)Mb_cur * x->S;
+            if ((e = dtw_nn_launch(x->tile_seed, x->blocks_seed, s, dn)) != cudaSuccess) return e;
+        }
+    }
     dn.G = x->G;
     // 4. compaction against the seeded best-so-far
-    TC_MARK(4);
+    TC_MARK(6);
     CompactArgs ca;
     memset(&ca, 0, sizeof(ca));
     ca.lb = x->lbm; ca.M = Mb_cur; ca.N = N; ca.ldLb = N; ca.thresh = nullptr; ca.bsf = x->bsf; ca.rho = x->rho;
@@ -472,7 +527,7 @@ cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_o
     ca.pairs = x->surv; ca.lbs = x->surv_lb; ca.pruned = x->counters + kPrunedMv;
     if ((e = launch_compact(ca, s)) != cudaSuccess) return e;
     // 5. gated tight bounds
-    TC_MARK(5);
+    TC_MARK(7);
     PairListArgs pl;
     pl.Q = q; pl.C = x->cand; pl.L = L; pl.D = D; pl.W = W; pl.pairs = x->surv;
     pl.count = x->scalars + kSurvTotal; pl.n_static = 0; pl.N = N; pl.lb = x->surv_lb;
@@ -493,7 +548,7 @@ cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_o
         if (e != cudaSuccess) return e;
     }
     // 6. DTW of the survivors
-    TC_MARK(6);
+    TC_MARK(8);
     dn.pairs = x->surv; dn.lb = x->surv_lb; dn.count = x->scalars + kSurvTotal; dn.n_static = 0;
     dn.cursor = x->scalars + kCursorSurv; dn.dtw = x->surv_dtw;
     // a block of a few queries leaves too few survivors to fill the GPU: each pair's
@@ -504,8 +559,8 @@ cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_o
     if ((e = dtw_nn_launch(few ? x->tile_seed : x->tile, few ? x->blocks_seed : x->blocks_nn, s, dn)) != cudaSuccess)
         return e;
     // 7. refine near-ties in FP64 and select
-    TC_MARK(7);
-    if ((e = launch_refine_select(x->seeds, x->seed_dtw, nullptr, (int64_t)Mb_cur * x->S, N, x->bsf, x->rho_ref,
+    TC_MARK(9);
+    if ((e = launch_refine_select(x->seeds, x->seed_dtw, nullptr, block_seeds(x, Mb_cur), N, x->bsf, x->rho_ref,
                                   x->refine, x->scalars + kRefineCount, x->refine_cap, x->sms, s)) != cudaSuccess)
         return e;
     if ((e = launch_refine_select(x->surv, x->surv_dtw, x->scalars + kSurvTotal, 0, N, x->bsf, x->rho_ref, x->refine,
@@ -538,7 +593,7 @@ cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_o
     if ((e = launch_finalize(Mb_cur, x->bestdf, x->best_idx_df, x->amb, x->best64, x->best_idx, idx_out, dist_out,
                              s)) != cudaSuccess)
         return e;
-    TC_MARK(8);
+    TC_MARK(10);
     return cudaSuccess;
 }
 
@@ -700,6 +755,9 @@ int tcdtw_build(const float *cand, int64_t N, int32_t L, int32_t D, int32_t W, i
     if (!x) return TCDTW_ERR_NOMEM;
     x->cand = cand; x->N = N; x->L = L; x->D = D; x->W = W; x->K = K; x->opts = o;
     x->S = (int)(o.seed_s < N ? o.seed_s : N);
+    // LB_MV with early abandoning: a prefix of every pair, then the live pairs' rest
+    x->mv_prefix = (o.mv_abandon && !o.no_prune) ? lb_mv_prefix(L * D) : 0;
+    x->S2 = x->mv_prefix > 0 ? (int)std::min<int64_t>(x->S, N - x->S) : 0;
     x->sms = num_sms();
     x->G_pc = (L + o.w - 1) / o.w;
     x->ldE = ((int64_t)L * D + 31) / 32 * 32;
@@ -814,12 +872,23 @@ int tcdtw_nn(tcdtw_index *x, const float *q, int64_t M, int64_t *idx, double *di
     if (stats) {
         unsigned long long c[kNumCounters];
         TC_TRY(cudaMemcpy(c, x->counters, sizeof(c), cudaMemcpyDeviceToHost));
-        const uint64_t seeds = (uint64_t)M * (uint64_t)x->S;
+        uint64_t seeds = 0;
+        for (int64_t m0 = 0; m0 < M; m0 += x->Mb)
+            seeds += (uint64_t)block_seeds(x, (int)((M - m0) < x->Mb ? (M - m0) : x->Mb));
         stats->pairs = (uint64_t)M * (uint64_t)x->N;
         stats->pruned_mv = c[kPrunedMv] - seeds + c[kPrunedDtw];
         stats->pruned_pc = c[kPrunedPc];
         stats->pruned_ti = c[kPrunedTi];
         stats->pruned_rev = c[kPrunedRev];
+        // the dense stream's terms (all of every pair, or the prefix of every pair) are
+        // counted here; the completion kernel counts its own
+        uint64_t dense = 0;
+        if (!x->opts.no_prune)
+            for (int64_t m0 = 0; m0 < M; m0 += x->Mb) {
+                const int mb = (int)((M - m0) < x->Mb ? (M - m0) : x->Mb);
+                dense += (uint64_t)mb * (uint64_t)x->N * (uint64_t)(block_abandons(x, mb) ? x->mv_prefix : E);
+            }
+        stats->mv_terms = dense + c[kMvTerms];
         stats->dtw_started = c[kStarted];
         stats->dtw_abandoned = c[kAbandoned];
         stats->cells = c[kCells];
@@ -913,6 +982,74 @@ int tcdtw_compact(const float *lb, int64_t M, int64_t N, const float *thresh, in
     ca.lb = lb; ca.M = M; ca.N = N; ca.ldLb = N; ca.thresh = thresh; ca.counts = count; ca.ldOut = N;
     ca.idx_out = out_idx;
     return cuda_err(launch_compact(ca, (cudaStream_t)stream));
+}
+
+int tcdtw_lb_mv_abandon(const float *q, int64_t M, const float *c, int64_t N, int32_t L, int32_t D, int32_t W,
+                        const float *thresh, float *out, void *stream) {
+    if (M < 0 || N < 0 || L < 1 || D < 1 || W < 0) return TCDTW_ERR_INVALID;
+    if (D > TCDTW_MAX_D) return TCDTW_ERR_UNSUPPORTED;
+    if (M == 0 || N == 0) return TCDTW_OK;
+    if (!q || !c || !thresh || !out) return TCDTW_ERR_INVALID;
+    if (W > L - 1) W = L - 1;
+    if ((double)M * (double)N >= 4.29e9) return TCDTW_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int sms = num_sms();
+    const int E = L * D;
+    const int E0 = lb_mv_prefix(E);
+    const int64_t ldE = ((int64_t)E + 31) / 32 * 32;
+    const int64_t Mp = (M + 31) / 32 * 32;
+    const int64_t ws_floats = std::min<int64_t>(kMvWsFloats, 64 * M * N);
+    const int64_t list_n = E0 > 0 ? lb_mv_rest_list_entries(N, (int)std::min<int64_t>(M, kRestQG), sms) : 1;
+    float *U = nullptr, *Lo = nullptr, *Up = nullptr, *Lp = nullptr, *ws = nullptr;
+    DevStatus *st = nullptr;
+    int32_t *cnt = nullptr;
+    uint32_t *list = nullptr;
+    auto release = [&]() {
+        for (void *p : {(void *)U, (void *)Lo, (void *)Up, (void *)Lp, (void *)ws, (void *)st, (void *)cnt,
+                        (void *)list})
+            cudaFree(p);
+    };
+    if (dev_malloc((void **)&U, sizeof(float) * Mp * ldE) != cudaSuccess ||
+        dev_malloc((void **)&Lo, sizeof(float) * Mp * ldE) != cudaSuccess ||
+        dev_malloc((void **)&Up, sizeof(float) * Mp * ldE) != cudaSuccess ||
+        dev_malloc((void **)&Lp, sizeof(float) * Mp * ldE) != cudaSuccess ||
+        dev_malloc((void **)&st, sizeof(DevStatus)) != cudaSuccess ||
+        dev_malloc((void **)&ws, sizeof(float) * ws_floats) != cudaSuccess ||
+        dev_malloc((void **)&cnt, sizeof(int32_t) * kMvTileCounters) != cudaSuccess ||
+        dev_malloc((void **)&list, sizeof(uint32_t) * list_n) != cudaSuccess) {
+        release();
+        return TCDTW_ERR_NOMEM;
+    }
+    cudaError_t e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * kMvTileCounters, s);
+    for (int64_t m0 = 0; m0 < M && e == cudaSuccess; m0 += 65534) {  // even chunks keep the pair layout
+        const int64_t mc = (M - m0) < 65534 ? (M - m0) : 65534;
+        e = launch_envelope_pairs_plain(q + m0 * E, mc, L, D, W, U + m0 * ldE, Lo + m0 * ldE, Up + m0 * ldE,
+                                        Lp + m0 * ldE, (int)ldE, s);
+    }
+    if (e == cudaSuccess) {  // the prefix of every pair (all of it when E0 == 0)
+        LbMvArgs mv;
+        mv.cand = c; mv.N = N; mv.E = E0 > 0 ? E0 : E; mv.ldC = E; mv.U = U; mv.Lo = Lo; mv.ldE = ldE;
+        mv.Mb = (int)M; mv.lb = out; mv.ldLb = N; mv.sms = sms; mv.status = st;
+        mv.ws = ws; mv.ws_floats = ws_floats; mv.tile_cnt = cnt; mv.tile_cnt_cap = kMvTileCounters;
+        e = launch_lb_mv(mv, s);
+    }
+    if (e == cudaSuccess && E0 > 0) {  // the rest of the pairs still under their threshold
+        LbMvRestArgs ra;
+        ra.cand = c; ra.N = N; ra.E = E; ra.E0 = E0; ra.ldC = E; ra.Up = Up; ra.Lp = Lp; ra.ldP = ldE;
+        ra.Mb = (int)M; ra.lb = out; ra.ldLb = N; ra.thresh = thresh; ra.bsf = nullptr; ra.rho = 1.f;
+        ra.list = list; ra.list_entries = list_n; ra.sms = sms;
+        e = launch_lb_mv_rest(ra, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int rc = cuda_err(e);
+    if (rc == TCDTW_OK) {
+        DevStatus h;
+        rc = cuda_err(cudaMemcpy(&h, st, sizeof(h), cudaMemcpyDeviceToHost));
+        if (rc == TCDTW_OK && h.code) rc = h.code;
+    }
+    release();
+    return rc;
 }
 
 int tcdtw_lower_bounds(const float *q, int64_t M, const float *c, int64_t N, int32_t L, int32_t D, int32_t W,

@@ -169,6 +169,7 @@ void tcdtw_default_opts(tcdtw_opts *o) {
     o->select = 1;
     o->use_rev = 0;
     o->ti_top = 1;
+    o->mv_abandon = 1;
 }
 
 const char *tcdtw_strerror(int code) {

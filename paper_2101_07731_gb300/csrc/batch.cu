@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_front(const BatchSet *_
             float(*su)[kBatchQB * kMvChunk] = (float(*)[kBatchQB * kMvChunk])(bsm + 2 * kMvRows * kMvChunk);
             float(*sl)[kBatchQB * kMvChunk] =
                 (float(*)[kBatchQB * kMvChunk])(bsm + 2 * kMvRows * kMvChunk + 2 * kBatchQB * kMvChunk);
-            lb_mv_tile<kBatchQB>(S.cand, S.N, S.L * S.D, S.vec4 != 0, S.U, S.Lo, S.ldE, S.M, S.lbm, S.N,
+            lb_mv_tile<kBatchQB>(S.cand, S.N, S.L * S.D, (int64_t)S.L * S.D, S.vec4 != 0, S.U, S.Lo, S.ldE, S.M, S.lbm, S.N,
                                  (int64_t)item.b * kMvRows, item.a * kBatchQB, sc, su, sl);
             batch_done(S.cnt + kCntMv);
         } else if (item.kind == kItemSeed) {

@@ -16,6 +16,10 @@ cudaError_t launch_envelope(const float *q, int64_t M, int L, int D, int W, floa
 // element e of query m at ((m/2)*ldE + e)*2 + m%2, entries e >= L*D set to +-inf
 cudaError_t launch_envelope_pairs(const float *q, int64_t M, int L, int D, int W, float *U, float *Lo, int ldE,
                                   cudaStream_t s);
+// both layouts at once: query-pair interleaved (U, Lo) and one query per row (U2, Lo2:
+// element e of query m at m*ldE + e, entries e >= L*D set to +-inf)
+cudaError_t launch_envelope_pairs_plain(const float *q, int64_t M, int L, int D, int W, float *U, float *Lo,
+                                        float *U2, float *Lo2, int ldE, cudaStream_t s);
 cudaError_t launch_query_dq(const float *q, int64_t M, int L, int D, float *dq_lo, float *dq_hi, cudaStream_t s);
 size_t pc_boxes_smem(int L, int D, int W, int K, int w, int *npow2_out);
 cudaError_t launch_pc_boxes(const float *q, int64_t M, int L, int D, int W, int K, int Lq, int w, float *boxes,
@@ -23,9 +27,10 @@ cudaError_t launch_pc_boxes(const float *q, int64_t M, int L, int D, int W, int 
 
 // lb.cu -- LB_MV over all (query, candidate) pairs of a block
 struct LbMvArgs {
-    const float *cand;  // [N][E], E = L*D
+    const float *cand;  // [N][ldC]; the stream covers elements [0, E) of every row
     int64_t N;
     int E;
+    int64_t ldC = 0;    // row stride of cand in floats (0: E)
     const float *U;     // query-pair interleaved envelope [(Mb+1)/2][ldE][2], +inf beyond E
     const float *Lo;    // likewise, -inf beyond E
     int64_t ldE;        // multiple of 32
@@ -55,6 +60,44 @@ constexpr int64_t kMvTileCounters = 4096;
 cudaError_t launch_lb_mv_tma(const LbMvArgs &a, cudaStream_t s);
 // whether the LB_MV stream may copy candidate rows 16 bytes at a time
 bool lb_mv_vec4(const float *cand, int E);
+
+// lb_rest.cu -- completion of LB_MV, with early abandoning, for the pairs whose sum over
+// the elements [0, E0) (already in lb) is at most their query's threshold; the others
+// keep their prefix sum.  Completed and abandoned values are written in place.
+constexpr int kRestTC = 256;   // candidates per tile, at most
+constexpr int kRestQG = 256;   // queries staged per pass, at most
+constexpr size_t kRestSmemMax = ((size_t)2 * kRestTC * 32 + (size_t)2 * kRestQG * 64 + kRestQG + 4) * sizeof(float);
+struct LbMvRestArgs {
+    const float *cand;      // [N][ldC], elements [0, E) used
+    int64_t N;
+    int E, E0;              // E0: prefix already summed, a multiple of 32, < E
+    int64_t ldC;
+    const float *Up, *Lp;   // envelope, one query per row: [Mb][ldP], +inf / -inf beyond E
+    int64_t ldP;            // a multiple of 32, >= E
+    int Mb;
+    float *lb;              // [Mb][ldLb]: prefix sums in, bounds out
+    int64_t ldLb;
+    const float *thresh;    // [Mb] thresholds, or null: prune_threshold(bsf[m], rho)
+    const unsigned long long *bsf;
+    float rho;
+    uint32_t *list;         // scratch: lb_mv_rest_list_entries(N, Mb, sms) entries
+    int64_t list_entries;
+    int sms;
+    unsigned long long *terms = nullptr;  // optional: += the (element, pair) terms summed
+};
+int lb_mv_rest_tile(int64_t N, int sms);
+int64_t lb_mv_rest_list_entries(int64_t N, int Mb, int sms);
+cudaError_t launch_lb_mv_rest(const LbMvRestArgs &a, cudaStream_t s);
+// Prefix length of the abandoning LB_MV for rows of E elements: 0 (no abandoning) when
+// the rows are too short for it to pay.
+inline int lb_mv_prefix(int E) {
+    const int nchunks = (E + 31) / 32;
+    if (nchunks < 4) return 0;
+    int c = nchunks / 16;
+    if (c < 1) c = 1;
+    if (c > 8) c = 8;
+    return 32 * c;
+}
 
 // compaction of rows of a bound matrix against per-row thresholds
 struct CompactArgs {

@@ -411,7 +411,8 @@ cudaError_t launch_variant(const LbMvArgs &a, const CUtensorMap &cm, const CUten
 }  // namespace
 
 bool lb_mv_tma_ok(const LbMvArgs &a) {
-    return a.status != nullptr && (a.E % 4) == 0 && (((uintptr_t)a.cand) & 15) == 0 &&
+    const int64_t ldC = a.ldC > 0 ? a.ldC : a.E;
+    return a.status != nullptr && (a.E % 4) == 0 && (ldC % 4) == 0 && ldC >= a.E && (((uintptr_t)a.cand) & 15) == 0 &&
            (((uintptr_t)a.U) & 15) == 0 && (((uintptr_t)a.Lo) & 15) == 0 && (a.ldE % kMvChunk) == 0 &&
            a.N < ((int64_t)1 << 31) - 256 && a.Mb < (1 << 30) && encode_fn() != nullptr;
 }
@@ -432,7 +433,8 @@ cudaError_t launch_lb_mv_tma(const LbMvArgs &a, cudaStream_t s) {
     p.n_qtiles = (a.Mb + QB - 1) / QB;
     const int64_t n_qp = (a.Mb + 1) / 2;
     CUtensorMap cm, um, lm;
-    if (!encode_2d(&cm, a.cand, (uint64_t)a.E, (uint64_t)a.N, (uint64_t)a.E * 4, kMvChunk, kMvRows,
+    const int64_t ldC = a.ldC > 0 ? a.ldC : a.E;
+    if (!encode_2d(&cm, a.cand, (uint64_t)a.E, (uint64_t)a.N, (uint64_t)ldC * 4, kMvChunk, kMvRows,
                    CU_TENSOR_MAP_SWIZZLE_128B) ||
         !encode_2d(&um, a.U, (uint64_t)a.ldE * 2, (uint64_t)n_qp, (uint64_t)a.ldE * 8, 2 * kMvChunk, QB / 2,
                    CU_TENSOR_MAP_SWIZZLE_NONE) ||

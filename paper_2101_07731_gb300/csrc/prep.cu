@@ -97,7 +97,8 @@ constexpr size_t kEnvVhSmemMax = 96 * 1024;
 __global__ void __launch_bounds__(kEnvVhThreads) k_envelope_vhgw(const float *__restrict__ q, int L, int D, int W,
                                                                  int Dg, float *__restrict__ U,
                                                                  float *__restrict__ Lo, int64_t ldE, int pad,
-                                                                 int pairs) {
+                                                                 int pairs, float *__restrict__ U2,
+                                                                 float *__restrict__ Lo2) {
     extern __shared__ float sh[];
     float *x = sh, *hmax = sh + (size_t)L * Dg, *hmin = hmax + (size_t)L * Dg;
     const int m = blockIdx.y, p0 = blockIdx.x * Dg, ng = min(Dg, D - p0);
@@ -142,8 +143,13 @@ __global__ void __launch_bounds__(kEnvVhThreads) k_envelope_vhgw(const float *__
             }
             const int o = xp - 2 * W;
             if (o >= 0 && o < L) {
-                U[env_pos(m, (int64_t)o * D + p, ldE, pairs)] = fmaxf(hmax[o * Dg + pp], mx);
-                Lo[env_pos(m, (int64_t)o * D + p, ldE, pairs)] = fminf(hmin[o * Dg + pp], mn);
+                const float u = fmaxf(hmax[o * Dg + pp], mx), l = fminf(hmin[o * Dg + pp], mn);
+                U[env_pos(m, (int64_t)o * D + p, ldE, pairs)] = u;
+                Lo[env_pos(m, (int64_t)o * D + p, ldE, pairs)] = l;
+                if (U2) {  // the same envelope, one query per row
+                    U2[(size_t)m * ldE + (size_t)o * D + p] = u;
+                    Lo2[(size_t)m * ldE + (size_t)o * D + p] = l;
+                }
             }
         }
     }
@@ -151,12 +157,16 @@ __global__ void __launch_bounds__(kEnvVhThreads) k_envelope_vhgw(const float *__
         for (int64_t k = (int64_t)L * D + threadIdx.x; k < ldE; k += blockDim.x) {
             U[env_pos(m, k, ldE, pairs)] = TC_INF;
             Lo[env_pos(m, k, ldE, pairs)] = -TC_INF;
+            if (U2) {
+                U2[(size_t)m * ldE + k] = TC_INF;
+                Lo2[(size_t)m * ldE + k] = -TC_INF;
+            }
         }
     }
 }
 
 static cudaError_t envelope_impl(const float *q, int64_t M, int L, int D, int W, float *U, float *Lo, int ldE,
-                                 int pairs, cudaStream_t s) {
+                                 int pairs, cudaStream_t s, float *U2 = nullptr, float *Lo2 = nullptr) {
     if (M <= 0) return cudaSuccess;
     if (W > L - 1) W = L - 1;
     const int pad = ldE > L * D;
@@ -173,7 +183,7 @@ static cudaError_t envelope_impl(const float *q, int64_t M, int L, int D, int W,
         }
         dim3 grid((D + Dg - 1) / Dg, (unsigned)M);
         const size_t sh = (size_t)3 * L * Dg * sizeof(float);
-        k_envelope_vhgw<<<grid, kEnvVhThreads, sh, s>>>(q, L, D, W, Dg, U, Lo, ldE, pad, pairs);
+        k_envelope_vhgw<<<grid, kEnvVhThreads, sh, s>>>(q, L, D, W, Dg, U, Lo, ldE, pad, pairs, U2, Lo2);
         note_launch();
         return cudaGetLastError();
     }
@@ -184,7 +194,9 @@ static cudaError_t envelope_impl(const float *q, int64_t M, int L, int D, int W,
     else
         k_envelope<false><<<grid, 128, 0, s>>>(q, L, D, W, U, Lo, ldE, pad, pairs);
     note_launch();
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !U2) return e;
+    return envelope_impl(q, M, L, D, W, U2, Lo2, ldE, 0, s);  // the one-query-per-row copy
 }
 
 cudaError_t launch_envelope(const float *q, int64_t M, int L, int D, int W, float *U, float *Lo, int ldE,
@@ -195,6 +207,11 @@ cudaError_t launch_envelope(const float *q, int64_t M, int L, int D, int W, floa
 cudaError_t launch_envelope_pairs(const float *q, int64_t M, int L, int D, int W, float *U, float *Lo, int ldE,
                                   cudaStream_t s) {
     return envelope_impl(q, M, L, D, W, U, Lo, ldE, 1, s);
+}
+
+cudaError_t launch_envelope_pairs_plain(const float *q, int64_t M, int L, int D, int W, float *U, float *Lo,
+                                        float *U2, float *Lo2, int ldE, cudaStream_t s) {
+    return envelope_impl(q, M, L, D, W, U, Lo, ldE, 1, s, U2, Lo2);
 }
 
 // ------------------------------------------------------------------ neighbour distances

@@ -134,7 +134,7 @@ def test_argument_errors_of_the_newer_calls(lib):
     # addresses are never dereferenced)
     import paper_2101_07731_gb300 as tc
     o = tc.default_opts()
-    assert (o.use_rev, o.ti_top, o.select) == (0, 1, 1)
+    assert (o.use_rev, o.ti_top, o.select, o.mv_abandon) == (0, 1, 1, 1)
     dummy = C.c_void_p(256)
     f = lib.tcdtw_lower_bounds
     f.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
@@ -178,6 +178,23 @@ def test_noalloc_refuses_what_the_allocating_call_refuses(lib):
         assert a == b, (M, N, L, D, W, a, b)
     assert g(dummy, 2, dummy, 3, 8, 65, 2, dummy, None) == tc.ERR_UNSUPPORTED
     assert g(None, 2, dummy, 3, 8, 2, 2, dummy, None) == tc.ERR_INVALID
+
+
+def test_abandoning_lb_mv_argument_errors(lib):
+    # tcdtw_lb_mv_abandon checks its arguments like tcdtw_lower_bounds(TCDTW_LB_MV), plus
+    # the threshold array, before any CUDA call
+    import paper_2101_07731_gb300 as tc
+    dummy = C.c_void_p(256)
+    g = lib.tcdtw_lb_mv_abandon
+    g.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
+                  C.c_void_p, C.c_void_p]
+    assert g(dummy, 2, dummy, 3, 8, 65, 2, dummy, dummy, None) == tc.ERR_UNSUPPORTED
+    assert g(dummy, 70000, dummy, 70000, 8, 2, 2, dummy, dummy, None) == tc.ERR_UNSUPPORTED
+    for M, N, L, D, W in [(-1, 3, 8, 2, 2), (2, 3, 0, 2, 2), (2, 3, 8, 0, 2), (2, 3, 8, 2, -1)]:
+        assert g(dummy, M, dummy, N, L, D, W, dummy, dummy, None) == tc.ERR_INVALID
+    assert g(dummy, 2, dummy, 3, 8, 2, 2, None, dummy, None) == tc.ERR_INVALID      # no thresholds
+    assert g(None, 2, dummy, 3, 8, 2, 2, dummy, dummy, None) == tc.ERR_INVALID
+    assert g(dummy, 0, dummy, 3, 8, 2, 2, None, None, None) == 0                   # nothing to do
 
 
 def test_alloc_failure_injection_switch(lib):
