@@ -502,7 +502,7 @@ cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_o
         ra.cand = x->cand; ra.N = N; ra.E = E; ra.E0 = x->mv_prefix; ra.ldC = E; ra.Up = x->Up; ra.Lp = x->Lp;
         ra.ldP = x->ldE; ra.Mb = Mb_cur; ra.lb = x->lbm; ra.ldLb = N; ra.thresh = nullptr; ra.bsf = x->bsf;
         ra.rho = x->rho; ra.list = x->rest_list; ra.list_entries = x->rest_list_entries; ra.sms = x->sms;
-        ra.terms = x->counters + kMvTerms;
+        ra.terms = x->counters + kMvTerms; ra.status = x->status;
         if ((e = launch_lb_mv_rest(ra, s)) != cudaSuccess) return e;
     }
     TC_MARK(5);
@@ -1038,7 +1038,7 @@ int tcdtw_lb_mv_abandon(const float *q, int64_t M, const float *c, int64_t N, in
         LbMvRestArgs ra;
         ra.cand = c; ra.N = N; ra.E = E; ra.E0 = E0; ra.ldC = E; ra.Up = Up; ra.Lp = Lp; ra.ldP = ldE;
         ra.Mb = (int)M; ra.lb = out; ra.ldLb = N; ra.thresh = thresh; ra.bsf = nullptr; ra.rho = 1.f;
-        ra.list = list; ra.list_entries = list_n; ra.sms = sms;
+        ra.list = list; ra.list_entries = list_n; ra.sms = sms; ra.status = st;
         e = launch_lb_mv_rest(ra, s);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -64,9 +64,8 @@ bool lb_mv_vec4(const float *cand, int E);
 // lb_rest.cu -- completion of LB_MV, with early abandoning, for the pairs whose sum over
 // the elements [0, E0) (already in lb) is at most their query's threshold; the others
 // keep their prefix sum.  Completed and abandoned values are written in place.
-constexpr int kRestTC = 256;   // candidates per tile, at most
+constexpr int kRestTC = 224;   // candidates per tile, at most
 constexpr int kRestQG = 256;   // queries staged per pass, at most
-constexpr size_t kRestSmemMax = ((size_t)2 * kRestTC * 32 + (size_t)2 * kRestQG * 64 + kRestQG + 4) * sizeof(float);
 struct LbMvRestArgs {
     const float *cand;      // [N][ldC], elements [0, E) used
     int64_t N;
@@ -84,6 +83,7 @@ struct LbMvRestArgs {
     int64_t list_entries;
     int sms;
     unsigned long long *terms = nullptr;  // optional: += the (element, pair) terms summed
+    DevStatus *status = nullptr;          // bounded waits of the bulk-tensor form (null: cp.async form)
 };
 int lb_mv_rest_tile(int64_t N, int sms);
 int64_t lb_mv_rest_list_entries(int64_t N, int Mb, int sms);

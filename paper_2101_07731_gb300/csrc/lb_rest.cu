@@ -8,15 +8,25 @@
 // The pairs left at or under the threshold (on nearest-neighbour workloads usually a
 // small share) are completed here, over the elements [E0, E).
 //
-// CTA = TC candidates (TC <= kRestTC) x up to qg <= kRestQG queries.  The CTA lists the
+// CTA = tn candidates (tn <= kRestTC) x up to qg <= kRestQG queries.  The CTA lists the
 // live (query, candidate) pairs of its tile (in a per-CTA global scratch region), then
 // streams the elements [E0, E) of its candidates and of its queries' envelopes through
-// shared memory in chunks of 32 (cp.async, double buffered; every 128-byte row stored
-// with its 16-byte segments XOR-swizzled by row & 7, so that threads reading different
-// rows mostly hit different banks); each thread advances up to kRestEpt listed pairs
-// by one chunk per step.  Every kRestCheck chunks a pair whose running sum has passed
+// shared memory in chunks of 32, two stages deep, every 128-byte row stored with its
+// 16-byte segments XOR-swizzled by row & 7 (threads reading different rows then mostly
+// hit different banks).  Each consumer thread advances up to kRestEpt listed pairs by
+// one chunk per stage.  Every kRestCheck chunks a pair whose running sum has passed
 // the threshold is abandoned again (its partial sum is written, a lower bound above
 // the threshold); a check that finds no listed pair left ends the stream.
+//
+// Two forms of the stream.  k_lb_mv_rest_tma: one producer thread issues, per chunk,
+// three 2-D bulk-tensor copies (candidate rows [tn][32], U and Lo rows [qg][32], the
+// 128-byte swizzle above) that complete on the stage's "full" mbarrier, and the 480
+// consumer threads only compute (a thread-issued copy costs address arithmetic per
+// 16 bytes, which at ~92 KB per chunk is as much work as the sums).  Every wait is
+// bounded (TCDTW_ERR_TIMEOUT in the status word, then the CTA winds down, waiting --
+// bounded again -- for its copies in flight).  k_lb_mv_rest_cp, the fallback for rows
+// whose stride is not a multiple of 16 bytes: every thread issues cp.async copies.
+//
 // Rounding as in the dense stream: terms and sums rounded down, so every stored value
 // is at most the exact LB_MV.
 #include <cuda_runtime.h>
@@ -25,15 +35,19 @@
 #include "common.cuh"
 #include "lb_device.cuh"
 #include "lb_kernels.cuh"
+#include "tma.cuh"
 
 namespace tc {
 
 namespace {
 
-constexpr int kRestThreads = 512;
-constexpr int kRestEpt = 4;                          // listed pairs per thread per round
-constexpr int kRestRound = kRestThreads * kRestEpt;  // listed pairs per round
-constexpr int kRestCheck = 16;                       // chunks between abandoning checks
+constexpr int kRestEpt = 4;      // listed pairs per consumer thread per round
+constexpr int kRestCheck = 16;   // chunks between abandoning checks
+// bulk-tensor form: 15 consumer warps + the producer warp, four warps per SM
+// sub-partition (a 17th warp would cap every thread at 96 registers)
+constexpr int kRestCons = 480;
+constexpr int kRestTmaThreads = kRestCons + 32;
+constexpr int kRestCpThreads = 512;  // cp.async form: every thread consumes
 
 // Two consecutive elements of one pair: c2 = {c_e, c_e+1} against {U_e, U_e+1},
 // {Lo_e, Lo_e+1}; the squared excess of each is added (rounded down) into its half of
@@ -47,12 +61,263 @@ __device__ __forceinline__ f2 rest_step(f2 c2, f2 u2, f2 l2, f2 part) {
     return fma2_rd(m2, m2, part);
 }
 
-// Copies chunk [e0, e0+32) of the tile's candidates and queries into one buffer.
+// One chunk of one pair: candidate row cr, envelope rows ur / lr (32 floats each,
+// segments swizzled by cs / es); returns the chunk's sum, rounded down.
+__device__ __forceinline__ float rest_chunk(const float *cr, const float *ur, const float *lr, int cs, int es) {
+    f2 p = 0ull;
+#pragma unroll
+    for (int sg = 0; sg < 8; ++sg) {
+        const float4 cv = *reinterpret_cast<const float4 *>(cr + ((sg ^ cs) << 2));
+        const float4 uv = *reinterpret_cast<const float4 *>(ur + ((sg ^ es) << 2));
+        const float4 lv = *reinterpret_cast<const float4 *>(lr + ((sg ^ es) << 2));
+        p = rest_step(pk(cv.x, cv.y), pk(uv.x, uv.y), pk(lv.x, lv.y), p);
+        p = rest_step(pk(cv.z, cv.w), pk(uv.z, uv.w), pk(lv.z, lv.w), p);
+    }
+    float p0, p1;
+    upk(p, p0, p1);
+    return __fadd_rd(p0, p1);
+}
+
+// The live pairs (bound at or under the query's threshold) of candidates [n0, n0+tn)
+// x queries [q0, q0+nq), appended to list as (query - q0) << 16 | (candidate - n0);
+// *cnt counts them.  Every thread of the CTA calls it (blockDim.x a multiple of 32:
+// whole warps take part in every ballot, nq * tn being a multiple of 32).
+__device__ __forceinline__ void rest_list(const LbMvRestArgs &a, int64_t n0, int tn, int q0, int nq,
+                                          const float *thr, int *cnt, uint32_t *list) {
+    const int lane = threadIdx.x & 31;
+    for (int base = 0; base < nq * tn; base += blockDim.x) {
+        const int idx = base + threadIdx.x;
+        const int ql = idx / tn, nl = idx - ql * tn;
+        bool live = false;
+        if (ql < nq && n0 + nl < a.N) {
+            const float v = a.lb[(size_t)(q0 + ql) * a.ldLb + n0 + nl];
+            live = v < TC_INF && v <= thr[ql];
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, live);
+        int pos = 0;
+        if (lane == 0 && bal) pos = atomicAdd(cnt, __popc(bal));
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        if (live) list[pos + __popc(bal & ((1u << lane) - 1u))] = ((uint32_t)ql << 16) | (uint32_t)nl;
+    }
+}
+
+__device__ __forceinline__ float rest_threshold(const LbMvRestArgs &a, int q) {
+    return a.thresh ? a.thresh[q] : prune_threshold(ld_volatile_u64(a.bsf + q), a.rho);
+}
+
+// The round's listed pairs of consumer thread t of nc: entries r0 + k * nc + t.
+struct RestPairs {
+    int q[kRestEpt], n[kRestEpt];
+    float acc[kRestEpt], th[kRestEpt];
+    bool act[kRestEpt];
+};
+
+__device__ __forceinline__ void rest_load(RestPairs &p, const LbMvRestArgs &a, const uint32_t *list, int r0, int t,
+                                          int nc, int cnt, int64_t n0, int q0, const float *thr) {
+#pragma unroll
+    for (int k = 0; k < kRestEpt; ++k) {
+        const int i = r0 + k * nc + t;
+        p.act[k] = i < cnt;
+        const uint32_t en = p.act[k] ? __ldcg(list + i) : 0u;
+        p.q[k] = (int)(en >> 16);
+        p.n[k] = (int)(en & 0xffffu);
+        p.acc[k] = p.act[k] ? a.lb[(size_t)(q0 + p.q[k]) * a.ldLb + n0 + p.n[k]] : 0.f;
+        p.th[k] = thr[p.q[k]];
+    }
+}
+
+// Abandons the pairs whose running sum passed their threshold (writing the partial
+// sum); true while any pair of this thread is still active.
+__device__ __forceinline__ bool rest_check(RestPairs &p, const LbMvRestArgs &a, int64_t n0, int q0) {
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < kRestEpt; ++k) {
+        if (p.act[k] && p.acc[k] > p.th[k]) {
+            a.lb[(size_t)(q0 + p.q[k]) * a.ldLb + n0 + p.n[k]] = p.acc[k];
+            p.act[k] = false;
+        }
+        any |= p.act[k];
+    }
+    return any;
+}
+
+__device__ __forceinline__ void rest_store(const RestPairs &p, const LbMvRestArgs &a, int64_t n0, int q0) {
+#pragma unroll
+    for (int k = 0; k < kRestEpt; ++k)
+        if (p.act[k]) a.lb[(size_t)(q0 + p.q[k]) * a.ldLb + n0 + p.n[k]] = p.acc[k];
+}
+
+// OR of v over the consumer threads (named barrier 1; the producer warp never joins).
+__device__ __forceinline__ bool consumers_any(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(kRestCons)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void rest_terms_flush(const LbMvRestArgs &a, unsigned long long terms) {
+    if (!a.terms) return;
+    for (int o = 16; o > 0; o >>= 1) terms += __shfl_xor_sync(0xffffffffu, terms, o);
+    if ((threadIdx.x & 31) == 0 && terms) atomicAdd(a.terms, terms);
+}
+
+// ------------------------------------------------------------------ bulk-tensor form
+// Shared memory from a 1024-byte aligned base: two stages of [cand tn x 128 B | U qgp x
+// 128 B | Lo qgp x 128 B] (qgp = qg rounded up to 8 rows, so every region starts on a
+// 1024-byte boundary, as the 128-byte swizzle needs), then full[2], empty[2] mbarriers,
+// four flags (stop, abort, issued, count) and the thresholds.
+__host__ __device__ constexpr uint32_t rest_tma_stage_bytes(int tn, int qg) {
+    return (uint32_t)(tn + 2 * ((qg + 7) / 8 * 8)) * 128u;
+}
+constexpr size_t rest_tma_smem(int tn, int qg) {
+    return 1024 + 2 * (size_t)rest_tma_stage_bytes(tn, qg) + 32 + 16 + (size_t)qg * 4;
+}
+static_assert(rest_tma_smem(kRestTC, kRestQG) <= 227 * 1024, "one CTA of the completion stream per SM");
+
+__global__ void __launch_bounds__(kRestTmaThreads, 1)
+    k_lb_mv_rest_tma(const __grid_constant__ CUtensorMap cmap, const __grid_constant__ CUtensorMap umap,
+                     const __grid_constant__ CUtensorMap lmap, const LbMvRestArgs a, int tn, int qg,
+                     uint64_t wait_ns) {
+    extern __shared__ unsigned char rest_raw[];
+    const uint32_t raw = smem_u32(rest_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char *sb = rest_raw + (base - raw);
+    const int qgp = (qg + 7) / 8 * 8;
+    const uint32_t stage = rest_tma_stage_bytes(tn, qg);
+    const uint32_t full0 = base + 2 * stage, empty0 = full0 + 16;
+    volatile int *flags = reinterpret_cast<volatile int *>(sb + 2 * stage + 32);  // stop, abort, issued, count
+    float *thr = reinterpret_cast<float *>(sb + 2 * stage + 48);
+    uint32_t *list = a.list + (size_t)blockIdx.x * tn * qg;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const bool producer = tid >= kRestCons;
+    const int nchunks = (a.E + kMvChunk - 1) / kMvChunk, c0 = a.E0 / kMvChunk;
+    const uint32_t tx = (uint32_t)(tn + 2 * qg) * 128u;  // bytes the three boxes deliver
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, kRestCons / 32);
+        }
+        flags[0] = flags[1] = flags[2] = flags[3] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (tid == kRestCons) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&cmap) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&umap) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&lmap) : "memory");
+    }
+    __syncthreads();
+    uint32_t kp = 0, kc = 0;  // stages issued (producer thread) / consumed (every consumer)
+    unsigned long long terms = 0;
+    const int64_t n_tiles = (a.N + tn - 1) / tn;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t n0 = tile * tn;
+        for (int q0 = 0; q0 < a.Mb; q0 += qg) {
+            const int nq = min(qg, a.Mb - q0);
+            __syncthreads();  // the previous pass is done with the thresholds and the list
+            if (tid == 0) flags[3] = 0;
+            for (int k = tid; k < nq; k += blockDim.x) thr[k] = rest_threshold(a, q0 + k);
+            __syncthreads();
+            rest_list(a, n0, tn, q0, nq, thr, (int *)&flags[3], list);
+            __syncthreads();  // the list (global, this CTA's region) and its count
+            const int cnt = flags[3];
+            for (int r0 = 0; r0 < cnt; r0 += kRestCons * kRestEpt) {
+                int consumed = 0;
+                if (producer) {
+                    if (lane == 0) {
+                        int issued = 0;
+                        for (int c = c0; c < nchunks && !flags[0] && !flags[1]; ++c) {
+                            const uint32_t s = kp & 1u;
+                            // the stage's previous chunk must have been released (the wait
+                            // also gives up when the consumers stop the stream)
+                            if (kp >= 2 && !mbar_wait(empty0 + 8 * s, ((kp >> 1) - 1) & 1u, flags, wait_ns)) {
+                                if (!flags[0] && !flags[1]) {
+                                    set_error(a.status, TCDTW_ERR_TIMEOUT, 50);
+                                    flags[1] = 1;
+                                }
+                                break;
+                            }
+                            const uint32_t dst = base + s * stage, full = full0 + 8 * s;
+                            mbar_expect_tx(full, tx);
+                            tma_load_2d(dst, &cmap, c * kMvChunk, (int)n0, full);
+                            tma_load_2d(dst + (uint32_t)tn * 128u, &umap, c * kMvChunk, q0, full);
+                            tma_load_2d(dst + (uint32_t)(tn + qgp) * 128u, &lmap, c * kMvChunk, q0, full);
+                            ++kp;
+                            ++issued;
+                        }
+                        flags[2] = issued;
+                    }
+                } else {
+                    RestPairs p;
+                    rest_load(p, a, list, r0, tid, kRestCons, cnt, n0, q0, thr);
+                    for (int c = c0; c < nchunks; ++c) {
+                        const uint32_t s = kc & 1u;
+                        if (!mbar_wait(full0 + 8 * s, (kc >> 1) & 1u, flags + 1, wait_ns) && !flags[1]) {
+                            set_error(a.status, TCDTW_ERR_TIMEOUT, 51);
+                            flags[1] = 1;
+                        }
+                        ++kc;
+                        ++consumed;
+                        if (!flags[1]) {
+                            const float *cb = reinterpret_cast<const float *>(sb + s * stage);
+                            const float *ub = cb + tn * 32, *lbp = ub + qgp * 32;
+#pragma unroll
+                            for (int k = 0; k < kRestEpt; ++k) {
+                                if (!p.act[k]) continue;
+                                p.acc[k] = __fadd_rd(p.acc[k], rest_chunk(cb + p.n[k] * 32, ub + p.q[k] * 32,
+                                                                          lbp + p.q[k] * 32, p.n[k] & 7, p.q[k] & 7));
+                                terms += (unsigned)min(kMvChunk, a.E - c * kMvChunk);
+                            }
+                        }
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(empty0 + 8 * s);
+                        if ((c - c0) % kRestCheck == kRestCheck - 1) {
+                            const bool any = rest_check(p, a, n0, q0);
+                            if (!consumers_any(any && !flags[1])) {
+                                if (tid == 0) flags[0] = 1;  // stop the producer
+                                break;
+                            }
+                        }
+                    }
+                    if (!flags[1]) rest_store(p, a, n0, q0);
+                }
+                __syncthreads();  // the producer is done issuing this round's chunks
+                if (!producer) {
+                    // chunks the producer issued past the consumers' stop: let them land
+                    // and release their stages, so the stage parities stay in step
+                    const int issued = flags[2];
+                    for (; consumed < issued; ++consumed, ++kc) {
+                        const uint32_t s = kc & 1u;
+                        mbar_wait(full0 + 8 * s, (kc >> 1) & 1u, nullptr, wait_ns);
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(empty0 + 8 * s);
+                    }
+                    if (tid == 0) flags[0] = 0;
+                }
+                __syncthreads();
+            }
+        }
+    }
+    if (!producer) rest_terms_flush(a, terms);
+    // no copy may still be landing when the CTA exits (after a timeout the consumers may
+    // have stopped waiting for some): the producer waits, bounded, for the last phase of
+    // each stage it issued
+    if (tid == kRestCons)
+        for (uint32_t j = kp >= 2 ? kp - 2 : 0; j < kp; ++j) mbar_wait(full0 + 8 * (j & 1u), (j >> 1) & 1u, nullptr, wait_ns);
+}
+
+// ------------------------------------------------------------------ cp.async form
+
+// Copies chunk [e0, e0+32) of the tile's candidates and queries into one buffer:
+// candidate rows [tn][32], query rows [qg][64] (U then Lo), segments swizzled by row.
 __device__ __forceinline__ void rest_issue(const LbMvRestArgs &a, int64_t n0, int tn, int q0, int nq, int e0,
                                            bool vec4, float *sc, float *se) {
     const int tid = threadIdx.x;
     if (vec4) {
-        for (int idx = tid; idx < tn * 8; idx += kRestThreads) {
+        for (int idx = tid; idx < tn * 8; idx += kRestCpThreads) {
             const int row = idx >> 3, seg = idx & 7;
             const int64_t n = n0 + row;
             const int e = e0 + seg * 4;
@@ -61,7 +326,7 @@ __device__ __forceinline__ void rest_issue(const LbMvRestArgs &a, int64_t n0, in
             cp_async16(sc + row * 32 + ((seg ^ (row & 7)) << 2), src, ok ? 16 : 0);
         }
     } else {
-        for (int idx = tid; idx < tn * 32; idx += kRestThreads) {
+        for (int idx = tid; idx < tn * 32; idx += kRestCpThreads) {
             const int row = idx >> 5, el = idx & 31;
             const int64_t n = n0 + row;
             const int e = e0 + el;
@@ -72,65 +337,43 @@ __device__ __forceinline__ void rest_issue(const LbMvRestArgs &a, int64_t n0, in
     }
     // envelope rows are padded with +inf / -inf up to ldP (a multiple of 32), so a
     // chunk that starts below E lies inside the row, and its elements >= E add 0
-    for (int idx = tid; idx < nq * 16; idx += kRestThreads) {
+    for (int idx = tid; idx < nq * 16; idx += kRestCpThreads) {
         const int row = idx >> 4, h = (idx >> 3) & 1, seg = idx & 7;
         const float *src = (h ? a.Lp : a.Up) + (size_t)(q0 + row) * a.ldP + e0 + seg * 4;
         cp_async16(se + row * 64 + h * 32 + ((seg ^ (row & 7)) << 2), src, 16);
     }
 }
 
-__global__ void __launch_bounds__(kRestThreads, 1) k_lb_mv_rest(const LbMvRestArgs a, int tn, int qg, int vec4) {
+constexpr size_t rest_cp_smem(int tn, int qg) {
+    return ((size_t)2 * tn * 32 + (size_t)2 * qg * 64 + qg + 4) * sizeof(float);
+}
+static_assert(rest_cp_smem(kRestTC, kRestQG) <= 227 * 1024, "one CTA of the completion stream per SM");
+
+__global__ void __launch_bounds__(kRestCpThreads, 1) k_lb_mv_rest_cp(const LbMvRestArgs a, int tn, int qg, int vec4) {
     extern __shared__ __align__(16) float rs[];
     // buffer b: candidates at rs + b * tn * 32, envelopes at env0 + b * qg * 64
     float *const env0 = rs + 2 * tn * 32;
     float *thr = env0 + 2 * qg * 64;
     int *s_cnt = reinterpret_cast<int *>(thr + qg);
     uint32_t *list = a.list + (size_t)blockIdx.x * tn * qg;
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x;
     const int nchunks = (a.E + kMvChunk - 1) / kMvChunk, c0 = a.E0 / kMvChunk;
     const int64_t n_tiles = (a.N + tn - 1) / tn;
-    unsigned long long terms = 0;  // (element, pair) terms this thread summed
+    unsigned long long terms = 0;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int64_t n0 = tile * tn;
         for (int q0 = 0; q0 < a.Mb; q0 += qg) {
             const int nq = min(qg, a.Mb - q0);
             __syncthreads();  // the previous pass is done with the thresholds and the list
             if (tid == 0) *s_cnt = 0;
-            for (int k = tid; k < nq; k += kRestThreads)
-                thr[k] = a.thresh ? a.thresh[q0 + k] : prune_threshold(ld_volatile_u64(a.bsf + q0 + k), a.rho);
+            for (int k = tid; k < nq; k += blockDim.x) thr[k] = rest_threshold(a, q0 + k);
             __syncthreads();
-            // the live pairs of the tile; whole warps take part in every ballot
-            // (nq * tn is a multiple of 32)
-            for (int base = 0; base < nq * tn; base += kRestThreads) {
-                const int idx = base + tid;
-                const int ql = idx / tn, nl = idx - ql * tn;
-                bool live = false;
-                if (ql < nq && n0 + nl < a.N) {
-                    const float v = a.lb[(size_t)(q0 + ql) * a.ldLb + n0 + nl];
-                    live = v < TC_INF && v <= thr[ql];
-                }
-                const unsigned bal = __ballot_sync(0xffffffffu, live);
-                int pos = 0;
-                if (lane == 0 && bal) pos = atomicAdd(s_cnt, __popc(bal));
-                pos = __shfl_sync(0xffffffffu, pos, 0);
-                if (live) list[pos + __popc(bal & ((1u << lane) - 1u))] = ((uint32_t)ql << 16) | (uint32_t)nl;
-            }
+            rest_list(a, n0, tn, q0, nq, thr, s_cnt, list);
             __syncthreads();  // the list (global, this CTA's region) and its count
             const int cnt = *s_cnt;
-            for (int r0 = 0; r0 < cnt; r0 += kRestRound) {
-                int qk[kRestEpt], nk[kRestEpt];
-                float acc[kRestEpt], th[kRestEpt];
-                bool act[kRestEpt];
-#pragma unroll
-                for (int k = 0; k < kRestEpt; ++k) {
-                    const int i = r0 + k * kRestThreads + tid;
-                    act[k] = i < cnt;
-                    const uint32_t en = act[k] ? __ldcg(list + i) : 0u;
-                    qk[k] = (int)(en >> 16);
-                    nk[k] = (int)(en & 0xffffu);
-                    acc[k] = act[k] ? a.lb[(size_t)(q0 + qk[k]) * a.ldLb + n0 + nk[k]] : 0.f;
-                    th[k] = thr[qk[k]];
-                }
+            for (int r0 = 0; r0 < cnt; r0 += kRestCpThreads * kRestEpt) {
+                RestPairs p;
+                rest_load(p, a, list, r0, tid, kRestCpThreads, cnt, n0, q0, thr);
                 rest_issue(a, n0, tn, q0, nq, c0 * kMvChunk, vec4, rs, env0);
                 cp_async_commit();
                 for (int c = c0; c < nchunks; ++c) {
@@ -144,57 +387,32 @@ __global__ void __launch_bounds__(kRestThreads, 1) k_lb_mv_rest(const LbMvRestAr
                         cp_async_wait<0>();
                     }
                     __syncthreads();
+                    const float *cb = rs + buf * tn * 32, *eb = env0 + buf * qg * 64;
 #pragma unroll
                     for (int k = 0; k < kRestEpt; ++k) {
-                        if (!act[k]) continue;
-                        const float *cr = rs + buf * tn * 32 + nk[k] * 32;
-                        const float *ur = env0 + buf * qg * 64 + qk[k] * 64, *lr = ur + 32;
-                        const int cs = nk[k] & 7, es = qk[k] & 7;
-                        f2 p = 0ull;
-#pragma unroll
-                        for (int sg = 0; sg < 8; ++sg) {
-                            const float4 cv = *reinterpret_cast<const float4 *>(cr + ((sg ^ cs) << 2));
-                            const float4 uv = *reinterpret_cast<const float4 *>(ur + ((sg ^ es) << 2));
-                            const float4 lv = *reinterpret_cast<const float4 *>(lr + ((sg ^ es) << 2));
-                            p = rest_step(pk(cv.x, cv.y), pk(uv.x, uv.y), pk(lv.x, lv.y), p);
-                            p = rest_step(pk(cv.z, cv.w), pk(uv.z, uv.w), pk(lv.z, lv.w), p);
-                        }
-                        float p0, p1;
-                        upk(p, p0, p1);
-                        acc[k] = __fadd_rd(acc[k], __fadd_rd(p0, p1));
+                        if (!p.act[k]) continue;
+                        const float *ur = eb + p.q[k] * 64;
+                        p.acc[k] = __fadd_rd(p.acc[k], rest_chunk(cb + p.n[k] * 32, ur, ur + 32, p.n[k] & 7,
+                                                                  p.q[k] & 7));
                         terms += (unsigned)min(kMvChunk, a.E - c * kMvChunk);
                     }
                     if ((c - c0) % kRestCheck == kRestCheck - 1) {
-                        bool any = false;
-#pragma unroll
-                        for (int k = 0; k < kRestEpt; ++k) {
-                            if (act[k] && acc[k] > th[k]) {  // abandoned: its partial sum
-                                a.lb[(size_t)(q0 + qk[k]) * a.ldLb + n0 + nk[k]] = acc[k];
-                                act[k] = false;
-                            }
-                            any |= act[k];
-                        }
                         // (also the barrier before the other buffer is refilled)
-                        if (!__syncthreads_or(any)) break;
+                        if (!__syncthreads_or(rest_check(p, a, n0, q0))) break;
                     } else {
                         __syncthreads();
                     }
                 }
-#pragma unroll
-                for (int k = 0; k < kRestEpt; ++k)
-                    if (act[k]) a.lb[(size_t)(q0 + qk[k]) * a.ldLb + n0 + nk[k]] = acc[k];
+                rest_store(p, a, n0, q0);
                 cp_async_wait<0>();  // a stream left early may still have a chunk in flight
                 __syncthreads();
             }
         }
     }
-    if (a.terms) {
-        for (int o = 16; o > 0; o >>= 1) terms += __shfl_xor_sync(0xffffffffu, terms, o);
-        if (lane == 0 && terms) atomicAdd(a.terms, terms);
-    }
+    rest_terms_flush(a, terms);
 }
 
-int g_rest_attr_dev = -1;
+int g_attr_dev_tma = -1, g_attr_dev_cp = -1;
 
 }  // namespace
 
@@ -219,8 +437,8 @@ int64_t lb_mv_rest_list_entries(int64_t N, int Mb, int sms) {
 
 cudaError_t launch_lb_mv_rest(const LbMvRestArgs &a, cudaStream_t s) {
     if (a.N <= 0 || a.Mb <= 0 || a.E0 >= a.E) return cudaSuccess;
-    if (a.E0 % kMvChunk != 0 || a.ldP % kMvChunk != 0 || a.ldP < a.E ||
-        (((uintptr_t)a.Up) & 15) != 0 || (((uintptr_t)a.Lp) & 15) != 0)
+    if (a.E0 % kMvChunk != 0 || a.ldP % kMvChunk != 0 || a.ldP < a.E || (((uintptr_t)a.Up) & 15) != 0 ||
+        (((uintptr_t)a.Lp) & 15) != 0)
         return cudaErrorInvalidValue;
     const int sms = a.sms > 0 ? a.sms : 1;
     const int tn = lb_mv_rest_tile(a.N, sms);
@@ -228,17 +446,37 @@ cudaError_t launch_lb_mv_rest(const LbMvRestArgs &a, cudaStream_t s) {
     const int64_t tiles = (a.N + tn - 1) / tn;
     const int64_t grid = tiles < sms ? tiles : sms;
     if (a.list_entries < grid * tn * qg) return cudaErrorInvalidValue;
-    const size_t smem = ((size_t)2 * tn * 32 + (size_t)2 * qg * 64 + qg + 4) * sizeof(float);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (g_rest_attr_dev != dev) {
-        e = cudaFuncSetAttribute(k_lb_mv_rest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRestSmemMax);
-        if (e != cudaSuccess) return e;
-        g_rest_attr_dev = dev;
+    // bulk-tensor copies need 16-byte aligned rows (and a status word for the waits)
+    CUtensorMap cm, um, lm;
+    const bool tma = a.status && (a.ldC % 4) == 0 && (((uintptr_t)a.cand) & 15) == 0 && a.N < ((int64_t)1 << 31) &&
+                     encode_2d(&cm, a.cand, (uint64_t)a.E, (uint64_t)a.N, (uint64_t)a.ldC * 4, kMvChunk, tn,
+                               CU_TENSOR_MAP_SWIZZLE_128B) &&
+                     encode_2d(&um, a.Up, (uint64_t)a.ldP, (uint64_t)a.Mb, (uint64_t)a.ldP * 4, kMvChunk, qg,
+                               CU_TENSOR_MAP_SWIZZLE_128B) &&
+                     encode_2d(&lm, a.Lp, (uint64_t)a.ldP, (uint64_t)a.Mb, (uint64_t)a.ldP * 4, kMvChunk, qg,
+                               CU_TENSOR_MAP_SWIZZLE_128B);
+    if (tma) {
+        if (g_attr_dev_tma != dev) {
+            e = cudaFuncSetAttribute(k_lb_mv_rest_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)rest_tma_smem(kRestTC, kRestQG));
+            if (e != cudaSuccess) return e;
+            g_attr_dev_tma = dev;
+        }
+        k_lb_mv_rest_tma<<<(unsigned)grid, kRestTmaThreads, rest_tma_smem(tn, qg), s>>>(cm, um, lm, a, tn, qg,
+                                                                                       kWaitNs);
+    } else {
+        if (g_attr_dev_cp != dev) {
+            e = cudaFuncSetAttribute(k_lb_mv_rest_cp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)rest_cp_smem(kRestTC, kRestQG));
+            if (e != cudaSuccess) return e;
+            g_attr_dev_cp = dev;
+        }
+        const int vec4 = (a.E % 4) == 0 && (a.ldC % 4) == 0 && (((uintptr_t)a.cand) & 15) == 0;
+        k_lb_mv_rest_cp<<<(unsigned)grid, kRestCpThreads, rest_cp_smem(tn, qg), s>>>(a, tn, qg, vec4);
     }
-    const int vec4 = (a.E % 4) == 0 && (a.ldC % 4) == 0 && (((uintptr_t)a.cand) & 15) == 0;
-    k_lb_mv_rest<<<(unsigned)grid, kRestThreads, smem, s>>>(a, tn, qg, vec4);
     note_launch();
     return cudaGetLastError();
 }
