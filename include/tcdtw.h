@@ -91,14 +91,15 @@ typedef struct tcdtw_index tcdtw_index; /* opaque; created by tcdtw_build */
  *          needs W <= 127 (else tcdtw_build and tcdtw_lower_bounds return
  *          UNSUPPORTED); tcdtw_batch_nn always uses 1.
  *  mv_abandon  1 = LB_MV with early abandoning (Section 7.1 applies abandoning to the
- *          lower bounds as well as to DTW): a block of at least 32 queries sums a prefix
- *          of every pair's LB_MV elements first (32 * clamp(ceil32(L*D)/512, 1, 8)
- *          elements), takes seed_s seeds from those prefix sums and runs their DTW,
- *          then completes LB_MV only for the pairs at or under the seeded threshold
- *          (the others keep their prefix sum, a lower bound above the threshold), and
- *          runs the DTW of a second round of seed_s seeds, the smallest completed
- *          bounds.  Rows of fewer than 128 elements never abandon.  The answers are the
- *          same (1).
+ *          lower bounds as well as to DTW): a block of at least 32 queries first sums,
+ *          for every pair, a sample of its LB_MV elements: s = clamp(C/16, 1, 8) chunks
+ *          of 32 spread evenly over the row (chunks 0, C/s, 2C/s, ...; C = ceil(L*D/32)),
+ *          a sum over a subset of the terms and hence a lower bound.  It takes seed_s
+ *          seeds from those sample sums and runs their DTW, then completes LB_MV only
+ *          for the pairs at or under the seeded threshold (the others keep their sample
+ *          sum, a lower bound above the threshold), and runs the DTW of a second round
+ *          of seed_s seeds, the smallest completed bounds (tcdtw_batch_nn: one round).
+ *          Rows of fewer than 128 elements never abandon.  The answers are the same (1).
  */
 typedef struct {
     int32_t P;
@@ -201,7 +202,7 @@ int tcdtw_index_info(tcdtw_index *index, int32_t *tile, int32_t *G, int32_t *qbl
  * every query block records CUDA events on the caller's stream at the stage
  * boundaries below and tcdtw_nn synchronises at its end to add the elapsed times.
  * Stages: 0 non-finite scan, 1 query preparation (envelope, dq, boxes), 2 LB_MV (with
- * mv_abandon: over the prefix), 3 seeds (selection and their DTW), 4 completion of the
+ * mv_abandon: over the sample), 3 seeds (selection and their DTW), 4 completion of the
  * abandoning LB_MV, 5 second seed round (4 and 5 are empty without abandoning),
  * 6 compaction, 7 LB_PC / LB_TI cascade, 8 DTW of the survivors, 9 refine (double-float,
  * then FP64 where needed) and selection.
@@ -286,7 +287,7 @@ int tcdtw_lower_bounds(const float *q, int64_t M, const float *c, int64_t N, int
                        void *stream);
 
 /* LB_MV with early abandoning against per-query thresholds (Section 7.1): every pair
- * first sums a prefix of its elements (the length mv_abandon uses); pairs whose prefix
+ * first sums a sample of its elements (the chunks mv_abandon uses); pairs whose sample
  * sum is at most thresh[m] complete the sum, the others stop there.  Hence
  * out[m][n] <= the exact LB_MV <= DTW(q[m], c[n]); where the computed LB_MV (rounded
  * down; summation order as in the search, which may differ from tcdtw_lower_bounds in

@@ -268,9 +268,10 @@ struct tcdtw_index {
     float *Uc = nullptr, *Lc = nullptr;  // candidate envelopes [N][L*D] (use_rev)
     float2 *ref_tab = nullptr;   // global cost tables of the double-float refine (long bands)
     int ref_slots = 0;
-    // LB_MV with early abandoning (opts.mv_abandon): prefix length (0: off), second-round
-    // seeds per query, the envelope one query per row, the completion kernel's pair lists
-    int mv_prefix = 0, S2 = 0;
+    // LB_MV with early abandoning (opts.mv_abandon): the sampled chunks (count, 0: off, and
+    // stride), second-round seeds per query, the envelope one query per row, the
+    // completion kernel's pair lists
+    int mv_samp = 0, mv_stride = 1, S2 = 0;
     float *Up = nullptr, *Lp = nullptr;
     uint32_t *rest_list = nullptr;
     int64_t rest_list_entries = 0;
@@ -350,7 +351,7 @@ int alloc_index(tcdtw_index *x) {
     TC_TRY(dalloc(&x->lbm, (size_t)Mb * N));
     TC_TRY(dalloc(&x->seeds, (size_t)Mb * (x->S + x->S2)));
     TC_TRY(dalloc(&x->seed_dtw, (size_t)Mb * (x->S + x->S2)));
-    if (x->mv_prefix > 0) {
+    if (x->mv_samp > 0) {
         TC_TRY(dalloc(&x->Up, (size_t)Mb * x->ldE));
         TC_TRY(dalloc(&x->Lp, (size_t)Mb * x->ldE));
         x->rest_list_entries = lb_mv_rest_list_entries(N, x->Mb, x->sms);
@@ -436,7 +437,7 @@ cudaError_t mark(tcdtw_index *x, int k, cudaStream_t s) {
 // repeats for any tile with a live pair, and the second seed round adds a DTW sweep of
 // latency: the plain stream is faster there.
 constexpr int kAbandonMinQueries = 32;
-bool block_abandons(const tcdtw_index *x, int Mb_cur) { return x->mv_prefix > 0 && Mb_cur >= kAbandonMinQueries; }
+bool block_abandons(const tcdtw_index *x, int Mb_cur) { return x->mv_samp > 0 && Mb_cur >= kAbandonMinQueries; }
 
 // Seed entries of a block (both rounds).
 int64_t block_seeds(const tcdtw_index *x, int Mb_cur) {
@@ -479,8 +480,10 @@ cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_o
         mv.cand = x->cand; mv.N = N; mv.E = E; mv.U = x->U; mv.Lo = x->Lo; mv.ldE = x->ldE; mv.Mb = Mb_cur;
         mv.lb = x->lbm; mv.ldLb = N; mv.sms = x->sms; mv.status = x->status;
         mv.ws = x->mv_ws; mv.ws_floats = x->mv_ws_floats; mv.tile_cnt = x->mv_cnt; mv.tile_cnt_cap = kMvTileCounters;
-        if (ab) {  // with abandoning: the prefix [0, mv_prefix) of every pair first
-            mv.E = x->mv_prefix;
+        if (ab) {  // with abandoning: the sampled chunks of every pair first
+            mv.E = x->mv_samp * 32;
+            mv.cstride = x->mv_stride;
+            mv.Erow = E;
             mv.ldC = E;
         }
         if ((e = launch_lb_mv(mv, s)) != cudaSuccess) return e;
@@ -497,9 +500,9 @@ cudaError_t run_block(tcdtw_index *x, const float *q, int Mb_cur, int64_t *idx_o
     TC_MARK(4);
     if (ab) {
         // the pairs still at or under the seeded threshold complete their LB_MV (the
-        // others keep the prefix sum, a lower bound above the threshold) ...
+        // others keep the sample sum, a lower bound above the threshold) ...
         LbMvRestArgs ra;
-        ra.cand = x->cand; ra.N = N; ra.E = E; ra.E0 = x->mv_prefix; ra.ldC = E; ra.Up = x->Up; ra.Lp = x->Lp;
+        ra.cand = x->cand; ra.N = N; ra.E = E; ra.samp = x->mv_samp; ra.sstride = x->mv_stride; ra.ldC = E; ra.Up = x->Up; ra.Lp = x->Lp;
         ra.ldP = x->ldE; ra.Mb = Mb_cur; ra.lb = x->lbm; ra.ldLb = N; ra.thresh = nullptr; ra.bsf = x->bsf;
         ra.rho = x->rho; ra.list = x->rest_list; ra.list_entries = x->rest_list_entries; ra.sms = x->sms;
         ra.terms = x->counters + kMvTerms; ra.status = x->status;
@@ -755,9 +758,9 @@ int tcdtw_build(const float *cand, int64_t N, int32_t L, int32_t D, int32_t W, i
     if (!x) return TCDTW_ERR_NOMEM;
     x->cand = cand; x->N = N; x->L = L; x->D = D; x->W = W; x->K = K; x->opts = o;
     x->S = (int)(o.seed_s < N ? o.seed_s : N);
-    // LB_MV with early abandoning: a prefix of every pair, then the live pairs' rest
-    x->mv_prefix = (o.mv_abandon && !o.no_prune) ? lb_mv_prefix(L * D) : 0;
-    x->S2 = x->mv_prefix > 0 ? (int)std::min<int64_t>(x->S, N - x->S) : 0;
+    // LB_MV with early abandoning: a spread sample of every pair, then the live pairs' rest
+    x->mv_samp = (o.mv_abandon && !o.no_prune) ? lb_mv_sample(L * D, &x->mv_stride) : 0;
+    x->S2 = x->mv_samp > 0 ? (int)std::min<int64_t>(x->S, N - x->S) : 0;
     x->sms = num_sms();
     x->G_pc = (L + o.w - 1) / o.w;
     x->ldE = ((int64_t)L * D + 31) / 32 * 32;
@@ -880,13 +883,13 @@ int tcdtw_nn(tcdtw_index *x, const float *q, int64_t M, int64_t *idx, double *di
         stats->pruned_pc = c[kPrunedPc];
         stats->pruned_ti = c[kPrunedTi];
         stats->pruned_rev = c[kPrunedRev];
-        // the dense stream's terms (all of every pair, or the prefix of every pair) are
+        // the dense stream's terms (all of every pair, or the sample of every pair) are
         // counted here; the completion kernel counts its own
         uint64_t dense = 0;
         if (!x->opts.no_prune)
             for (int64_t m0 = 0; m0 < M; m0 += x->Mb) {
                 const int mb = (int)((M - m0) < x->Mb ? (M - m0) : x->Mb);
-                dense += (uint64_t)mb * (uint64_t)x->N * (uint64_t)(block_abandons(x, mb) ? x->mv_prefix : E);
+                dense += (uint64_t)mb * (uint64_t)x->N * (uint64_t)(block_abandons(x, mb) ? 32 * x->mv_samp : E);
             }
         stats->mv_terms = dense + c[kMvTerms];
         stats->dtw_started = c[kStarted];
@@ -995,11 +998,12 @@ int tcdtw_lb_mv_abandon(const float *q, int64_t M, const float *c, int64_t N, in
     cudaStream_t s = (cudaStream_t)stream;
     const int sms = num_sms();
     const int E = L * D;
-    const int E0 = lb_mv_prefix(E);
+    int sstride = 1;
+    const int samp = lb_mv_sample(E, &sstride);
     const int64_t ldE = ((int64_t)E + 31) / 32 * 32;
     const int64_t Mp = (M + 31) / 32 * 32;
     const int64_t ws_floats = std::min<int64_t>(kMvWsFloats, 64 * M * N);
-    const int64_t list_n = E0 > 0 ? lb_mv_rest_list_entries(N, (int)std::min<int64_t>(M, kRestQG), sms) : 1;
+    const int64_t list_n = samp > 0 ? lb_mv_rest_list_entries(N, (int)std::min<int64_t>(M, kRestQG), sms) : 1;
     float *U = nullptr, *Lo = nullptr, *Up = nullptr, *Lp = nullptr, *ws = nullptr;
     DevStatus *st = nullptr;
     int32_t *cnt = nullptr;
@@ -1027,16 +1031,17 @@ int tcdtw_lb_mv_abandon(const float *q, int64_t M, const float *c, int64_t N, in
         e = launch_envelope_pairs_plain(q + m0 * E, mc, L, D, W, U + m0 * ldE, Lo + m0 * ldE, Up + m0 * ldE,
                                         Lp + m0 * ldE, (int)ldE, s);
     }
-    if (e == cudaSuccess) {  // the prefix of every pair (all of it when E0 == 0)
+    if (e == cudaSuccess) {  // the sample of every pair (all of it without a sample)
         LbMvArgs mv;
-        mv.cand = c; mv.N = N; mv.E = E0 > 0 ? E0 : E; mv.ldC = E; mv.U = U; mv.Lo = Lo; mv.ldE = ldE;
+        mv.cand = c; mv.N = N; mv.E = samp > 0 ? 32 * samp : E; mv.cstride = sstride; mv.Erow = E; mv.ldC = E;
+        mv.U = U; mv.Lo = Lo; mv.ldE = ldE;
         mv.Mb = (int)M; mv.lb = out; mv.ldLb = N; mv.sms = sms; mv.status = st;
         mv.ws = ws; mv.ws_floats = ws_floats; mv.tile_cnt = cnt; mv.tile_cnt_cap = kMvTileCounters;
         e = launch_lb_mv(mv, s);
     }
-    if (e == cudaSuccess && E0 > 0) {  // the rest of the pairs still under their threshold
+    if (e == cudaSuccess && samp > 0) {  // the rest of the pairs still under their threshold
         LbMvRestArgs ra;
-        ra.cand = c; ra.N = N; ra.E = E; ra.E0 = E0; ra.ldC = E; ra.Up = Up; ra.Lp = Lp; ra.ldP = ldE;
+        ra.cand = c; ra.N = N; ra.E = E; ra.samp = samp; ra.sstride = sstride; ra.ldC = E; ra.Up = Up; ra.Lp = Lp; ra.ldP = ldE;
         ra.Mb = (int)M; ra.lb = out; ra.ldLb = N; ra.thresh = thresh; ra.bsf = nullptr; ra.rho = 1.f;
         ra.list = list; ra.list_entries = list_n; ra.sms = sms; ra.status = st;
         e = launch_lb_mv_rest(ra, s);

@@ -38,6 +38,7 @@
 #include "dtw_core.cuh"
 #include "lb_device.cuh"
 #include "lb_kernels.cuh"
+#include "lb_rest.cuh"
 #include "prep_device.cuh"
 
 namespace tc {
@@ -113,6 +114,10 @@ __device__ void prep_item(const BatchSet &S, int q, float *smem, BatchCtl *ctl) 
         const size_t pos = (size_t)(((q >> 1) * S.ldE + k) * 2 + (q & 1));
         S.U[pos] = u;
         S.Lo[pos] = l;
+        if (S.samp > 0) {  // the one-query-per-row copy the LB_MV completion reads
+            S.Up[(size_t)q * S.ldE + k] = u;
+            S.Lp[(size_t)q * S.ldE + k] = l;
+        }
     }
     if (S.use_ti) {
         for (int i = threadIdx.x; i < L; i += blockDim.x) {
@@ -218,7 +223,8 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_front(const BatchSet *_
             float(*su)[kBatchQB * kMvChunk] = (float(*)[kBatchQB * kMvChunk])(bsm + 2 * kMvRows * kMvChunk);
             float(*sl)[kBatchQB * kMvChunk] =
                 (float(*)[kBatchQB * kMvChunk])(bsm + 2 * kMvRows * kMvChunk + 2 * kBatchQB * kMvChunk);
-            lb_mv_tile<kBatchQB>(S.cand, S.N, S.L * S.D, (int64_t)S.L * S.D, S.vec4 != 0, S.U, S.Lo, S.ldE, S.M, S.lbm, S.N,
+            lb_mv_tile<kBatchQB>(S.cand, S.N, S.samp > 0 ? S.samp : (S.L * S.D + kMvChunk - 1) / kMvChunk,
+                                 S.samp > 0 ? S.sstride : 1, S.L * S.D, (int64_t)S.L * S.D, S.vec4 != 0, S.U, S.Lo, S.ldE, S.M, S.lbm, S.N,
                                  (int64_t)item.b * kMvRows, item.a * kBatchQB, sc, su, sl);
             batch_done(S.cnt + kCntMv);
         } else if (item.kind == kItemSeed) {
@@ -321,6 +327,65 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_mid(const BatchSet *__r
         const BatchItem item = items[it];
         mid_item(sets[item.set], item.a, ctl);
     }
+}
+
+// ------------------------------------------------------------------ LB_MV completion
+// Items (set, candidate tile of kBatchRestTile): the completion pass of the abandoning
+// LB_MV (lb_rest.cuh), against the best-so-far the seeds left; the pairs whose sample
+// sum already exceeds the threshold keep it.
+constexpr int kBatchRestTile = kRestTC;
+constexpr int kSeed2Threads = 256;
+
+// Second-round seeds of query q (sets whose LB_MV abandons): the S2 smallest bounds of
+// the completed row go to the slots after the first round's seeds, marked pending for
+// the DTW phase 2 (and set to +inf in the row, so compaction skips them).
+__device__ void seed2_item(const BatchSet &S, int q) {
+    __shared__ uint32_t picked[kSeedSlots];
+    const int na = S.nseed[q];
+    const int s2 = min(S.S2, kSeedSlots - na);
+    if (s2 <= 0) return;  // (the same for every thread)
+    seed_topk_row(S.lbm + (size_t)q * S.N, S.N, s2, picked);
+    if (threadIdx.x < (unsigned)s2) {
+        const uint32_t n = picked[threadIdx.x];
+        S.seeds[(size_t)q * kSeedSlots + na + threadIdx.x] = n;
+        S.seed_dtw[(size_t)q * kSeedSlots + na + threadIdx.x] = n != 0xffffffffu ? kSeedPending : TC_INF;
+    }
+    if (threadIdx.x == 0) {
+        int ns = 0;
+        for (int k = 0; k < s2; ++k) ns += picked[k] != 0xffffffffu;
+        S.nseed[q] = na + ns;
+    }
+}
+
+__global__ void __launch_bounds__(kSeed2Threads) k_batch_seed2(const BatchSet *__restrict__ sets,
+                                                               const BatchItem *__restrict__ items, int begin) {
+    const BatchItem item = items[begin + blockIdx.x];
+    seed2_item(sets[item.set], item.a);
+}
+
+__global__ void __launch_bounds__(kRestCpThreads, 1) k_batch_rest(const BatchSet *__restrict__ sets,
+                                                                  const BatchItem *__restrict__ items, int begin,
+                                                                  int end, BatchCtl *ctl, uint32_t *lists,
+                                                                  int qg_max) {
+    extern __shared__ __align__(16) float rs[];
+    uint32_t *list = lists + (size_t)blockIdx.x * kBatchRestTile * qg_max;
+    unsigned long long terms = 0;
+    LbMvRestArgs a;
+    memset(&a, 0, sizeof(a));
+    for (;;) {
+        const int it = grab_item(ctl, 3, begin, end);
+        if (it >= end) break;
+        const BatchItem item = items[it];
+        const BatchSet &S = sets[item.set];
+        a.cand = S.cand; a.N = S.N; a.E = S.L * S.D; a.samp = S.samp; a.sstride = S.sstride; a.ldC = a.E; a.Up = S.Up; a.Lp = S.Lp;
+        a.ldP = S.ldE; a.Mb = S.M; a.lb = S.lbm; a.ldLb = S.N; a.thresh = nullptr; a.bsf = S.bsf; a.rho = S.rho;
+        const int qg = min(S.M, qg_max);
+        for (int q0 = 0; q0 < S.M; q0 += qg)
+            rest_pass_cp(a, (int64_t)item.a * kBatchRestTile, kBatchRestTile, q0, min(qg, S.M - q0), qg, S.vec4, rs,
+                         list, terms);
+    }
+    a.terms = &ctl->counters[9];
+    rest_terms_flush(a, terms);
 }
 
 // ------------------------------------------------------------------ refine launch
@@ -500,8 +565,13 @@ struct BatchPlan {
     BatchCtl *d_ctl = nullptr;
     int *d_counts = nullptr, *d_order = nullptr;
     int n_sets = 0;
-    int front_end = 0, mid_end = 0, n_items = 0;  // item ranges [0, front_end), [front_end, mid_end), [mid_end, n_items)
-    int grid_front = 0, grid_mid = 0, grid_refine = 0;
+    // item ranges: front [0, front_end), LB_MV completion [front_end, rest_end), second-
+    // round seeds [rest_end, seed2_end), mid [seed2_end, mid_end), refine [mid_end, n_items)
+    int front_end = 0, rest_end = 0, seed2_end = 0, mid_end = 0, n_items = 0;
+    int grid_front = 0, grid_mid = 0, grid_refine = 0, grid_rest = 0;
+    int rest_qg = 0;              // queries per completion pass (0: no set abandons)
+    uint32_t *d_rest_lists = nullptr;
+    uint64_t dense_terms = 0;     // LB_MV terms of the front's tiles per run
     // DTW launches: per tile class present, its sets d_order[off, off + n) and grid
     struct DtwClass { int R, dm, off, n, grid; };
     std::vector<DtwClass> classes;
@@ -513,7 +583,8 @@ struct BatchPlan {
     // tail (its last, longest pairs on a few warps) overlaps the others' work
     static constexpr int kSide = 4;
     cudaStream_t side[kSide] = {};
-    cudaEvent_t ev_fork[2] = {}, ev_join[2][kSide] = {};
+    static constexpr int kPhases = 3;  // seeds, survivors, second-round seeds
+    cudaEvent_t ev_fork[kPhases] = {}, ev_join[kPhases][kSide] = {};
 };
 std::vector<BatchPlan *> g_plans;
 std::mutex g_plans_mu;
@@ -524,10 +595,10 @@ void free_plan(BatchPlan *p) {
     if (p->exec) cudaGraphExecDestroy(p->exec);
     for (int k = 0; k < BatchPlan::kSide; ++k) {
         if (p->side[k]) cudaStreamDestroy(p->side[k]);
-        for (int ph = 0; ph < 2; ++ph)
+        for (int ph = 0; ph < BatchPlan::kPhases; ++ph)
             if (p->ev_join[ph][k]) cudaEventDestroy(p->ev_join[ph][k]);
     }
-    for (int ph = 0; ph < 2; ++ph)
+    for (int ph = 0; ph < BatchPlan::kPhases; ++ph)
         if (p->ev_fork[ph]) cudaEventDestroy(p->ev_fork[ph]);
     cudaFree(p->arena);
     delete p;
@@ -588,8 +659,13 @@ int build_plan(const tcdtw_dataset *sets, const std::vector<int> &mk, const tcdt
         b.ldE = ((int64_t)d.L * d.D + 31) / 32 * 32;
         b.n_qtiles = (int)((d.M + kBatchQB - 1) / kBatchQB);
         b.n_ctiles = (int)((d.N + kMvRows - 1) / kMvRows);
+        // LB_MV with early abandoning for sets of at least 32 queries (as tcdtw_nn)
+        b.samp = (o.mv_abandon && !o.no_prune && d.M >= 32) ? lb_mv_sample(d.L * d.D, &b.sstride) : 0;
+        b.S2 = b.samp > 0 ? (int)std::max<int64_t>(0, std::min<int64_t>(std::min(b.S, kSeedSlots - b.S), d.N - b.S)) : 0;
+        p->dense_terms += (uint64_t)d.M * d.N * (uint64_t)(b.samp > 0 ? 32 * b.samp : d.L * d.D);
         const size_t Mp = (size_t)(d.M + 1) / 2 * 2, M = (size_t)d.M, N = (size_t)d.N;
         bytes += 2 * carve_bytes<float>(Mp * b.ldE) + 2 * carve_bytes<float>(M * d.L);
+        if (b.samp > 0) bytes += 2 * carve_bytes<float>(M * b.ldE);
         if (b.use_pc) bytes += carve_bytes<float>(M * b.Gpc * d.K * 2 * d.D) + carve_bytes<int32_t>(M * b.Gpc);
         bytes += 3 * carve_bytes<float>(M * N) + 2 * carve_bytes<uint32_t>(M * N) + carve_bytes<double>(M * (N + 8));
         bytes += carve_bytes<uint32_t>(M * kSeedSlots) + carve_bytes<float>(M * kSeedSlots);
@@ -637,6 +713,16 @@ int build_plan(const tcdtw_dataset *sets, const std::vector<int> &mk, const tcdt
         for (int m = 0; m < hs[k].M; ++m) items.push_back({kItemSeed, k, m, 0});
     p->front_end = (int)items.size();
     for (int k : order)
+        if (hs[k].samp > 0) {
+            p->rest_qg = std::max(p->rest_qg, std::min(hs[k].M, kRestQG));
+            for (int64_t t = 0; t * kBatchRestTile < hs[k].N; ++t) items.push_back({kItemRest, k, (int)t, 0});
+        }
+    p->rest_end = (int)items.size();
+    for (int k : order)
+        if (hs[k].S2 > 0)
+            for (int m = 0; m < hs[k].M; ++m) items.push_back({kItemSeed2, k, m, 0});
+    p->seed2_end = (int)items.size();
+    for (int k : order)
         for (int m = 0; m < hs[k].M; ++m) items.push_back({kItemMid, k, m, 0});
     p->mid_end = (int)items.size();
     for (int k : order)
@@ -644,6 +730,9 @@ int build_plan(const tcdtw_dataset *sets, const std::vector<int> &mk, const tcdt
     p->n_items = (int)items.size();
     bytes += carve_bytes<BatchSet>(ns) + carve_bytes<BatchItem>(items.size()) + carve_bytes<BatchCtl>(1) +
              carve_bytes<int>((size_t)kCntPerSet * ns) + carve_bytes<int>(ns);
+    const int rest_items = p->rest_end - p->front_end;
+    p->grid_rest = std::max(1, std::min(rest_items, num_sms()));  // one CTA per SM (shared memory, registers)
+    if (p->rest_qg > 0) bytes += carve_bytes<uint32_t>((size_t)p->grid_rest * kBatchRestTile * p->rest_qg);
     if (dev_malloc((void **)&p->arena, bytes) != cudaSuccess) {
         delete p;
         return TCDTW_ERR_NOMEM;
@@ -654,6 +743,7 @@ int build_plan(const tcdtw_dataset *sets, const std::vector<int> &mk, const tcdt
     p->d_ctl = carve<BatchCtl>(c, 1);
     p->d_counts = carve<int>(c, (size_t)kCntPerSet * ns);
     p->d_order = carve<int>(c, ns);
+    if (p->rest_qg > 0) p->d_rest_lists = carve<uint32_t>(c, (size_t)p->grid_rest * kBatchRestTile * p->rest_qg);
     for (int k = 0; k < ns; ++k) {
         BatchSet &b = hs[k];
         const size_t Mp = (size_t)(b.M + 1) / 2 * 2, M = (size_t)b.M, N = (size_t)b.N;
@@ -661,6 +751,10 @@ int build_plan(const tcdtw_dataset *sets, const std::vector<int> &mk, const tcdt
         b.Lo = carve<float>(c, Mp * b.ldE);
         b.dq_lo = carve<float>(c, M * b.L);
         b.dq_hi = carve<float>(c, M * b.L);
+        if (b.samp > 0) {
+            b.Up = carve<float>(c, M * b.ldE);
+            b.Lp = carve<float>(c, M * b.ldE);
+        }
         if (b.use_pc) {
             b.boxes = carve<float>(c, M * b.Gpc * b.K * 2 * b.D);
             b.box_counts = carve<int32_t>(c, M * b.Gpc);
@@ -690,12 +784,16 @@ int build_plan(const tcdtw_dataset *sets, const std::vector<int> &mk, const tcdt
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     for (int k = 0; k < BatchPlan::kSide && e == cudaSuccess; ++k) {
         e = cudaStreamCreateWithFlags(&p->side[k], cudaStreamNonBlocking);
-        for (int ph = 0; ph < 2 && e == cudaSuccess; ++ph)
+        for (int ph = 0; ph < BatchPlan::kPhases && e == cudaSuccess; ++ph)
             e = cudaEventCreateWithFlags(&p->ev_join[ph][k], cudaEventDisableTiming);
     }
-    for (int ph = 0; ph < 2 && e == cudaSuccess; ++ph) e = cudaEventCreateWithFlags(&p->ev_fork[ph], cudaEventDisableTiming);
+    for (int ph = 0; ph < BatchPlan::kPhases && e == cudaSuccess; ++ph)
+        e = cudaEventCreateWithFlags(&p->ev_fork[ph], cudaEventDisableTiming);
     if (e == cudaSuccess) e = kernel_grid((const void *)k_batch_front, kBatchSmem, &p->grid_front);
     if (e == cudaSuccess) e = kernel_grid((const void *)k_batch_mid, 0, &p->grid_mid);
+    if (e == cudaSuccess && p->rest_qg > 0)
+        e = cudaFuncSetAttribute(k_batch_rest, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)rest_cp_smem(kBatchRestTile, p->rest_qg));
     if (e == cudaSuccess) e = kernel_grid((const void *)k_batch_refine, kBatchSmem, &p->grid_refine);
     if (e != cudaSuccess) {
         free_plan(p);
@@ -703,13 +801,17 @@ int build_plan(const tcdtw_dataset *sets, const std::vector<int> &mk, const tcdt
     }
     p->n_sets = ns;
     p->grid_front = std::max(1, std::min(p->grid_front, p->front_end));
-    p->grid_mid = std::max(1, std::min(p->grid_mid, p->mid_end - p->front_end));
+    p->grid_mid = std::max(1, std::min(p->grid_mid, p->mid_end - p->seed2_end));
     p->grid_refine = std::max(1, std::min(p->grid_refine, p->n_items - p->mid_end));
     *out = p;
     return TCDTW_OK;
 }
 
-int kernels_per_run(const BatchPlan *p) { return 3 + 2 * (int)p->classes.size(); }
+int kernels_per_run(const BatchPlan *p) {
+    const int nc = (int)p->classes.size();
+    const int seed2 = p->seed2_end > p->rest_end ? 1 + nc : 0;
+    return 3 + (p->rest_qg > 0 ? 1 : 0) + seed2 + 2 * nc;
+}
 
 // One DTW phase: the classes (largest first) round robin over the side streams, each
 // side stream ordered after the work already on s and s after all of them.
@@ -741,7 +843,14 @@ cudaError_t enqueue_plan(BatchPlan *p, cudaStream_t s, long long spin_limit) {
     k_batch_front<<<p->grid_front, kBatchThreads, kBatchSmem, s>>>(p->d_sets, p->d_items, 0, p->front_end, p->d_ctl,
                                                                    spin_limit);
     if ((e = run_dtw_classes(p, s, 0)) != cudaSuccess) return e;
-    k_batch_mid<<<p->grid_mid, kBatchThreads, 0, s>>>(p->d_sets, p->d_items, p->front_end, p->mid_end, p->d_ctl);
+    if (p->rest_qg > 0)
+        k_batch_rest<<<p->grid_rest, kRestCpThreads, rest_cp_smem(kBatchRestTile, p->rest_qg), s>>>(
+            p->d_sets, p->d_items, p->front_end, p->rest_end, p->d_ctl, p->d_rest_lists, p->rest_qg);
+    if (p->seed2_end > p->rest_end) {  // second-round seeds from the completed bounds, and their DTW
+        k_batch_seed2<<<p->seed2_end - p->rest_end, kSeed2Threads, 0, s>>>(p->d_sets, p->d_items, p->rest_end);
+        if ((e = run_dtw_classes(p, s, 2)) != cudaSuccess) return e;
+    }
+    k_batch_mid<<<p->grid_mid, kBatchThreads, 0, s>>>(p->d_sets, p->d_items, p->seed2_end, p->mid_end, p->d_ctl);
     if ((e = run_dtw_classes(p, s, 1)) != cudaSuccess) return e;
     k_batch_refine<<<p->grid_refine, kBatchThreads, kBatchSmem, s>>>(p->d_sets, p->d_items, p->mid_end, p->n_items,
                                                                      p->d_ctl);
@@ -861,6 +970,7 @@ int tcdtw_batch_nn(const tcdtw_dataset *sets, int32_t nsets, const tcdtw_opts *o
             stats->pruned_ti += ctl.counters[6];
             stats->refined += ctl.counters[7];
             stats->refined64 += ctl.counters[8];
+            stats->mv_terms += plan->dense_terms + ctl.counters[9];
         }
         for (int k : mk) pairs += (uint64_t)sets[k].M * (uint64_t)sets[k].N;
     }
@@ -878,6 +988,7 @@ int tcdtw_batch_nn(const tcdtw_dataset *sets, int32_t nsets, const tcdtw_opts *o
             stats->pruned_mv += st.pruned_mv; stats->pruned_pc += st.pruned_pc; stats->pruned_ti += st.pruned_ti;
             stats->dtw_started += st.dtw_started; stats->dtw_abandoned += st.dtw_abandoned;
             stats->cells += st.cells; stats->refined += st.refined; stats->refined64 += st.refined64;
+            stats->mv_terms += st.mv_terms;
         }
         pairs += (uint64_t)d.M * (uint64_t)d.N;
     }

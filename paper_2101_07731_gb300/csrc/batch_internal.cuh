@@ -20,7 +20,9 @@ constexpr long long kSpinLimit = 4000000;  // ~1 s of 256 ns sleeps
 constexpr size_t kBatchSmem = 48 * 1024;   // LB_MV double buffers / box scratch / FP64 row slots
 
 // Per-set counters (ints, zeroed before every run).
-enum : int { kCntPrep = 0, kCntMv, kCntList, kCntSeedCursor, kCntSurvCursor, kCntPerSet };
+enum : int { kCntPrep = 0, kCntMv, kCntList, kCntSeedCursor, kCntSurvCursor, kCntSeed2Cursor, kCntPerSet };
+// seed_dtw of a second-round seed whose DTW is still to run
+constexpr float kSeedPending = -1.f;
 
 struct BatchSet {
     const float *cand, *q;
@@ -30,12 +32,15 @@ struct BatchSet {
     int L, D, W, K, M;
     int G, R, dcase, Rref, S;  // DTW lanes per pair, rows per lane and tile DM; FP64 rows per lane;
                                // seeds per query
+    int S2;                    // second-round seeds per query (abandoning LB_MV)
     int use_pc, use_ti, Lq, w, P, Gpc, np2, vec4, check_finite;
     float e_pc, e_ti, rho, rho_ref;
     double kappa;
     int64_t ldE;
     int n_qtiles, n_ctiles;
+    int samp, sstride;                   // LB_MV sample of the abandoning form (samp 0: whole rows)
     float *U, *Lo, *dq_lo, *dq_hi, *boxes;
+    float *Up, *Lp;                      // [M][ldE] envelope, one query per row (samp > 0)
     int32_t *box_counts;
     float *lbm;                          // [M][N] LB_MV
     uint32_t *surv;                      // [M][N] survivor candidate ids, per query
@@ -49,24 +54,25 @@ struct BatchSet {
     int *cnt;                            // kCntPerSet counters
 };
 
-enum : int { kItemPrep = 0, kItemMv, kItemSeed, kItemMid, kItemRefine, kItemStall };
+enum : int { kItemPrep = 0, kItemMv, kItemSeed, kItemMid, kItemRefine, kItemStall, kItemRest, kItemSeed2 };
 constexpr int kRefinePerItem = 4;  // queries per refine item (one per warp)
 struct BatchItem {
     int kind, set, a, b;
 };
 
 struct BatchCtl {
-    int next[3];  // cursors of the front, mid and refine item ranges
+    int next[4];  // cursors of the front, mid, refine and LB_MV completion item ranges
     int abort;
     int never;    // stays 0: the self-test waits on it
     DevStatus status;
-    unsigned long long counters[9];  // started, abandoned, cells, pruned at DTW, pruned MV, PC, TI, refined,
-                                     // refined in FP64
+    unsigned long long counters[10];  // started, abandoned, cells, pruned at DTW, pruned MV, PC, TI, refined,
+                                      // refined in FP64, LB_MV terms of the completion pass
 };
 
 
 // ------------------------------------------------------------------ DTW launches
-// Phase 0: the seed entries i < M*8 (query i/8, slot i%8); phase 1: the work list.
+// Phase 0: the seed entries i < M*8 (query i/8, slot i%8); phase 1: the work list;
+// phase 2: the second-round seed entries (slots whose seed_dtw is kSeedPending).
 // A warp takes 32/G consecutive entries of one set (one per lane group) and runs
 // them in lockstep, as the single-set kernel does; the sets follow each other in
 // the order given, each with its own cursor, so warps move on as a set runs dry.
@@ -79,8 +85,8 @@ __device__ __forceinline__ void dtw_set(const BatchSet &S, int phase, float *sta
     const int L = S.L, D = S.D, W = S.W;
     const int64_t N = S.N;
     const int nv = (L + R - 1) / R;
-    const int n_entries = phase == 0 ? S.M * kSeedSlots : S.cnt[kCntList];
-    int *cursor = S.cnt + (phase == 0 ? kCntSeedCursor : kCntSurvCursor);
+    const int n_entries = phase == 1 ? S.cnt[kCntList] : S.M * kSeedSlots;
+    int *cursor = S.cnt + (phase == 0 ? kCntSeedCursor : phase == 1 ? kCntSurvCursor : kCntSeed2Cursor);
     unsigned long long started = 0, aband = 0, ncells = 0, pruned = 0;
     for (;;) {
         int base = 0;
@@ -94,11 +100,11 @@ __device__ __forceinline__ void dtw_set(const BatchSet &S, int phase, float *sta
         float lbe = 0.f;
         float *out = nullptr;
         if (live) {
-            if (phase == 0) {
+            if (phase != 1) {
                 q = e / kSeedSlots;
                 cn = S.seeds[e];
                 out = S.seed_dtw + e;
-                live = cn != 0xffffffffu;
+                live = cn != 0xffffffffu && (phase == 0 || *out == kSeedPending);
             } else {
                 const uint32_t pid = S.list[e];
                 q = (int)(pid / (uint64_t)N);

@@ -29,7 +29,8 @@ namespace tc {
 // in one packed f32x2 instruction each.  Sums are two-level (32 elements of a chunk,
 // then the chunk sums), so a round-down chain is at most 32 + E/32 long.
 template <int QB>
-__global__ void __launch_bounds__(128) k_lb_mv(const float *__restrict__ cand, int64_t N, int E, int64_t ldC, int vec4,
+__global__ void __launch_bounds__(128) k_lb_mv(const float *__restrict__ cand, int64_t N, int nchunks, int cstride,
+                                               int Erow, int64_t ldC, int vec4,
                                                const float *__restrict__ UI, const float *__restrict__ LI,
                                                int64_t ldE, int Mb, float *__restrict__ lb, int64_t ldLb,
                                                int n_ctiles, int n_qtiles) {
@@ -39,12 +40,14 @@ __global__ void __launch_bounds__(128) k_lb_mv(const float *__restrict__ cand, i
     const int ntiles = n_ctiles * n_qtiles;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int ct = tile / n_qtiles, qt = tile % n_qtiles;
-        lb_mv_tile<QB>(cand, N, E, ldC, vec4, UI, LI, ldE, Mb, lb, ldLb, (int64_t)ct * kMvRows, qt * QB, sc, su, sl);
+        lb_mv_tile<QB>(cand, N, nchunks, cstride, Erow, ldC, vec4, UI, LI, ldE, Mb, lb, ldLb, (int64_t)ct * kMvRows,
+                       qt * QB, sc, su, sl);
     }
 }
 
 bool lb_mv_vec4(const float *cand, int E) { return (E % 4) == 0 && (((uintptr_t)cand) & 15) == 0; }
 static int64_t row_stride(const LbMvArgs &a) { return a.ldC > 0 ? a.ldC : a.E; }
+static int row_elems(const LbMvArgs &a) { return a.Erow > 0 ? a.Erow : a.E; }
 
 cudaError_t launch_lb_mv(const LbMvArgs &a, cudaStream_t s) {
     if (a.N <= 0 || a.Mb <= 0) return cudaSuccess;
@@ -53,7 +56,9 @@ cudaError_t launch_lb_mv(const LbMvArgs &a, cudaStream_t s) {
         if (e != cudaErrorNotSupported) return e;
     }
     const int64_t ldC = row_stride(a);
-    const int vec4 = lb_mv_vec4(a.cand, a.E) && (ldC % 4) == 0;
+    const int Erow = row_elems(a), cstride = a.cstride > 0 ? a.cstride : 1;
+    const int nchunks = (a.E + kMvChunk - 1) / kMvChunk;
+    const int vec4 = lb_mv_vec4(a.cand, Erow) && (ldC % 4) == 0;
     const int n_ctiles = (int)((a.N + kMvRows - 1) / kMvRows);
     int QB = 32;
     if (a.Mb <= 8) QB = 8;
@@ -66,7 +71,8 @@ cudaError_t launch_lb_mv(const LbMvArgs &a, cudaStream_t s) {
         int64_t tiles = (int64_t)n_ctiles * n_qtiles;                                                           \
         int64_t grid = (int64_t)(occ > 0 ? occ : 1) * a.sms;                                                    \
         if (grid > tiles) grid = tiles;                                                                         \
-        k_lb_mv<QBV><<<(int)grid, 128, 0, s>>>(a.cand, a.N, a.E, ldC, vec4, a.U, a.Lo, a.ldE, a.Mb, a.lb, a.ldLb, \
+        k_lb_mv<QBV><<<(int)grid, 128, 0, s>>>(a.cand, a.N, nchunks, cstride, Erow, ldC, vec4, a.U, a.Lo, a.ldE, \
+                                               a.Mb, a.lb, a.ldLb,                                              \
                                                n_ctiles, n_qtiles);                                             \
         note_launch();                                                                                          \
     } while (0)

@@ -60,9 +60,10 @@ __device__ __forceinline__ f2 mv_step(f2 c2, float u0, float u1, float l0, float
     return fma2_rd(m2, m2, part);
 }
 
-// Candidate rows are ldC floats apart; the stream reads their first E elements.
+// Candidate rows are ldC floats apart and hold Erow valid elements; e0 is the row
+// element where the chunk starts.
 template <int QB>
-__device__ __forceinline__ void mv_issue(const float *__restrict__ cand, int64_t N, int E, int64_t ldC, bool vec4,
+__device__ __forceinline__ void mv_issue(const float *__restrict__ cand, int64_t N, int Erow, int64_t ldC, bool vec4,
                                          const float *UI, const float *LI, int64_t ldE, int n_qp, int64_t n0, int q0,
                                          int e0, float *sc, float *su, float *sl) {
     const int tid = threadIdx.x;
@@ -73,7 +74,7 @@ __device__ __forceinline__ void mv_issue(const float *__restrict__ cand, int64_t
             const int row = idx >> 3, seg = idx & 7;
             const int64_t n = n0 + row;
             const int e = e0 + seg * 4;
-            const bool ok = n < N && e < E;
+            const bool ok = n < N && e < Erow;
             const float *src = ok ? cand + (size_t)n * ldC + e : cand;
             cp_async16(sc + row * kMvChunk + ((seg ^ (row & 7)) << 2), src, ok ? 16 : 0);
         }
@@ -83,7 +84,7 @@ __device__ __forceinline__ void mv_issue(const float *__restrict__ cand, int64_t
             const int row = idx >> 5, el = idx & 31;
             const int64_t n = n0 + row;
             const int e = e0 + el;
-            const bool ok = n < N && e < E;
+            const bool ok = n < N && e < Erow;
             const float *src = ok ? cand + (size_t)n * ldC + e : cand;
             const int seg = el >> 2;
             cp_async4(sc + row * kMvChunk + ((seg ^ (row & 7)) << 2) + (el & 3), src, ok ? 4 : 0);
@@ -102,25 +103,27 @@ __device__ __forceinline__ void mv_issue(const float *__restrict__ cand, int64_t
 
 // One LB_MV tile: candidates [n0, n0+128) x queries [q0, q0+QB) of the stream, using
 // the caller's shared buffers sc[2][128*32], su[2][QB*32], sl[2][QB*32] (16-byte aligned).
+// The tile sums nchunks chunks of 32 elements, chunk k starting at row element
+// k * cstride * 32 (cstride 1: the first nchunks chunks; rows hold Erow elements).
 template <int QB>
-__device__ __forceinline__ void lb_mv_tile(const float *__restrict__ cand, int64_t N, int E, int64_t ldC, bool vec4,
+__device__ __forceinline__ void lb_mv_tile(const float *__restrict__ cand, int64_t N, int nchunks, int cstride,
+                                           int Erow, int64_t ldC, bool vec4,
                                            const float *__restrict__ UI, const float *__restrict__ LI, int64_t ldE,
                                            int Mb, float *__restrict__ lb, int64_t ldLb, int64_t n0, int q0,
                                            float (*sc)[kMvRows * kMvChunk], float (*su)[QB * kMvChunk],
                                            float (*sl)[QB * kMvChunk]) {
     const int tid = threadIdx.x;
-    const int nchunks = (E + kMvChunk - 1) / kMvChunk;
     const int n_qp = (Mb + 1) / 2;
     f2 acc[QB / 2];
 #pragma unroll
     for (int k = 0; k < QB / 2; ++k) acc[k] = 0ull;
-    mv_issue<QB>(cand, N, E, ldC, vec4, UI, LI, ldE, n_qp, n0, q0, 0, sc[0], su[0], sl[0]);
+    mv_issue<QB>(cand, N, Erow, ldC, vec4, UI, LI, ldE, n_qp, n0, q0, 0, sc[0], su[0], sl[0]);
     cp_async_commit();
     for (int c = 0; c < nchunks; ++c) {
         const int buf = c & 1;
         if (c + 1 < nchunks) {
-            mv_issue<QB>(cand, N, E, ldC, vec4, UI, LI, ldE, n_qp, n0, q0, (c + 1) * kMvChunk, sc[buf ^ 1], su[buf ^ 1],
-                         sl[buf ^ 1]);
+            mv_issue<QB>(cand, N, Erow, ldC, vec4, UI, LI, ldE, n_qp, n0, q0, (c + 1) * cstride * kMvChunk,
+                         sc[buf ^ 1], su[buf ^ 1], sl[buf ^ 1]);
             cp_async_commit();
             cp_async_wait<1>();
         } else {

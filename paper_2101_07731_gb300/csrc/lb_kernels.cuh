@@ -27,10 +27,13 @@ cudaError_t launch_pc_boxes(const float *q, int64_t M, int L, int D, int W, int 
 
 // lb.cu -- LB_MV over all (query, candidate) pairs of a block
 struct LbMvArgs {
-    const float *cand;  // [N][ldC]; the stream covers elements [0, E) of every row
+    const float *cand;  // [N][ldC]: rows of Erow valid elements
     int64_t N;
-    int E;
+    int E;              // elements the stream sums per pair: ceil(E/32) chunks of 32, chunk k
+                        // starting at row element k * cstride * 32
     int64_t ldC = 0;    // row stride of cand in floats (0: E)
+    int Erow = 0;       // valid elements per row (0: E)
+    int cstride = 1;    // row chunks per stream chunk (1: the first E elements)
     const float *U;     // query-pair interleaved envelope [(Mb+1)/2][ldE][2], +inf beyond E
     const float *Lo;    // likewise, -inf beyond E
     int64_t ldE;        // multiple of 32
@@ -62,19 +65,22 @@ cudaError_t launch_lb_mv_tma(const LbMvArgs &a, cudaStream_t s);
 bool lb_mv_vec4(const float *cand, int E);
 
 // lb_rest.cu -- completion of LB_MV, with early abandoning, for the pairs whose sum over
-// the elements [0, E0) (already in lb) is at most their query's threshold; the others
-// keep their prefix sum.  Completed and abandoned values are written in place.
+// a sample of their elements (already in lb) is at most their query's threshold; the
+// others keep that partial sum.  The sample is samp chunks of 32 elements spread over
+// the row, chunk k * sstride for k < samp.  Completed and abandoned values are written
+// in place.
 constexpr int kRestTC = 224;   // candidates per tile, at most
 constexpr int kRestQG = 256;   // queries staged per pass, at most
 struct LbMvRestArgs {
     const float *cand;      // [N][ldC], elements [0, E) used
     int64_t N;
-    int E, E0;              // E0: prefix already summed, a multiple of 32, < E
+    int E;
+    int samp, sstride;      // the sampled chunks, already summed (samp >= 1, chunks full)
     int64_t ldC;
     const float *Up, *Lp;   // envelope, one query per row: [Mb][ldP], +inf / -inf beyond E
     int64_t ldP;            // a multiple of 32, >= E
     int Mb;
-    float *lb;              // [Mb][ldLb]: prefix sums in, bounds out
+    float *lb;              // [Mb][ldLb]: sample sums in, bounds out
     int64_t ldLb;
     const float *thresh;    // [Mb] thresholds, or null: prune_threshold(bsf[m], rho)
     const unsigned long long *bsf;
@@ -88,15 +94,24 @@ struct LbMvRestArgs {
 int lb_mv_rest_tile(int64_t N, int sms);
 int64_t lb_mv_rest_list_entries(int64_t N, int Mb, int sms);
 cudaError_t launch_lb_mv_rest(const LbMvRestArgs &a, cudaStream_t s);
-// Prefix length of the abandoning LB_MV for rows of E elements: 0 (no abandoning) when
-// the rows are too short for it to pay.
-inline int lb_mv_prefix(int E) {
+// Sample of the abandoning LB_MV for rows of E elements: the number of sampled chunks
+// (0: no abandoning, the rows are too short for it to pay) and their stride in chunks.
+// Chunks 0, stride, 2*stride, ... lie before the last chunk, so each is whole.  The
+// sample spreads over the whole series, so its sums rank candidates much as the full
+// bound does (a prefix would rank them by their first few points only).
+inline int lb_mv_sample(int E, int *stride) {
     const int nchunks = (E + 31) / 32;
+    *stride = 1;
     if (nchunks < 4) return 0;
     int c = nchunks / 16;
     if (c < 1) c = 1;
     if (c > 8) c = 8;
-    return 32 * c;
+    *stride = nchunks / c;
+    return c;
+}
+// Whether row chunk c belongs to that sample.
+__host__ __device__ inline bool lb_mv_sampled(int c, int samp, int sstride) {
+    return c % sstride == 0 && c / sstride < samp;
 }
 
 // compaction of rows of a bound matrix against per-row thresholds

@@ -1,16 +1,17 @@
 // lb_rest.cu -- LB_MV with early abandoning (Section 7.1: abandoning applies to the
 // lower-bound computations as well as to DTW).
 //
-// The dense stream (lb.cu) first sums the elements [0, E0) of every (query, candidate)
-// pair.  A pair whose prefix sum already exceeds its query's threshold is abandoned
-// there: every LB_MV term is >= 0, so the prefix sum is a lower bound of LB_MV, hence
-// of DTW, and it already exceeds the threshold, which is all the search needs of it.
-// The pairs left at or under the threshold (on nearest-neighbour workloads usually a
-// small share) are completed here, over the elements [E0, E).
+// The dense stream (lb.cu) first sums a sample of the elements of every (query,
+// candidate) pair: samp chunks of 32 spread evenly over the row.  A pair whose sample
+// sum already exceeds its query's threshold is abandoned there: every LB_MV term is
+// >= 0, so a sum over any subset of the terms is a lower bound of LB_MV, hence of DTW,
+// and it already exceeds the threshold, which is all the search needs of it.  The pairs
+// left at or under the threshold (on nearest-neighbour workloads usually a small share)
+// are completed here, over the chunks the sample did not cover.
 //
 // CTA = tn candidates (tn <= kRestTC) x up to qg <= kRestQG queries.  The CTA lists the
 // live (query, candidate) pairs of its tile (in a per-CTA global scratch region), then
-// streams the elements [E0, E) of its candidates and of its queries' envelopes through
+// streams the remaining chunks of its candidates and of its queries' envelopes through
 // shared memory in chunks of 32, two stages deep, every 128-byte row stored with its
 // 16-byte segments XOR-swizzled by row & 7 (threads reading different rows then mostly
 // hit different banks).  Each consumer thread advances up to kRestEpt listed pairs by
@@ -35,134 +36,12 @@
 #include "common.cuh"
 #include "lb_device.cuh"
 #include "lb_kernels.cuh"
+#include "lb_rest.cuh"
 #include "tma.cuh"
 
 namespace tc {
 
 namespace {
-
-constexpr int kRestEpt = 4;      // listed pairs per consumer thread per round
-constexpr int kRestCheck = 16;   // chunks between abandoning checks
-// bulk-tensor form: 15 consumer warps + the producer warp, four warps per SM
-// sub-partition (a 17th warp would cap every thread at 96 registers)
-constexpr int kRestCons = 480;
-constexpr int kRestTmaThreads = kRestCons + 32;
-constexpr int kRestCpThreads = 512;  // cp.async form: every thread consumes
-
-// Two consecutive elements of one pair: c2 = {c_e, c_e+1} against {U_e, U_e+1},
-// {Lo_e, Lo_e+1}; the squared excess of each is added (rounded down) into its half of
-// part.
-__device__ __forceinline__ f2 rest_step(f2 c2, f2 u2, f2 l2, f2 part) {
-    float a0, a1, b0, b1;
-    upk(sub2_rd(c2, u2), a0, a1);
-    upk(sub2_rd(l2, c2), b0, b1);
-    const float m0 = max3f(a0, b0, 0.f), m1 = max3f(a1, b1, 0.f);
-    const f2 m2 = pk(m0, m1);
-    return fma2_rd(m2, m2, part);
-}
-
-// One chunk of one pair: candidate row cr, envelope rows ur / lr (32 floats each,
-// segments swizzled by cs / es); returns the chunk's sum, rounded down.
-__device__ __forceinline__ float rest_chunk(const float *cr, const float *ur, const float *lr, int cs, int es) {
-    f2 p = 0ull;
-#pragma unroll
-    for (int sg = 0; sg < 8; ++sg) {
-        const float4 cv = *reinterpret_cast<const float4 *>(cr + ((sg ^ cs) << 2));
-        const float4 uv = *reinterpret_cast<const float4 *>(ur + ((sg ^ es) << 2));
-        const float4 lv = *reinterpret_cast<const float4 *>(lr + ((sg ^ es) << 2));
-        p = rest_step(pk(cv.x, cv.y), pk(uv.x, uv.y), pk(lv.x, lv.y), p);
-        p = rest_step(pk(cv.z, cv.w), pk(uv.z, uv.w), pk(lv.z, lv.w), p);
-    }
-    float p0, p1;
-    upk(p, p0, p1);
-    return __fadd_rd(p0, p1);
-}
-
-// The live pairs (bound at or under the query's threshold) of candidates [n0, n0+tn)
-// x queries [q0, q0+nq), appended to list as (query - q0) << 16 | (candidate - n0);
-// *cnt counts them.  Every thread of the CTA calls it (blockDim.x a multiple of 32:
-// whole warps take part in every ballot, nq * tn being a multiple of 32).
-__device__ __forceinline__ void rest_list(const LbMvRestArgs &a, int64_t n0, int tn, int q0, int nq,
-                                          const float *thr, int *cnt, uint32_t *list) {
-    const int lane = threadIdx.x & 31;
-    for (int base = 0; base < nq * tn; base += blockDim.x) {
-        const int idx = base + threadIdx.x;
-        const int ql = idx / tn, nl = idx - ql * tn;
-        bool live = false;
-        if (ql < nq && n0 + nl < a.N) {
-            const float v = a.lb[(size_t)(q0 + ql) * a.ldLb + n0 + nl];
-            live = v < TC_INF && v <= thr[ql];
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, live);
-        int pos = 0;
-        if (lane == 0 && bal) pos = atomicAdd(cnt, __popc(bal));
-        pos = __shfl_sync(0xffffffffu, pos, 0);
-        if (live) list[pos + __popc(bal & ((1u << lane) - 1u))] = ((uint32_t)ql << 16) | (uint32_t)nl;
-    }
-}
-
-__device__ __forceinline__ float rest_threshold(const LbMvRestArgs &a, int q) {
-    return a.thresh ? a.thresh[q] : prune_threshold(ld_volatile_u64(a.bsf + q), a.rho);
-}
-
-// The round's listed pairs of consumer thread t of nc: entries r0 + k * nc + t.
-struct RestPairs {
-    int q[kRestEpt], n[kRestEpt];
-    float acc[kRestEpt], th[kRestEpt];
-    bool act[kRestEpt];
-};
-
-__device__ __forceinline__ void rest_load(RestPairs &p, const LbMvRestArgs &a, const uint32_t *list, int r0, int t,
-                                          int nc, int cnt, int64_t n0, int q0, const float *thr) {
-#pragma unroll
-    for (int k = 0; k < kRestEpt; ++k) {
-        const int i = r0 + k * nc + t;
-        p.act[k] = i < cnt;
-        const uint32_t en = p.act[k] ? __ldcg(list + i) : 0u;
-        p.q[k] = (int)(en >> 16);
-        p.n[k] = (int)(en & 0xffffu);
-        p.acc[k] = p.act[k] ? a.lb[(size_t)(q0 + p.q[k]) * a.ldLb + n0 + p.n[k]] : 0.f;
-        p.th[k] = thr[p.q[k]];
-    }
-}
-
-// Abandons the pairs whose running sum passed their threshold (writing the partial
-// sum); true while any pair of this thread is still active.
-__device__ __forceinline__ bool rest_check(RestPairs &p, const LbMvRestArgs &a, int64_t n0, int q0) {
-    bool any = false;
-#pragma unroll
-    for (int k = 0; k < kRestEpt; ++k) {
-        if (p.act[k] && p.acc[k] > p.th[k]) {
-            a.lb[(size_t)(q0 + p.q[k]) * a.ldLb + n0 + p.n[k]] = p.acc[k];
-            p.act[k] = false;
-        }
-        any |= p.act[k];
-    }
-    return any;
-}
-
-__device__ __forceinline__ void rest_store(const RestPairs &p, const LbMvRestArgs &a, int64_t n0, int q0) {
-#pragma unroll
-    for (int k = 0; k < kRestEpt; ++k)
-        if (p.act[k]) a.lb[(size_t)(q0 + p.q[k]) * a.ldLb + n0 + p.n[k]] = p.acc[k];
-}
-
-// OR of v over the consumer threads (named barrier 1; the producer warp never joins).
-__device__ __forceinline__ bool consumers_any(bool v) {
-    uint32_t r;
-    asm volatile(
-        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
-        : "=r"(r)
-        : "r"((uint32_t)v), "r"(kRestCons)
-        : "memory");
-    return r != 0;
-}
-
-__device__ __forceinline__ void rest_terms_flush(const LbMvRestArgs &a, unsigned long long terms) {
-    if (!a.terms) return;
-    for (int o = 16; o > 0; o >>= 1) terms += __shfl_xor_sync(0xffffffffu, terms, o);
-    if ((threadIdx.x & 31) == 0 && terms) atomicAdd(a.terms, terms);
-}
 
 // ------------------------------------------------------------------ bulk-tensor form
 // Shared memory from a 1024-byte aligned base: two stages of [cand tn x 128 B | U qgp x
@@ -193,7 +72,7 @@ __global__ void __launch_bounds__(kRestTmaThreads, 1)
     uint32_t *list = a.list + (size_t)blockIdx.x * tn * qg;
     const int tid = threadIdx.x, lane = tid & 31;
     const bool producer = tid >= kRestCons;
-    const int nchunks = (a.E + kMvChunk - 1) / kMvChunk, c0 = a.E0 / kMvChunk;
+    const int nchunks = (a.E + kMvChunk - 1) / kMvChunk;
     const uint32_t tx = (uint32_t)(tn + 2 * qg) * 128u;  // bytes the three boxes deliver
     if (tid == 0) {
         for (int s = 0; s < 2; ++s) {
@@ -229,7 +108,8 @@ __global__ void __launch_bounds__(kRestTmaThreads, 1)
                 if (producer) {
                     if (lane == 0) {
                         int issued = 0;
-                        for (int c = c0; c < nchunks && !flags[0] && !flags[1]; ++c) {
+                        for (int c = rest_next(a, 0, nchunks); c < nchunks && !flags[0] && !flags[1];
+                             c = rest_next(a, c + 1, nchunks)) {
                             const uint32_t s = kp & 1u;
                             // the stage's previous chunk must have been released (the wait
                             // also gives up when the consumers stop the stream)
@@ -253,7 +133,8 @@ __global__ void __launch_bounds__(kRestTmaThreads, 1)
                 } else {
                     RestPairs p;
                     rest_load(p, a, list, r0, tid, kRestCons, cnt, n0, q0, thr);
-                    for (int c = c0; c < nchunks; ++c) {
+                    int step = 0;
+                    for (int c = rest_next(a, 0, nchunks); c < nchunks; c = rest_next(a, c + 1, nchunks), ++step) {
                         const uint32_t s = kc & 1u;
                         if (!mbar_wait(full0 + 8 * s, (kc >> 1) & 1u, flags + 1, wait_ns) && !flags[1]) {
                             set_error(a.status, TCDTW_ERR_TIMEOUT, 51);
@@ -274,7 +155,7 @@ __global__ void __launch_bounds__(kRestTmaThreads, 1)
                         }
                         __syncwarp();
                         if (lane == 0) mbar_arrive(empty0 + 8 * s);
-                        if ((c - c0) % kRestCheck == kRestCheck - 1) {
+                        if (step % kRestCheck == kRestCheck - 1) {
                             const bool any = rest_check(p, a, n0, q0);
                             if (!consumers_any(any && !flags[1])) {
                                 if (tid == 0) flags[0] = 1;  // stop the producer
@@ -310,105 +191,14 @@ __global__ void __launch_bounds__(kRestTmaThreads, 1)
 }
 
 // ------------------------------------------------------------------ cp.async form
-
-// Copies chunk [e0, e0+32) of the tile's candidates and queries into one buffer:
-// candidate rows [tn][32], query rows [qg][64] (U then Lo), segments swizzled by row.
-__device__ __forceinline__ void rest_issue(const LbMvRestArgs &a, int64_t n0, int tn, int q0, int nq, int e0,
-                                           bool vec4, float *sc, float *se) {
-    const int tid = threadIdx.x;
-    if (vec4) {
-        for (int idx = tid; idx < tn * 8; idx += kRestCpThreads) {
-            const int row = idx >> 3, seg = idx & 7;
-            const int64_t n = n0 + row;
-            const int e = e0 + seg * 4;
-            const bool ok = n < a.N && e < a.E;
-            const float *src = ok ? a.cand + (size_t)n * a.ldC + e : a.cand;
-            cp_async16(sc + row * 32 + ((seg ^ (row & 7)) << 2), src, ok ? 16 : 0);
-        }
-    } else {
-        for (int idx = tid; idx < tn * 32; idx += kRestCpThreads) {
-            const int row = idx >> 5, el = idx & 31;
-            const int64_t n = n0 + row;
-            const int e = e0 + el;
-            const bool ok = n < a.N && e < a.E;
-            const float *src = ok ? a.cand + (size_t)n * a.ldC + e : a.cand;
-            cp_async4(sc + row * 32 + (((el >> 2) ^ (row & 7)) << 2) + (el & 3), src, ok ? 4 : 0);
-        }
-    }
-    // envelope rows are padded with +inf / -inf up to ldP (a multiple of 32), so a
-    // chunk that starts below E lies inside the row, and its elements >= E add 0
-    for (int idx = tid; idx < nq * 16; idx += kRestCpThreads) {
-        const int row = idx >> 4, h = (idx >> 3) & 1, seg = idx & 7;
-        const float *src = (h ? a.Lp : a.Up) + (size_t)(q0 + row) * a.ldP + e0 + seg * 4;
-        cp_async16(se + row * 64 + h * 32 + ((seg ^ (row & 7)) << 2), src, 16);
-    }
-}
-
-constexpr size_t rest_cp_smem(int tn, int qg) {
-    return ((size_t)2 * tn * 32 + (size_t)2 * qg * 64 + qg + 4) * sizeof(float);
-}
-static_assert(rest_cp_smem(kRestTC, kRestQG) <= 227 * 1024, "one CTA of the completion stream per SM");
-
 __global__ void __launch_bounds__(kRestCpThreads, 1) k_lb_mv_rest_cp(const LbMvRestArgs a, int tn, int qg, int vec4) {
     extern __shared__ __align__(16) float rs[];
-    // buffer b: candidates at rs + b * tn * 32, envelopes at env0 + b * qg * 64
-    float *const env0 = rs + 2 * tn * 32;
-    float *thr = env0 + 2 * qg * 64;
-    int *s_cnt = reinterpret_cast<int *>(thr + qg);
     uint32_t *list = a.list + (size_t)blockIdx.x * tn * qg;
-    const int tid = threadIdx.x;
-    const int nchunks = (a.E + kMvChunk - 1) / kMvChunk, c0 = a.E0 / kMvChunk;
     const int64_t n_tiles = (a.N + tn - 1) / tn;
     unsigned long long terms = 0;
-    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const int64_t n0 = tile * tn;
-        for (int q0 = 0; q0 < a.Mb; q0 += qg) {
-            const int nq = min(qg, a.Mb - q0);
-            __syncthreads();  // the previous pass is done with the thresholds and the list
-            if (tid == 0) *s_cnt = 0;
-            for (int k = tid; k < nq; k += blockDim.x) thr[k] = rest_threshold(a, q0 + k);
-            __syncthreads();
-            rest_list(a, n0, tn, q0, nq, thr, s_cnt, list);
-            __syncthreads();  // the list (global, this CTA's region) and its count
-            const int cnt = *s_cnt;
-            for (int r0 = 0; r0 < cnt; r0 += kRestCpThreads * kRestEpt) {
-                RestPairs p;
-                rest_load(p, a, list, r0, tid, kRestCpThreads, cnt, n0, q0, thr);
-                rest_issue(a, n0, tn, q0, nq, c0 * kMvChunk, vec4, rs, env0);
-                cp_async_commit();
-                for (int c = c0; c < nchunks; ++c) {
-                    const int buf = (c - c0) & 1;
-                    if (c + 1 < nchunks) {
-                        rest_issue(a, n0, tn, q0, nq, (c + 1) * kMvChunk, vec4, rs + (buf ^ 1) * tn * 32,
-                                   env0 + (buf ^ 1) * qg * 64);
-                        cp_async_commit();
-                        cp_async_wait<1>();
-                    } else {
-                        cp_async_wait<0>();
-                    }
-                    __syncthreads();
-                    const float *cb = rs + buf * tn * 32, *eb = env0 + buf * qg * 64;
-#pragma unroll
-                    for (int k = 0; k < kRestEpt; ++k) {
-                        if (!p.act[k]) continue;
-                        const float *ur = eb + p.q[k] * 64;
-                        p.acc[k] = __fadd_rd(p.acc[k], rest_chunk(cb + p.n[k] * 32, ur, ur + 32, p.n[k] & 7,
-                                                                  p.q[k] & 7));
-                        terms += (unsigned)min(kMvChunk, a.E - c * kMvChunk);
-                    }
-                    if ((c - c0) % kRestCheck == kRestCheck - 1) {
-                        // (also the barrier before the other buffer is refilled)
-                        if (!__syncthreads_or(rest_check(p, a, n0, q0))) break;
-                    } else {
-                        __syncthreads();
-                    }
-                }
-                rest_store(p, a, n0, q0);
-                cp_async_wait<0>();  // a stream left early may still have a chunk in flight
-                __syncthreads();
-            }
-        }
-    }
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x)
+        for (int q0 = 0; q0 < a.Mb; q0 += qg)
+            rest_pass_cp(a, tile * tn, tn, q0, min(qg, a.Mb - q0), qg, vec4, rs, list, terms);
     rest_terms_flush(a, terms);
 }
 
@@ -436,8 +226,9 @@ int64_t lb_mv_rest_list_entries(int64_t N, int Mb, int sms) {
 }
 
 cudaError_t launch_lb_mv_rest(const LbMvRestArgs &a, cudaStream_t s) {
-    if (a.N <= 0 || a.Mb <= 0 || a.E0 >= a.E) return cudaSuccess;
-    if (a.E0 % kMvChunk != 0 || a.ldP % kMvChunk != 0 || a.ldP < a.E || (((uintptr_t)a.Up) & 15) != 0 ||
+    if (a.N <= 0 || a.Mb <= 0) return cudaSuccess;
+    if (a.samp < 1 || a.sstride < 1 || (int64_t)(a.samp - 1) * a.sstride * kMvChunk + kMvChunk > a.E ||
+        a.ldP % kMvChunk != 0 || a.ldP < a.E || (((uintptr_t)a.Up) & 15) != 0 ||
         (((uintptr_t)a.Lp) & 15) != 0)
         return cudaErrorInvalidValue;
     const int sms = a.sms > 0 ? a.sms : 1;

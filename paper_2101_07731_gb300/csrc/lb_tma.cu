@@ -82,7 +82,7 @@ __device__ __forceinline__ int64_t sk_owner(int64_t x, int64_t total, int64_t gr
 template <int QB, int NG, int NS>
 __global__ void __launch_bounds__(128 * NG + 32)
     k_lb_mv_tma(const __grid_constant__ CUtensorMap cmap, const __grid_constant__ CUtensorMap umap,
-                const __grid_constant__ CUtensorMap lmap, int64_t N, int E, int Mb, float *__restrict__ lb,
+                const __grid_constant__ CUtensorMap lmap, int64_t N, int E, int cstride, int Mb, float *__restrict__ lb,
                 int64_t ldLb, int n_ctiles, int n_qtiles, int tile_aligned, float *__restrict__ ws,
                 int *__restrict__ tile_cnt, DevStatus *status, uint64_t wait_ns, int stall) {
     using Lay = MvTmaLayout<QB, NG, NS>;
@@ -131,10 +131,11 @@ __global__ void __launch_bounds__(128 * NG + 32)
             const int ct = (int)(tile / n_qtiles), qt = (int)(tile - (int64_t)ct * n_qtiles);
             const uint32_t full = full0 + 8 * s;
             mbar_expect_tx(full, Lay::kStageTx);
-            tma_load_2d(base + Lay::kCandOff + s * kCandBytes, &cmap, c * kMvChunk, ct * kMvRows, full);
+            // stream chunk c is row chunk c * cstride
+            tma_load_2d(base + Lay::kCandOff + s * kCandBytes, &cmap, c * cstride * kMvChunk, ct * kMvRows, full);
             const uint32_t env = base + Lay::kEnvOff + s * 2 * Lay::kEnvBytes;
-            tma_load_2d(env, &umap, c * 2 * kMvChunk, qt * (QB / 2), full);
-            tma_load_2d(env + Lay::kEnvBytes, &lmap, c * 2 * kMvChunk, qt * (QB / 2), full);
+            tma_load_2d(env, &umap, c * cstride * 2 * kMvChunk, qt * (QB / 2), full);
+            tma_load_2d(env + Lay::kEnvBytes, &lmap, c * cstride * 2 * kMvChunk, qt * (QB / 2), full);
         }
         // the last copies must have landed before the CTA may exit (bounded)
         for (int j = k - NS > 0 ? k - NS : 0; j < k; ++j) mbar_wait(full0 + 8 * (j % NS), (j / NS) & 1, nullptr, wait_ns);
@@ -321,7 +322,8 @@ cudaError_t launch_variant(const LbMvArgs &a, const CUtensorMap &cm, const CUten
         const bool fine = a.ws && a.tile_cnt && tiles <= a.tile_cnt_cap && grid * 2 * QB * kMvRows <= a.ws_floats;
         if (!fine && grid > tiles) grid = tiles;
         k_lb_mv_tma<QB, NG, NS><<<(int)grid, 128 * NG + 32, Lay::kBytes, s>>>(
-            cm, um, lm, a.N, a.E, a.Mb, a.lb, a.ldLb, p.n_ctiles, p.n_qtiles, fine ? 0 : 1, a.ws, a.tile_cnt,
+            cm, um, lm, a.N, a.E, a.cstride > 0 ? a.cstride : 1, a.Mb, a.lb, a.ldLb, p.n_ctiles, p.n_qtiles,
+            fine ? 0 : 1, a.ws, a.tile_cnt,
             a.status, wait_ns, stall);
         note_launch();
         return cudaGetLastError();
@@ -359,7 +361,8 @@ bool encode_2d(CUtensorMap *m, const float *ptr, uint64_t width, uint64_t height
 
 bool lb_mv_tma_ok(const LbMvArgs &a) {
     const int64_t ldC = a.ldC > 0 ? a.ldC : a.E;
-    return a.status != nullptr && (a.E % 4) == 0 && (ldC % 4) == 0 && ldC >= a.E && (((uintptr_t)a.cand) & 15) == 0 &&
+    const int Erow = a.Erow > 0 ? a.Erow : a.E;
+    return a.status != nullptr && (Erow % 4) == 0 && (ldC % 4) == 0 && ldC >= Erow && (((uintptr_t)a.cand) & 15) == 0 &&
            (((uintptr_t)a.U) & 15) == 0 && (((uintptr_t)a.Lo) & 15) == 0 && (a.ldE % kMvChunk) == 0 &&
            a.N < ((int64_t)1 << 31) - 256 && a.Mb < (1 << 30) && encode_fn() != nullptr;
 }
@@ -381,7 +384,8 @@ cudaError_t launch_lb_mv_tma(const LbMvArgs &a, cudaStream_t s) {
     const int64_t n_qp = (a.Mb + 1) / 2;
     CUtensorMap cm, um, lm;
     const int64_t ldC = a.ldC > 0 ? a.ldC : a.E;
-    if (!encode_2d(&cm, a.cand, (uint64_t)a.E, (uint64_t)a.N, (uint64_t)ldC * 4, kMvChunk, kMvRows,
+    const int Erow = a.Erow > 0 ? a.Erow : a.E;
+    if (!encode_2d(&cm, a.cand, (uint64_t)Erow, (uint64_t)a.N, (uint64_t)ldC * 4, kMvChunk, kMvRows,
                    CU_TENSOR_MAP_SWIZZLE_128B) ||
         !encode_2d(&um, a.U, (uint64_t)a.ldE * 2, (uint64_t)n_qp, (uint64_t)a.ldE * 8, 2 * kMvChunk, QB / 2,
                    CU_TENSOR_MAP_SWIZZLE_NONE) ||

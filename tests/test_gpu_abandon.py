@@ -103,7 +103,7 @@ def _check_nn(Q, Cn, W, K=16, **opts):
 
 @pytest.mark.parametrize("mv_abandon", [0, 1])
 @pytest.mark.parametrize("kind,M,N,L,D,W,n_proto", [
-    ("proto_warp", 40, 2000, 128, 5, 13, 20),    # prototype classes: most pairs abandon after the prefix
+    ("proto_warp", 40, 2000, 128, 5, 13, 20),    # prototype classes: most pairs abandon after the sample
     ("random_walk", 36, 500, 100, 3, 10, 0),     # loose LB_MV: most pairs complete
     ("proto_warp", 32, 500, 200, 32, 20, 8),     # wide points (ring DTW tile)
     ("proto_warp", 7, 300, 64, 4, 6, 5),         # a block of fewer than 32 queries: never abandons

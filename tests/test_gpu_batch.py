@@ -258,3 +258,22 @@ def test_tune_cache_file_is_written_and_read(tmp_path):
     assert r.returncode == 0, r.stderr
     assert list(map(int, r.stdout.split()[-2:])) == [tile, G2]
     assert len(path.read_text().splitlines()) == 1          # nothing tuned, nothing appended
+
+
+@pytest.mark.parametrize("mv_abandon", [0, 1])
+def test_batch_abandoning_lb_mv(mv_abandon):
+    # sets of at least 32 queries sum a sample of every pair's LB_MV and complete only
+    # the pairs still under the seeded threshold (one set of 300 queries: two query
+    # passes per candidate tile; E = L*D not a multiple of 4: 4-byte copies); the
+    # answers are the oracle's either way
+    shapes = [(40, 500, 64, 3, 6, 8), (36, 300, 97, 5, 10, 8), (300, 60, 40, 4, 4, 4), (32, 450, 120, 12, 12, 16),
+              (64, 1000, 50, 2, 5, 8), (7, 200, 64, 3, 6, 8)]
+    host, sets = _make(shapes, 400)
+    outs, st = tc.batch_nn(sets, stats=True, mv_abandon=mv_abandon)
+    _check(host, outs)
+    _check_stats(st, shapes)
+    full = sum(M * N * L * D for (M, N, L, D, *_r) in shapes)
+    if mv_abandon:
+        assert st["mv_terms"] < full
+    else:
+        assert st["mv_terms"] == full
