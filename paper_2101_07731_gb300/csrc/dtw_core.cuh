@@ -139,8 +139,8 @@ constexpr int kAbandonEvery = 8;
 // at t for up to kRingFill*(kRingAhead+1) - 1 steps ahead span fewer than
 // kRingFill*(kRingAhead+1) + G slots; virtual lanes start at most one per step, so
 // kRingFill*(kRingAhead+1) row slots suffice.
-constexpr int kRingFill = 4;
-constexpr int kRingAhead = 3;
+constexpr int kRingFill = 8;
+constexpr int kRingAhead = 1;
 constexpr int kRingRows = 16;
 static_assert(kRingRows >= kRingFill * (kRingAhead + 1), "row ring too small");
 __host__ __device__ constexpr int ring_stride(int DM) { return ((DM / 4) & 1) ? DM + 8 : DM + 4; }
@@ -183,16 +183,35 @@ __device__ __forceinline__ void ring_fill(float *rcols, float *rrows, int RC, co
                                           int D, int W, int v1, int T, int *col_hi, int *v_hi, bool vec,
                                           const Grp &g) {
     constexpr int DMS = ring_stride(DM);
+    constexpr int SEG = DM / 4;  // 16-byte segments of a slot row (a power of two)
     const int c_end = min(L, T - ring_vmin(T, R, W, L) + 1);
-    for (int c = *col_hi; c < c_end; ++c)
-        ring_copy(rcols + (c & (RC - 1)) * DMS, B + (size_t)c * D, D, vec, g);
-    if (c_end > *col_hi) *col_hi = c_end;
     const int v_end = min(v1, ring_vmax(T, R, W, v1) + 1);
-    for (int vv = *v_hi; vv < v_end; ++vv) {
-        float *dst = rrows + (vv & (kRingRows - 1)) * R * DM;
-        const int nr = min(R, L - vv * R);
-        for (int r = 0; r < nr; ++r) ring_copy(dst + r * DM, A + (size_t)(vv * R + r) * D, D, vec, g);
+    if (vec) {
+        // one (point, 16-byte segment) item per lane and pass, over all the points of
+        // the fill: the new columns, then the rows of the new virtual lanes (consecutive
+        // query rows), so that every lane copies rather than one point per pass
+        const int segs = D >> 2, c0 = *col_hi, nc = c_end > c0 ? c_end - c0 : 0;
+        for (int k = g.lig; k < nc * SEG; k += g.G) {
+            const int c = c0 + k / SEG, s = k % SEG;
+            if (s < segs) cp_async_16(rcols + (c & (RC - 1)) * DMS + 4 * s, B + (size_t)c * D + 4 * s);
+        }
+        const int r0 = *v_hi * R, r1 = min(v_end * R, L), nr = r1 > r0 ? r1 - r0 : 0;
+        for (int k = g.lig; k < nr * SEG; k += g.G) {
+            const int row = r0 + k / SEG, s = k % SEG;
+            if (s < segs)
+                cp_async_16(rrows + ((row / R) & (kRingRows - 1)) * R * DM + (row % R) * DM + 4 * s,
+                            A + (size_t)row * D + 4 * s);
+        }
+    } else {
+        for (int c = *col_hi; c < c_end; ++c)
+            ring_copy(rcols + (c & (RC - 1)) * DMS, B + (size_t)c * D, D, vec, g);
+        for (int vv = *v_hi; vv < v_end; ++vv) {
+            float *dst = rrows + (vv & (kRingRows - 1)) * R * DM;
+            const int nr = min(R, L - vv * R);
+            for (int r = 0; r < nr; ++r) ring_copy(dst + r * DM, A + (size_t)(vv * R + r) * D, D, vec, g);
+        }
     }
+    if (c_end > *col_hi) *col_hi = c_end;
     if (v_end > *v_hi) *v_hi = v_end;
 }
 
