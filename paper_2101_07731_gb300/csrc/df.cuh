@@ -161,6 +161,42 @@ __device__ double band_pass_df(const float *__restrict__ A, const float *__restr
     return res_h < INF ? __dadd_rn((double)res_h, (double)res_l) : __longlong_as_double(0x7ff0000000000000LL);
 }
 
+// A point of D floats (D <= DM) into registers, zero-padded to DM; vec: 16-byte loads
+// (D a multiple of 4, p 16-byte aligned).
+template <int DM>
+__device__ __forceinline__ void df_load_point(const float *p, int D, bool vec, float (&x)[DM]) {
+    if (vec) {
+#pragma unroll
+        for (int k = 0; k < DM / 4; ++k) {
+            const float4 v = 4 * k < D ? __ldg(reinterpret_cast<const float4 *>(p) + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+            x[4 * k] = v.x;
+            x[4 * k + 1] = v.y;
+            x[4 * k + 2] = v.z;
+            x[4 * k + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < DM; ++k) x[k] = k < D ? __ldg(p + k) : 0.f;
+    }
+}
+
+// df_cell_cost (below) of two points already in registers: the same operations in the
+// same order, so the same value.
+template <int DM>
+__device__ __forceinline__ void df_cell_cost_regs(const float (&a)[DM], const float (&b)[DM], int D, float &c_h,
+                                                  float &c_l) {
+    float sh = 0.f, sl = 0.f;
+#pragma unroll
+    for (int p = 0; p < DM; ++p) {
+        if (p < D) {
+            float th, tl;
+            two_sum(a[p], -b[p], th, tl);
+            df_square_term(th, tl, sh, sl);
+        }
+    }
+    fast_two_sum(sh, sl, c_h, c_l);
+}
+
 // Double-float cost of one cell (rows a and b of D floats, D <= DM), in the operation
 // order of band_pass_df: (c_h, c_l) = FastTwoSum of the exact-part sum and the
 // small-part sum.

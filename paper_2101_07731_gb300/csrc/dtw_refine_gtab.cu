@@ -20,7 +20,11 @@
 
 namespace tc {
 
-constexpr int kGtabThreads = 256;
+constexpr int kGtabThreads = 128;  // two blocks (table slots) per SM at up to 255 registers
+// consecutive band columns of one row per thread and item (registers: the query point and
+// the columns' candidate points, DM floats each)
+template <int DM>
+__host__ __device__ constexpr int gtab_cols() { return DM <= 32 ? 4 : 2; }
 
 // Steps of the band sweep with R rows per lane: tau in [0, tau_end].
 __host__ __device__ inline int sweep_steps(int L, int W, int R) {
@@ -48,28 +52,34 @@ __global__ void __launch_bounds__(kGtabThreads) k_dtw_refine_df_gtab(const float
         const int64_t n = (int64_t)(pid - (uint32_t)m * (uint32_t)N);
         const float *qa = Q + (size_t)m * E, *cb = Cand + (size_t)n * E;
         __syncthreads();  // the previous entry's sweep is done with the slot
-        for (int k0 = threadIdx.x; k0 < cells; k0 += 2 * kGtabThreads) {
-            float ch[2], cl[2];
-            bool in[2];
-            int kk[2], ii[2], jj2[2];
+        // items (row i, kGtabCols consecutive band offsets): the query point once, the
+        // candidate points of the columns next (their loads in flight together), then
+        // the costs; 16-byte loads where the rows allow
+        const bool vec = (D % 4) == 0 && ((((uintptr_t)qa) | ((uintptr_t)cb)) & 15) == 0;
+        constexpr int kGtabCols = gtab_cols<DM>();
+        const int ngrp = (BW + kGtabCols - 1) / kGtabCols;
+        for (int it = threadIdx.x; it < L * ngrp; it += kGtabThreads) {
+            const int i = it / ngrp, o0 = (it - i * ngrp) * kGtabCols;
+            float a[DM];
+            df_load_point<DM>(qa + (size_t)i * D, D, vec, a);
+            float b[kGtabCols][DM];
+            bool in[kGtabCols];
+            int jj[kGtabCols];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                kk[u] = k0 + u * kGtabThreads;
-                const int k = kk[u] < cells ? kk[u] : cells - 1;
-                const int i = k / BW, j = i + (k - i * BW) - W;
-                in[u] = kk[u] < cells && j >= 0 && j < L;
-                const int jj = in[u] ? j : i;
-                ii[u] = i;
-                jj2[u] = jj;
-                df_cell_cost<DM>(qa + (size_t)i * D, cb + (size_t)jj * D, D, ch[u], cl[u]);
+            for (int u = 0; u < kGtabCols; ++u) {
+                const int j = i + o0 + u - W;
+                in[u] = o0 + u < BW && j >= 0 && j < L;
+                jj[u] = in[u] ? j : i;
+                df_load_point<DM>(cb + (size_t)jj[u] * D, D, vec, b[u]);
             }
+            // cell (i, j) is row r of virtual lane vv = i / R, read by lane vv % 32 at step j + vv
+            const int vv = i / R, r = i - vv * R;
 #pragma unroll
-            for (int u = 0; u < 2; ++u)
-                if (in[u]) {
-                    // cell (i, j) is row r of virtual lane vv = i / R, read by lane vv % 32 at step j + vv
-                    const int vv = ii[u] / R, r = ii[u] - vv * R;
-                    cost[table_dp_pos(jj2[u] + vv, vv & 31, R, r)] = make_float2(ch[u], cl[u]);
-                }
+            for (int u = 0; u < kGtabCols; ++u) {
+                float ch, cl;
+                df_cell_cost_regs<DM>(a, b[u], D, ch, cl);
+                if (in[u]) cost[table_dp_pos(jj[u] + vv, vv & 31, R, r)] = make_float2(ch, cl);
+            }
         }
         __syncthreads();  // the block's table writes are visible to its first warp
         if (threadIdx.x < 32) {
