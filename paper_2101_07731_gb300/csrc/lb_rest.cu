@@ -13,9 +13,9 @@
 // live (query, candidate) pairs of its tile (in a per-CTA global scratch region), then
 // streams the remaining chunks of its candidates and of its queries' envelopes through
 // shared memory in chunks of 32, two stages deep, every 128-byte row stored with its
-// 16-byte segments XOR-swizzled by row & 7 (threads reading different rows then mostly
-// hit different banks).  Each consumer thread advances up to kRestEpt listed pairs by
-// one chunk per stage.  Every kRestCheck chunks a pair whose running sum has passed
+// 16-byte segments XOR-swizzled by row & 7.  The consumers advance their listed pairs by
+// one chunk per stage (bulk-tensor form: groups of 8 lanes per pair, see below; cp.async
+// form: one thread per pair).  Every kRestCheck chunks a pair whose running sum has passed
 // the threshold is abandoned again (its partial sum is written, a lower bound above
 // the threshold); a check that finds no listed pair left ends the stream.
 //
@@ -55,6 +55,30 @@ constexpr size_t rest_tma_smem(int tn, int qg) {
     return 1024 + 2 * (size_t)rest_tma_stage_bytes(tn, qg) + 32 + 16 + (size_t)qg * 4;
 }
 static_assert(rest_tma_smem(kRestTC, kRestQG) <= 227 * 1024, "one CTA of the completion stream per SM");
+
+// Consumers of the bulk-tensor form in groups of 8 lanes: a group advances one listed
+// pair at a time and lane s takes 16-byte segment s of the chunk (four elements) of its
+// candidate row and of its query's U and Lo rows -- the 8 lanes read all 8 segments of
+// each 128-byte row, so a phase of a shared-memory load touches all 32 banks once (one
+// thread per pair read 8 different rows per phase, whose swizzled segments collided).
+// Each lane keeps its own partial sum; the pair's sum is the 8 partials added, rounded
+// down, in a fixed xor-shuffle order (the same on every lane), at every check and at the
+// end.
+constexpr int kRestGroupEpt = 14;          // listed pairs per 8-lane group per round
+constexpr int kRestGroups = kRestCons / 8;
+constexpr int kRestGroupRound = kRestGroups * kRestGroupEpt;
+
+struct RestGroupPairs {
+    int q[kRestGroupEpt], n[kRestGroupEpt];
+    float acc[kRestGroupEpt], th[kRestGroupEpt];
+    bool act[kRestGroupEpt];
+};
+
+__device__ __forceinline__ float group8_sum_rd(float v) {
+    v = __fadd_rd(v, __shfl_xor_sync(0xffffffffu, v, 1));
+    v = __fadd_rd(v, __shfl_xor_sync(0xffffffffu, v, 2));
+    return __fadd_rd(v, __shfl_xor_sync(0xffffffffu, v, 4));
+}
 
 __global__ void __launch_bounds__(kRestTmaThreads, 1)
     k_lb_mv_rest_tma(const __grid_constant__ CUtensorMap cmap, const __grid_constant__ CUtensorMap umap,
@@ -103,7 +127,7 @@ __global__ void __launch_bounds__(kRestTmaThreads, 1)
             rest_list(a, n0, tn, q0, nq, thr, (int *)&flags[3], list);
             __syncthreads();  // the list (global, this CTA's region) and its count
             const int cnt = flags[3];
-            for (int r0 = 0; r0 < cnt; r0 += kRestCons * kRestEpt) {
+            for (int r0 = 0; r0 < cnt; r0 += kRestGroupRound) {
                 int consumed = 0;
                 if (producer) {
                     if (lane == 0) {
@@ -131,8 +155,19 @@ __global__ void __launch_bounds__(kRestTmaThreads, 1)
                         flags[2] = issued;
                     }
                 } else {
-                    RestPairs p;
-                    rest_load(p, a, list, r0, tid, kRestCons, cnt, n0, q0, thr);
+                    const int grp = tid >> 3, seg = tid & 7;
+                    RestGroupPairs p;
+#pragma unroll
+                    for (int k = 0; k < kRestGroupEpt; ++k) {
+                        const int i = r0 + k * kRestGroups + grp;
+                        p.act[k] = i < cnt;
+                        const uint32_t en = p.act[k] ? __ldcg(list + i) : 0u;
+                        p.q[k] = (int)(en >> 16);
+                        p.n[k] = (int)(en & 0xffffu);
+                        // the sample sum enters once, through lane 0 of the group
+                        p.acc[k] = p.act[k] && seg == 0 ? a.lb[(size_t)(q0 + p.q[k]) * a.ldLb + n0 + p.n[k]] : 0.f;
+                        p.th[k] = thr[p.q[k]];
+                    }
                     int step = 0;
                     for (int c = rest_next(a, 0, nchunks); c < nchunks; c = rest_next(a, c + 1, nchunks), ++step) {
                         const uint32_t s = kc & 1u;
@@ -145,25 +180,48 @@ __global__ void __launch_bounds__(kRestTmaThreads, 1)
                         if (!flags[1]) {
                             const float *cb = reinterpret_cast<const float *>(sb + s * stage);
                             const float *ub = cb + tn * 32, *lbp = ub + qgp * 32;
+                            const unsigned el = (unsigned)min(kMvChunk, a.E - c * kMvChunk);
 #pragma unroll
-                            for (int k = 0; k < kRestEpt; ++k) {
+                            for (int k = 0; k < kRestGroupEpt; ++k) {
                                 if (!p.act[k]) continue;
-                                p.acc[k] = __fadd_rd(p.acc[k], rest_chunk(cb + p.n[k] * 32, ub + p.q[k] * 32,
-                                                                          lbp + p.q[k] * 32, p.n[k] & 7, p.q[k] & 7));
-                                terms += (unsigned)min(kMvChunk, a.E - c * kMvChunk);
+                                const int cs = (seg ^ (p.n[k] & 7)) << 2, es = (seg ^ (p.q[k] & 7)) << 2;
+                                const float4 cv = *reinterpret_cast<const float4 *>(cb + p.n[k] * 32 + cs);
+                                const float4 uv = *reinterpret_cast<const float4 *>(ub + p.q[k] * 32 + es);
+                                const float4 lv = *reinterpret_cast<const float4 *>(lbp + p.q[k] * 32 + es);
+                                f2 pp = rest_step(pk(cv.x, cv.y), pk(uv.x, uv.y), pk(lv.x, lv.y), 0ull);
+                                pp = rest_step(pk(cv.z, cv.w), pk(uv.z, uv.w), pk(lv.z, lv.w), pp);
+                                float p0, p1;
+                                upk(pp, p0, p1);
+                                p.acc[k] = __fadd_rd(p.acc[k], __fadd_rd(p0, p1));
+                                if (seg == 0) terms += el;
                             }
                         }
                         __syncwarp();
                         if (lane == 0) mbar_arrive(empty0 + 8 * s);
                         if (step % kRestCheck == kRestCheck - 1) {
-                            const bool any = rest_check(p, a, n0, q0);
+                            bool any = false;
+#pragma unroll
+                            for (int k = 0; k < kRestGroupEpt; ++k) {
+                                const float tot = group8_sum_rd(p.acc[k]);  // every lane takes part
+                                if (p.act[k] && tot > p.th[k]) {  // abandoned: its partial sum
+                                    if (seg == 0) a.lb[(size_t)(q0 + p.q[k]) * a.ldLb + n0 + p.n[k]] = tot;
+                                    p.act[k] = false;
+                                }
+                                any |= p.act[k];
+                            }
                             if (!consumers_any(any && !flags[1])) {
                                 if (tid == 0) flags[0] = 1;  // stop the producer
                                 break;
                             }
                         }
                     }
-                    if (!flags[1]) rest_store(p, a, n0, q0);
+                    if (!flags[1]) {
+#pragma unroll
+                        for (int k = 0; k < kRestGroupEpt; ++k) {
+                            const float tot = group8_sum_rd(p.acc[k]);
+                            if (p.act[k] && seg == 0) a.lb[(size_t)(q0 + p.q[k]) * a.ldLb + n0 + p.n[k]] = tot;
+                        }
+                    }
                 }
                 __syncthreads();  // the producer is done issuing this round's chunks
                 if (!producer) {
