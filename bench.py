@@ -784,7 +784,7 @@ def run_ours(a):
     else:
         other["lb_mv"] = other["lb_rest"] = 0.0
     res["roofline_other_stage"] = _roofline(other, per_step, B, N, L, D, n_sm, _peaks(),
-                                            profile_mv="ncu_k_lb_mv_32_proto_1024x100000")
+                                            profile_mv="ncu_k_lb_mv_rest_tma_proto_1024x100000")
     if res["roofline"]["traffic"] is not None:
         res["roofline"]["traffic_note"] = ("DRAM bytes per pair of an ncu capture of the same kernel (the tuner's "
                                            "16,384-pair launch on a slice of the workload) x the step's DTW pairs")
