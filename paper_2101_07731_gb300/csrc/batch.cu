@@ -58,7 +58,7 @@ __device__ __forceinline__ int ld_acquire_s32(const int *p) {
     return v;
 }
 
-// Thread 0 spins until *cnt >= target (bounded); every thread gets the verdict.
+// Thread 0 spins until *cnt >= target (bounded); every thread gets the outcome.
 __device__ bool batch_wait(const int *cnt, int target, long long limit, BatchCtl *ctl, int where) {
     __shared__ int ok;
     if (threadIdx.x == 0) {
