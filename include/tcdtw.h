@@ -403,6 +403,12 @@ int tcdtw_batch_selftest_timeout(int64_t spin_limit, void *stream);
  * of the self-test, INVALID for wait_us outside [1, 10^7], NOMEM, CUDA on a runtime
  * error.  Synchronous on `stream`. */
 int tcdtw_lb_mv_selftest_timeout(int64_t wait_us, void *stream);
+/* The same test for the bulk-tensor completion kernel of the abandoning LB_MV
+ * (tcdtw_lb_mv_abandon, mv_abandon): a launch whose producer issues nothing, so its
+ * consumers' first wait runs out after wait_us microseconds.  Synchronous on `stream`.
+ * Returns TIMEOUT when the wait limit worked; INVALID (wait_us outside [1, 1e7]),
+ * NOMEM, CUDA. */
+int tcdtw_lb_mv_rest_selftest_timeout(int64_t wait_us, void *stream);
 
 /* Number of compiled DTW band tiles, and the shape of tile t: G lanes per pair,
  * R rows per lane (host outputs).  Returns INVALID for an unknown t. */

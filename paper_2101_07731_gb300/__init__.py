@@ -94,6 +94,7 @@ _SIGS = {
     "tcdtw_batch_nn": (C.c_int, [C.POINTER(Dataset), _I32, C.POINTER(Opts), C.POINTER(Stats), _P]),
     "tcdtw_batch_selftest_timeout": (C.c_int, [_I64, _P]),
     "tcdtw_lb_mv_selftest_timeout": (C.c_int, [_I64, _P]),
+    "tcdtw_lb_mv_rest_selftest_timeout": (C.c_int, [_I64, _P]),
     "tcdtw_batch_release": (C.c_int, []),
     "tcdtw_batch_tiles": (C.c_int, [C.POINTER(Dataset), _I32, C.POINTER(Opts), C.POINTER(_I32), C.POINTER(_I32), _P]),
     "tcdtw_inject_alloc_failure": (C.c_int, [_I64]),
@@ -376,6 +377,13 @@ def lb_mv_selftest_timeout(wait_us: int = 20000) -> int:
     """Run the TMA LB_MV stream's wait-limit self-test; returns the status code
     (TIMEOUT when the device-side wait ran out and the launch ended by itself)."""
     return int(_load().tcdtw_lb_mv_selftest_timeout(int(wait_us), _stream()))
+
+
+def lb_mv_rest_selftest_timeout(wait_us: int = 20000) -> int:
+    """Run the wait-limit self-test of the abandoning LB_MV's completion kernel;
+    returns the status code (TIMEOUT when its consumers' wait ran out and the launch
+    ended by itself)."""
+    return int(_load().tcdtw_lb_mv_rest_selftest_timeout(int(wait_us), _stream()))
 
 
 # ----------------------------------------------------------------- pipeline stages

@@ -90,6 +90,8 @@ struct LbMvRestArgs {
     int sms;
     unsigned long long *terms = nullptr;  // optional: += the (element, pair) terms summed
     DevStatus *status = nullptr;          // bounded waits of the bulk-tensor form (null: cp.async form)
+    uint64_t wait_ns = 0;                 // their limit (0: the library default)
+    int stall = 0;                        // self-test: the producer issues nothing
 };
 int lb_mv_rest_tile(int64_t N, int sms);
 int64_t lb_mv_rest_list_entries(int64_t N, int Mb, int sms);

@@ -31,8 +31,10 @@
 // Rounding as in the dense stream: terms and sums rounded down, so every stored value
 // is at most the exact LB_MV.
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
+#include "api_internal.h"
 #include "common.cuh"
 #include "lb_device.cuh"
 #include "lb_kernels.cuh"
@@ -132,7 +134,7 @@ __global__ void __launch_bounds__(kRestTmaThreads, 1)
                 if (producer) {
                     if (lane == 0) {
                         int issued = 0;
-                        for (int c = rest_next(a, 0, nchunks); c < nchunks && !flags[0] && !flags[1];
+                        for (int c = rest_next(a, 0, nchunks); c < nchunks && !flags[0] && !flags[1] && !a.stall;
                              c = rest_next(a, c + 1, nchunks)) {
                             const uint32_t s = kp & 1u;
                             // the stage's previous chunk must have been released (the wait
@@ -314,9 +316,10 @@ cudaError_t launch_lb_mv_rest(const LbMvRestArgs &a, cudaStream_t s) {
             if (e != cudaSuccess) return e;
             g_attr_dev_tma = dev;
         }
-        k_lb_mv_rest_tma<<<(unsigned)grid, kRestTmaThreads, rest_tma_smem(tn, qg), s>>>(cm, um, lm, a, tn, qg,
-                                                                                       kWaitNs);
+        k_lb_mv_rest_tma<<<(unsigned)grid, kRestTmaThreads, rest_tma_smem(tn, qg), s>>>(
+            cm, um, lm, a, tn, qg, a.wait_ns ? a.wait_ns : kWaitNs);
     } else {
+        if (a.stall) return cudaErrorNotSupported;  // the self-test needs the bulk-tensor form
         if (g_attr_dev_cp != dev) {
             e = cudaFuncSetAttribute(k_lb_mv_rest_cp, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)rest_cp_smem(kRestTC, kRestQG));
@@ -331,3 +334,54 @@ cudaError_t launch_lb_mv_rest(const LbMvRestArgs &a, cudaStream_t s) {
 }
 
 }  // namespace tc
+
+// Failure-detection self-test: one completion launch whose producer issues nothing, so
+// its consumers' first wait on a chunk runs out after wait_us microseconds; the launch
+// records TCDTW_ERR_TIMEOUT and ends by itself.
+extern "C" int tcdtw_lb_mv_rest_selftest_timeout(int64_t wait_us, void *stream) {
+    using namespace tc;
+    if (wait_us < 1 || wait_us > 10000000) return TCDTW_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    // 32 candidates of 64 elements (chunk 0 sampled, chunk 1 to complete), 2 queries
+    const int N = 32, E = 64, M = 2;
+    const int64_t list_n = lb_mv_rest_list_entries(N, M, 1);
+    const size_t floats = (size_t)N * E + 2 * (size_t)M * E + (size_t)M * N;
+    float *buf = nullptr;
+    uint32_t *list = nullptr;
+    DevStatus *st = nullptr;
+    if (dev_malloc((void **)&buf, floats * sizeof(float)) != cudaSuccess) return TCDTW_ERR_NOMEM;
+    if (dev_malloc((void **)&list, (size_t)list_n * sizeof(uint32_t)) != cudaSuccess ||
+        dev_malloc((void **)&st, sizeof(DevStatus)) != cudaSuccess) {
+        cudaFree(buf);
+        cudaFree(list);
+        return TCDTW_ERR_NOMEM;
+    }
+    // zero candidates, envelopes and bounds: every pair's sample sum (0) is under the
+    // +inf threshold, so every pair is listed and the consumers wait for chunk 1
+    cudaError_t e = cudaMemsetAsync(buf, 0, floats * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(DevStatus), s);
+    LbMvRestArgs a;
+    a.cand = buf; a.N = N; a.E = E; a.samp = 1; a.sstride = 2; a.ldC = E;
+    a.Up = buf + (size_t)N * E; a.Lp = a.Up + (size_t)M * E; a.ldP = E; a.Mb = M;
+    a.lb = buf + (size_t)N * E + 2 * (size_t)M * E; a.ldLb = N; a.thresh = nullptr; a.bsf = nullptr; a.rho = 1.f;
+    a.list = list; a.list_entries = list_n; a.sms = 1; a.status = st;
+    a.wait_ns = (uint64_t)wait_us * 1000; a.stall = 1;
+    // thresholds +inf (bsf is not read when thresholds are given)
+    float *dthr = nullptr;
+    if (e == cudaSuccess) e = dev_malloc((void **)&dthr, M * sizeof(float));
+    if (e == cudaSuccess) {
+        const float inf[M] = {INFINITY, INFINITY};
+        e = cudaMemcpyAsync(dthr, inf, sizeof(inf), cudaMemcpyHostToDevice, s);
+        a.thresh = dthr;
+    }
+    if (e == cudaSuccess) e = launch_lb_mv_rest(a, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    DevStatus h{0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(&h, st, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(buf);
+    cudaFree(list);
+    cudaFree(st);
+    cudaFree(dthr);
+    if (e != cudaSuccess) return cuda_err(e);
+    return h.code == TCDTW_ERR_TIMEOUT ? TCDTW_ERR_TIMEOUT : (h.code ? h.code : TCDTW_OK);
+}

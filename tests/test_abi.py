@@ -154,6 +154,9 @@ def test_argument_errors_of_the_newer_calls(lib):
     assert lib.tcdtw_lb_mv_selftest_timeout(0, None) == tc.ERR_INVALID
     assert lib.tcdtw_lb_mv_selftest_timeout(10_000_001, None) == tc.ERR_INVALID
     assert lib.tcdtw_batch_selftest_timeout(0, None) == tc.ERR_INVALID
+    lib.tcdtw_lb_mv_rest_selftest_timeout.argtypes = [C.c_int64, C.c_void_p]
+    assert lib.tcdtw_lb_mv_rest_selftest_timeout(0, None) == tc.ERR_INVALID
+    assert lib.tcdtw_lb_mv_rest_selftest_timeout(10_000_001, None) == tc.ERR_INVALID
 
 
 def test_noalloc_refuses_what_the_allocating_call_refuses(lib):

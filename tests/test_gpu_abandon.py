@@ -88,6 +88,17 @@ def test_lb_mv_abandon_complete_values_match_the_plain_stream():
     np.testing.assert_allclose(a, b, rtol=2 * _lb_rtol(96, 5), atol=1e-6)
 
 
+def test_lb_mv_completion_wait_limit_selftest():
+    # a completion launch whose producer issues nothing: its consumers' first wait runs
+    # out, the launch reports TIMEOUT and ends, and the context stays usable
+    assert tc.lb_mv_rest_selftest_timeout(2000) == tc.ERR_TIMEOUT
+    Q, Cn = _set("proto_warp", 33, 200, 128, 4, 91)
+    ref = _oracle_lb(Q, Cn, 6)
+    thr = np.quantile(ref, 0.2, axis=1).astype(np.float32)
+    out = tc.lb_mv_abandon(_gpu(Q), _gpu(Cn), 6, _gpu(thr)).cpu().numpy().astype(np.float64)
+    _check_contract(out, ref, thr, 128, 4)
+
+
 def _check_nn(Q, Cn, W, K=16, **opts):
     index = tc.Index(_gpu(Cn), W, K, **opts)
     idx, dist, st = index.nn(_gpu(Q), stats=True)
