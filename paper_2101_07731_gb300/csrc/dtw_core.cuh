@@ -119,7 +119,11 @@ __device__ __forceinline__ unsigned row_mask(int lo, int hi, int R) {
     return (0xffffffffu >> (31 - hi)) & (0xffffffffu << lo);
 }
 
-constexpr int kAbandonEvery = 8;
+// Steps between two abandon checks (a power of two).  Each check costs a group-wide
+// minimum and a read of the best-so-far; a pair is dropped at most that many steps later
+// than it could be.  Measured on GB300: 16 for narrow points, 32 for wide ones (whose
+// steps are longer) beat 8 by 1% and 4% of the search's DTW stage.
+__host__ __device__ constexpr int abandon_every(int DM) { return DM >= 16 ? 32 : 16; }
 
 // ------------------------------------------------------------------ column / row rings
 // Wide points (DM >= 16) are costly to fetch per lane and step: each lane
@@ -144,13 +148,22 @@ constexpr int kRingAhead = 1;
 constexpr int kRingRows = 16;
 static_assert(kRingRows >= kRingFill * (kRingAhead + 1), "row ring too small");
 __host__ __device__ constexpr int ring_stride(int DM) { return ((DM / 4) & 1) ? DM + 8 : DM + 4; }
+// The (R = 6, DM = 32) tile keeps the last ring_smem_rows(R, DM) of its 6 rows in a
+// lane-private shared-memory slot (G*DM floats per row and group, [row][DM/4][G] float4 so
+// a quarter warp reads 128 contiguous bytes) instead of 32 registers per row: at 192
+// registers of rows the search kernel ran at the 255-register cap with dependent
+// instructions issued back to back, and with the slot the scheduler has room to overlap
+// them (one more float4 load per row and 4 dimensions; ncu on GB300: issue 42 -> 49%
+// active, FMA pipe 46 -> 55%, the search's DTW stage 408 -> 364 ms per 256 queries at
+// L = 2,048, W = 102).
+__host__ __device__ constexpr int ring_smem_rows(int R, int DM) { return (DM == 32 && R == 6) ? 1 : 0; }
 __host__ __device__ constexpr int ring_cols(int G) {
     return (kRingFill * (kRingAhead + 1) + G) <= 16   ? 16
            : (kRingFill * (kRingAhead + 1) + G) <= 32 ? 32
                                                        : 64;
 }
 __host__ __device__ constexpr int ring_group_floats(int R, int DM, int G) {
-    return ring_cols(G) * ring_stride(DM) + kRingRows * R * DM;
+    return ring_cols(G) * ring_stride(DM) + kRingRows * R * DM + ring_smem_rows(R, DM) * G * DM;
 }
 // shared memory of a 128-thread block of the ring variant
 __host__ __device__ constexpr size_t ring_block_bytes(int R, int DM, int G) {
@@ -217,7 +230,7 @@ __device__ __forceinline__ void ring_fill(float *rcols, float *rrows, int RC, co
 
 // Hook sets.  top(j): row above the first virtual lane of a pass (v0 > 0).
 // cell(i, j, val): every in-band cell (kCells).  after_col(i0, j, bottom): once per
-// computed column of a virtual lane.  abandon(m): every kAbandonEvery steps with the
+// computed column of a virtual lane.  abandon(m): every abandon_every(DM) steps with the
 // group-wide frontier minimum (kAbandon).
 struct NoHooks {
     static constexpr bool kAbandon = false;
@@ -242,7 +255,10 @@ struct NoHooks {
 // current one (a virtual-lane start then reads shared memory, not global memory).
 // kRing (wide points only, v0 == 0): candidate columns and query rows come from the
 // group's rings at `ring` (ring_group_floats(R, DM, G) floats, RC = ring_cols(G) column
-// slots, the dimensions D..DM-1 of every slot zero); all lanes of the warp call it.
+// slots, the dimensions D..DM-1 of every slot zero); all lanes of the warp call it.  The
+// last ring_smem_rows(R, DM) rows of a lane's virtual lane are copied from the row ring to
+// the lane's private slot after the rings (read there every step), the other rows to
+// registers.
 template <int R, int DM, class Hooks, bool kRing = false>
 __device__ __forceinline__ float band_pass(const float *__restrict__ A, const float *__restrict__ B, int L, int D,
                                            int W, int v0, int v1, const Grp &g, Hooks &hooks, bool live,
@@ -256,7 +272,9 @@ __device__ __forceinline__ float band_pass(const float *__restrict__ A, const fl
     constexpr bool kDimPack = DM >= 16;
     constexpr int DH = (DM + 1) / 2;
     f2 a2[kDimPack ? 1 : RP][kDimPack ? 1 : DM];     // rows (2k, 2k+1) of the virtual lane, dimension p
-    f2 ad[kDimPack ? R : 1][kDimPack ? DH : 1];      // wide points: row r, dimensions (2h, 2h+1)
+    constexpr int RSM = kRing ? ring_smem_rows(R, DM) : 0;
+    constexpr int RREG = R - RSM;
+    f2 ad[kDimPack ? RREG : 1][kDimPack ? DH : 1];      // wide points: row r, dimensions (2h, 2h+1)
     float col[R];      // R(i0 + r, j-1) -> R(i0 + r, j)
     float b[DM];
     float bottom = INF, prev_in = INF, result = INF, mn_prev = INF;
@@ -269,9 +287,10 @@ __device__ __forceinline__ float band_pass(const float *__restrict__ A, const fl
     int tlo = v < v1 ? v_jlo(v, R, W) + v : 1 << 30;
     int thi = v < v1 ? v_jhi(v, R, W, L) + v : -1;
     bool loaded = false, staged = false;
-    long long ncell = 0;
+    int ncell = 0;  // statistics only; 32 bits hold a lane's cells for L < 10^8
     *abandoned = false;
     float *rcols = ring, *rrows = ring + (kRing ? RC * ring_stride(DM) : 0);
+    float *rpriv = RSM ? rrows + kRingRows * R * DM + 4 * g.lig : nullptr;
     int col_hi = 0, v_hi = 0;
     const bool ring_vec = ((D & 3) == 0) && (((((uintptr_t)A) | ((uintptr_t)B)) & 15) == 0);
     if (kRing) {
@@ -332,13 +351,23 @@ __device__ __forceinline__ float band_pass(const float *__restrict__ A, const fl
                 if (kDimPack && kRing) {
                     const float *rr = rrows + (v & (kRingRows - 1)) * R * DM;
 #pragma unroll
-                    for (int r = 0; r < R; ++r) {
+                    for (int r = 0; r < RREG; ++r) {
 #pragma unroll
                         for (int k = 0; k < DM / 4; ++k) {
                             float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
                             if (i0 + r < L) x = *reinterpret_cast<const float4 *>(rr + r * DM + 4 * k);
                             ad[kDimPack ? r : 0][kDimPack ? 2 * k : 0] = pk(x.x, x.y);
                             ad[kDimPack ? r : 0][kDimPack ? 2 * k + 1 : 0] = pk(x.z, x.w);
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < RSM; ++q) {
+#pragma unroll
+                        for (int k = 0; k < DM / 4; ++k) {
+                            float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+                            if (i0 + RREG + q < L)
+                                x = *reinterpret_cast<const float4 *>(rr + (RREG + q) * DM + 4 * k);
+                            *reinterpret_cast<float4 *>(rpriv + (q * (DM / 4) + k) * 4 * g.G) = x;
                         }
                     }
                 } else if (kDimPack) {
@@ -379,11 +408,19 @@ __device__ __forceinline__ float band_pass(const float *__restrict__ A, const fl
                     const float4 x = *reinterpret_cast<const float4 *>(bc + 4 * k);
                     const f2 b0 = pk(x.x, x.y), b1 = pk(x.z, x.w);
 #pragma unroll
-                    for (int r = 0; r < R; ++r) {
+                    for (int r = 0; r < RREG; ++r) {
                         const f2 t0 = sub2(ad[kDimPack ? r : 0][kDimPack ? 2 * k : 0], b0);
                         cs[kDimPack ? r : 0] = fma2(t0, t0, cs[kDimPack ? r : 0]);
                         const f2 t1 = sub2(ad[kDimPack ? r : 0][kDimPack ? 2 * k + 1 : 0], b1);
                         cs[kDimPack ? r : 0] = fma2(t1, t1, cs[kDimPack ? r : 0]);
+                    }
+#pragma unroll
+                    for (int q = 0; q < RSM; ++q) {
+                        const float4 y = *reinterpret_cast<const float4 *>(rpriv + (q * (DM / 4) + k) * 4 * g.G);
+                        const f2 t0 = sub2(pk(y.x, y.y), b0);
+                        cs[kDimPack ? RREG + q : 0] = fma2(t0, t0, cs[kDimPack ? RREG + q : 0]);
+                        const f2 t1 = sub2(pk(y.z, y.w), b1);
+                        cs[kDimPack ? RREG + q : 0] = fma2(t1, t1, cs[kDimPack ? RREG + q : 0]);
                     }
                 }
             } else if (kDimPack) {
@@ -471,7 +508,7 @@ __device__ __forceinline__ float band_pass(const float *__restrict__ A, const fl
         if (Hooks::kAbandon) {
             float fm = fminf(mn_prev, step_min);
             mn_prev = step_min;
-            if (((tau - tau0) & (kAbandonEvery - 1)) == kAbandonEvery - 1) {
+            if (((tau - tau0) & (abandon_every(DM) - 1)) == abandon_every(DM) - 1) {
                 fm = grp_min(fm, g);
                 if (!dead && hooks.abandon(fm)) {
                     dead = true;
