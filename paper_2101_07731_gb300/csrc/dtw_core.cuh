@@ -43,6 +43,12 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
     return r;
 }
+// max that returns NaN when either operand is NaN (a NaN cost stays NaN, as with a select)
+__device__ __forceinline__ float max_nan(float a, float b) {
+    float r;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
 __device__ __forceinline__ float min3f(float a, float b, float c) {
     float r;
     asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
@@ -165,9 +171,22 @@ __host__ __device__ constexpr int ring_cols(int G) {
 __host__ __device__ constexpr int ring_group_floats(int R, int DM, int G) {
     return ring_cols(G) * ring_stride(DM) + kRingRows * R * DM + ring_smem_rows(R, DM) * G * DM;
 }
-// shared memory of a 128-thread block of the ring variant
+// Band table of the row-slot tile (one per block, after the groups' rings): whether row r
+// of a virtual lane is inside the band at column j depends only on dj = j - i0, so entry
+// dj + W (0 <= dj + W < 2W + R) holds the cost floor of each row (0 inside the band, +inf
+// outside: a max of cost and floor replaces a bit test and a select per row) and the number of
+// rows inside, read with two float4 loads per step.  Rows past the end of the series
+// (the last virtual lane when R does not divide L) take the exact row mask instead.
+// Space is kept for G(R+1) >= 2W+R entries, the most a valid (tile, G) can need.
+__host__ __device__ constexpr bool ring_band_table(int R, int DM) { return ring_smem_rows(R, DM) > 0 && R <= 7; }
+constexpr int kBandEntry = 8;  // floats per entry: R floors, the row count (int bits), padding
+__host__ __device__ constexpr size_t band_table_bytes(int R, int DM, int G) {
+    return ring_band_table(R, DM) ? (size_t)G * (R + 1) * kBandEntry * sizeof(float) : 0;
+}
+// shared memory of a 128-thread block of the ring variant: the groups' rings, then the
+// band table
 __host__ __device__ constexpr size_t ring_block_bytes(int R, int DM, int G) {
-    return (size_t)(128 / G) * ring_group_floats(R, DM, G) * sizeof(float);
+    return (size_t)(128 / G) * ring_group_floats(R, DM, G) * sizeof(float) + band_table_bytes(R, DM, G);
 }
 __device__ __forceinline__ void cp_async_wait_ahead() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(kRingAhead) : "memory");
@@ -263,7 +282,7 @@ template <int R, int DM, class Hooks, bool kRing = false>
 __device__ __forceinline__ float band_pass(const float *__restrict__ A, const float *__restrict__ B, int L, int D,
                                            int W, int v0, int v1, const Grp &g, Hooks &hooks, bool live,
                                            bool *abandoned, long long *cells, float *stage = nullptr,
-                                           float *ring = nullptr, int RC = 0) {
+                                           float *ring = nullptr, int RC = 0, const float *band = nullptr) {
     const bool stage_vec4 = (((uintptr_t)A) & 15) == 0;
     static_assert(R % 2 == 0, "rows are processed in pairs");
     static_assert(!kRing || (DM >= 16 && DM % 4 == 0), "rings hold float4-aligned wide points");
@@ -456,7 +475,29 @@ __device__ __forceinline__ float band_pass(const float *__restrict__ A, const fl
                 diag = (j >= 1 && j <= i0 + W) ? prev_in : INF;
             }
             // rows of this column inside the band: r in [j-W-i0, j+W-i0] and i < L
-            const unsigned vm = row_mask(j - W - i0, min(j + W - i0, L - 1 - i0), R);
+            // (the search kernel keeps the row mask: with its abandoning state the table's
+            // floors took it from 248 to 255 registers and 4% longer; the pairs kernel runs
+            // 7% faster with the table)
+            constexpr bool kTable = kRing && ring_band_table(R, DM) && !Hooks::kCells && !Hooks::kAbandon;
+            unsigned vm = 0u;
+            float floor_r[kTable ? R : 1];
+            int nin = 0;
+            if (kTable && i0 + R <= L) {
+                const float *be = band + (j - i0 + W) * kBandEntry;
+                const float4 ba = *reinterpret_cast<const float4 *>(be);
+                const float4 bb4 = *reinterpret_cast<const float4 *>(be + 4);
+                const float fl[8] = {ba.x, ba.y, ba.z, ba.w, bb4.x, bb4.y, bb4.z, bb4.w};
+#pragma unroll
+                for (int r = 0; r < (kTable ? R : 1); ++r) floor_r[r] = fl[r];
+                nin = __float_as_int(fl[kTable ? R : 1]);
+            } else {
+                vm = row_mask(j - W - i0, min(j + W - i0, L - 1 - i0), R);
+                if (kTable) {
+#pragma unroll
+                    for (int r = 0; r < (kTable ? R : 1); ++r) floor_r[r] = ((vm >> r) & 1u) ? 0.f : INF;
+                }
+                nin = __popc(vm);
+            }
             f2 bb[kDimPack ? 1 : DM];
             if (!kDimPack) {
 #pragma unroll
@@ -483,8 +524,13 @@ __device__ __forceinline__ float band_pass(const float *__restrict__ A, const fl
                 // row 2k
                 // cells outside the band get cost +inf (so the value is +inf), which keeps
                 // the masking off the row-to-row dependency chain
-                c0 = ((vm >> (2 * k)) & 1u) ? c0 : INF;
-                c1 = ((vm >> (2 * k + 1)) & 1u) ? c1 : INF;
+                if (kTable) {
+                    c0 = max_nan(c0, floor_r[kTable ? 2 * k : 0]);
+                    c1 = max_nan(c1, floor_r[kTable ? 2 * k + 1 : 0]);
+                } else {
+                    c0 = ((vm >> (2 * k)) & 1u) ? c0 : INF;
+                    c1 = ((vm >> (2 * k + 1)) & 1u) ? c1 : INF;
+                }
                 float left = col[2 * k];
                 float val = __fadd_rn(c0, min3f(up, left, diag));
                 diag = left;
@@ -502,7 +548,7 @@ __device__ __forceinline__ float band_pass(const float *__restrict__ A, const fl
             }
             bottom = col[R - 1];
             hooks.after_col(i0, j, bottom);
-            ncell += __popc(vm);
+            ncell += nin;
         }
         prev_in = in;
         if (Hooks::kAbandon) {
@@ -565,11 +611,28 @@ constexpr size_t stage_bytes() { return (size_t)128 * R * DM * sizeof(float); }
 
 // Block rings of the ring variant: the group's slice of the dynamic shared memory,
 // zeroed once (the dimensions D..DM-1 of every slot are never written afterwards).
-template <int R, int DM, bool kRing>
-__device__ __forceinline__ float *block_ring(float *smem, int G) {
+template <int R, int DM, bool kRing, bool kBand>
+__device__ __forceinline__ float *block_ring(float *smem, int G, int W, const float **band) {
+    *band = nullptr;
     if (!kRing) return nullptr;
     const int gf = ring_group_floats(R, DM, G);
     for (int k = threadIdx.x; k < (128 / G) * gf; k += blockDim.x) smem[k] = 0.f;
+    if (kBand && ring_band_table(R, DM)) {
+        float *tab = smem + (size_t)(128 / G) * gf;
+        const int nt = min(2 * W + R, G * (R + 1));  // valid (tile, G, W): 2W + R <= G(R+1)
+        for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+            const int dj = t - W;
+            int nin = 0;
+            for (int r = 0; r < R; ++r) {
+                const bool in = dj - r <= W && r - dj <= W;
+                tab[t * kBandEntry + r] = in ? 0.f : TC_INF;
+                nin += in;
+            }
+            tab[t * kBandEntry + R] = __int_as_float(nin);
+            for (int r = R + 1; r < kBandEntry; ++r) tab[t * kBandEntry + r] = 0.f;
+        }
+        *band = tab;
+    }
     __syncthreads();
     return smem + (size_t)(threadIdx.x / G) * gf;
 }
@@ -580,7 +643,8 @@ __global__ void __launch_bounds__(128) k_dtw_pairs(const float *__restrict__ A, 
                                                     float *__restrict__ ckpt, int C) {
     extern __shared__ __align__(16) float stage_smem[];
     float *stage = kRing ? nullptr : stage_smem + (size_t)threadIdx.x * R * DM;
-    float *ring = block_ring<R, DM, kRing>(stage_smem, G);
+    const float *band = nullptr;
+    float *ring = block_ring<R, DM, kRing, true>(stage_smem, G, W, &band);
     const int RC = ring_cols(G);
     Grp g = make_grp(G);
     g.mask = 0xffffffffu;  // lockstep: every group of the warp runs the same schedule
@@ -601,7 +665,7 @@ __global__ void __launch_bounds__(128) k_dtw_pairs(const float *__restrict__ A, 
         long long cells;
         const int64_t pp = live ? p : 0;
         float r = band_pass<R, DM, CkptHooks<R>, kRing>(A + (size_t)pp * L * D, B + (size_t)pp * L * D, L, D, W, 0,
-                                                       nv, g, h, live, &ab, &cells, stage, ring, RC);
+                                                       nv, g, h, live, &ab, &cells, stage, ring, RC, band);
         r = grp_min(r, g);
         if (live && g.lig == 0) dist[p] = r;
     }
@@ -632,7 +696,8 @@ __global__ void __launch_bounds__(128, (R >= 16 && DM <= 5) ? 4 : 1) k_dtw_nn(co
                                                  unsigned long long *__restrict__ counters) {
     extern __shared__ __align__(16) float stage_smem[];
     float *stage = kRing ? nullptr : stage_smem + (size_t)threadIdx.x * R * DM;
-    float *ring = block_ring<R, DM, kRing>(stage_smem, G);
+    const float *band = nullptr;
+    float *ring = block_ring<R, DM, kRing, false>(stage_smem, G, W, &band);
     const int RC = ring_cols(G);
     Grp g = make_grp(G);
     g.mask = 0xffffffffu;  // lockstep: every group of the warp runs the same schedule
@@ -668,7 +733,7 @@ __global__ void __launch_bounds__(128, (R >= 16 && DM <= 5) ? 4 : 1) k_dtw_nn(co
         bool ab = false;
         long long cells = 0;
         float r = band_pass<R, DM, NnHooks, kRing>(Q + (size_t)m * L * D, Cand + (size_t)n * L * D, L, D, W, 0, nv, g,
-                                                   h, live, &ab, &cells, stage, ring, RC);
+                                                   h, live, &ab, &cells, stage, ring, RC, band);
         r = grp_min(r, g);
         long long cs = cells;
         for (int o = G >> 1; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
