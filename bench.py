@@ -60,7 +60,7 @@ def _args():
     ap.add_argument("--no-few", action="store_true", help="skip the few-queries leg")
     ap.add_argument("--queries", type=int, default=0, help="queries of the workload to use (0 = all 1,024)")
     ap.add_argument("--candidates", type=int, default=0, help="candidates to use (0 = all 100,000)")
-    ap.add_argument("--leg", choices=["batched", "pairs", "cascade"], default=None,
+    ap.add_argument("--leg", choices=["batched", "pairs", "cascade", "few"], default=None,
                     help="run only this side leg and print its JSON (for profiler runs)")
     ap.add_argument("--workload", choices=["large", "mid"], default="large",
                     help="the search the timed steps run: the 1,024 x 100,000 headline (default) or the 256 x "
@@ -114,11 +114,17 @@ def few_queries_leg(tc, cand, q, wl, flush, stream, Ms=(1, 2, 4, 8, 16), reps=10
     """Searches of a few queries against the full candidate set: the LB_MV stream is
     then one pass over the candidates (HBM-bound; TMA-fed, stream-K split), the rest of
     the search is latency-bound.  Stage times come from CUDA events inside the replayed
-    graph (no host gaps); L2 is flushed before every call."""
+    graph (no host gaps).  Before every call the L2 is flushed by writing a 256 MB
+    buffer; in the `clean` timing a read of a second 256 MB buffer follows, so that the
+    flush's dirty lines are written back before the timed call (a write-only flush leaves
+    the L2 full of dirty lines, and their write-back then runs inside the LB_MV stream,
+    which streams the 102 MB candidate set at the same time)."""
     import torch
     hbm = _peaks().get("hbm_gbs")
     cand_bytes = wl.N * wl.spec.L * wl.spec.D * 4
-    out = {"M": list(Ms), "lb_mv_us": [], "lb_mv_hbm_frac": [], "search_us": []}
+    rd = torch.ones(flush.numel(), dtype=torch.float32, device=flush.device)
+    out = {"M": list(Ms), "lb_mv_us": [], "lb_mv_hbm_frac": [], "search_us": [],
+           "lb_mv_us_dirty_l2": [], "lb_mv_hbm_frac_dirty_l2": []}
     for M in Ms:
         x = tc.Index(cand, wl.W, wl.K)
         qm = q[:M].contiguous()
@@ -126,25 +132,36 @@ def few_queries_leg(tc, cand, q, wl, flush, stream, Ms=(1, 2, 4, 8, 16), reps=10
         for _ in range(3):
             x.nn(qm, out=o)
         torch.cuda.synchronize()
-        x.set_profiling(True)
-        tot = 0.0
-        for _ in range(reps):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            x.nn(qm, out=o)
-            e1.record(stream)
-            e1.synchronize()
-            tot += e0.elapsed_time(e1)
-        st, _ = x.stage_times()
-        x.set_profiling(False)
+        for clean in (True, False):
+            x.set_profiling(True)
+            tot = 0.0
+            for _ in range(reps):
+                flush.zero_()
+                if clean:
+                    rd.amax()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                x.nn(qm, out=o)
+                e1.record(stream)
+                e1.synchronize()
+                tot += e0.elapsed_time(e1)
+            st, _ = x.stage_times()
+            x.set_profiling(False)
+            t_mv = (st["lb_mv"] + st["lb_rest"]) / reps / 1e3
+            frac = cand_bytes / t_mv / 1e9 / hbm if hbm else None
+            if clean:
+                out["lb_mv_us"].append(t_mv * 1e6)
+                out["lb_mv_hbm_frac"].append(frac)
+                out["search_us"].append(tot / reps * 1e3)
+            else:
+                out["lb_mv_us_dirty_l2"].append(t_mv * 1e6)
+                out["lb_mv_hbm_frac_dirty_l2"].append(frac)
         x.close()
-        t_mv = (st["lb_mv"] + st["lb_rest"]) / reps / 1e3
-        out["lb_mv_us"].append(t_mv * 1e6)
-        out["lb_mv_hbm_frac"].append(cand_bytes / t_mv / 1e9 / hbm if hbm else None)
-        out["search_us"].append(tot / reps * 1e3)
-    out["note"] = ("lb_mv_hbm_frac: candidate bytes / LB_MV stage time / measured HBM copy bandwidth; "
-                   "search_us: whole tcdtw_nn call, profiling events on")
+    del rd
+    out["note"] = ("lb_mv_hbm_frac: candidate bytes / LB_MV stage time / measured HBM copy bandwidth, L2 "
+                   "flushed clean before each call (written, then evicted by a 256 MB read); "
+                   "*_dirty_l2: the same after the write alone; search_us: whole tcdtw_nn call, profiling "
+                   "events on, clean flush")
     return out
 
 
@@ -962,6 +979,13 @@ def run_leg(a):
     elif a.leg == "pairs":
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
         res = pairs_leg(tc, dev, flush)
+    elif a.leg == "few":
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        wl = SIDE
+        cand = torch.from_numpy(wl.candidates()).to(dev)
+        q = torch.from_numpy(wl.queries()).to(dev)
+        res = {"workload": wl.name,
+               "few_queries": few_queries_leg(tc, cand, q, wl, flush, torch.cuda.current_stream())}
     else:
         res = cascade_leg(tc, dev)
     print(json.dumps({"leg": a.leg, **res}), flush=True)
