@@ -560,17 +560,22 @@ def _roofline(stage_ms_step, st, M, N, L, D, n_sm, peaks, profile_dtw="ncu_k_dtw
             "achieved_note": what + ", per step, over its CUDA-event time inside the timed region"}
 
 
-def cpu_oracle_large(Q, C_sample, N_full, W, K):
+def cpu_oracle_large(Q, C_sample, N_full, W, K, target_s):
     """The oracle's pruned search (the paper's loop in FP64, OpenMP over queries, its
-    default bounds) on the host cores: every query of Q against the first
-    len(C_sample) candidates; queries/s extrapolated linearly to N_full candidates."""
+    default bounds) on the host cores: rounds of one query per core against the first
+    len(C_sample) candidates until target_s seconds have passed (or Q is used up);
+    queries/s extrapolated linearly to N_full candidates."""
     import oracle
     cores = oracle.num_threads()
-    t0 = time.perf_counter()
-    oracle.nn_pruned(Q, C_sample, W, K=K)
-    secs = time.perf_counter() - t0
-    value = len(Q) / (secs * N_full / len(C_sample))
-    return value, cores, secs
+    done, secs = 0, 0.0
+    while done < len(Q) and secs < target_s:
+        batch = Q[done:done + cores]
+        t0 = time.perf_counter()
+        oracle.nn_pruned(batch, C_sample, W, K=K)
+        secs += time.perf_counter() - t0
+        done += len(batch)
+    value = done / (secs * N_full / len(C_sample))
+    return value, cores, secs, done
 
 
 def side_leg(tc, dev, flush, stream, a):
@@ -872,11 +877,11 @@ def run_ours(a):
     torch.cuda.empty_cache()
 
     if C_s is not None:
-        nqc = 16
-        qps, cores, secs = cpu_oracle_large(Qn[:nqc], C_s, N, wl.W, wl.K)
+        qps, cores, secs, nqc = cpu_oracle_large(Qn[:64], C_s, N, wl.W, wl.K, a.cpu_seconds)
         res["cpu_baseline"] = {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
                                "sample": f"{nqc} queries x the first {ns} of the {N} candidates (pruned FP64 "
-                                         f"search, default bounds), extrapolated linearly to {N} candidates",
+                                         f"search, default bounds, rounds of one query per core until "
+                                         f"{a.cpu_seconds:g} s), extrapolated linearly to {N} candidates",
                                "seconds": secs}
         if not a.no_extra:
             res["cpu_bruteforce"] = cpu_brute_large_sample(max(cores, 4))
